@@ -1,0 +1,227 @@
+"""Plain FP64 CPU oracle for the Givens bidiagonal update (BGU).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the library.  The arithmetic lives in
+``bgu_oracle.c`` (Sec. 3.4, Algorithm 2, in the schedule documented at the top
+of that file); this module only marshals numpy arrays through ctypes.
+
+Functions
+---------
+rot(f, g)                       rotation generator (Eqs. giv, giv1)
+update(Q, d, e, P, B, C)        full update, Eqs. rk1 / bidiagsubproblem / bidiagplus
+generate(m, n, d, e, U, V)      the reduction only: rotation lists + new (d, e)
+apply_rows(X, rows, rotlist)    X(rows, :) <- X(rows, :) * prod(rotations)
+jacobi_sv(X)                    one-sided Jacobi singular values (tiny inputs)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+PHASES = ("spike", "phase1", "phase2", "phase3")
+
+
+class _RotList(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64),
+        ("cap", ctypes.c_int64),
+        ("c", ctypes.POINTER(ctypes.c_double)),
+        ("s", ctypes.POINTER(ctypes.c_double)),
+        ("a", ctypes.POINTER(ctypes.c_int32)),
+        ("phase", ctypes.POINTER(ctypes.c_int8)),
+    ]
+
+
+class _Counts(ctypes.Structure):
+    _fields_ = [
+        ("left", ctypes.c_int64 * 4),
+        ("right", ctypes.c_int64 * 4),
+        ("band_violations", ctypes.c_int64),
+        ("zero_violations", ctypes.c_int64),
+    ]
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+_ERR = {1: "invalid argument", 2: "out of memory", 3: "band invariant violated",
+        4: "an entry the schedule must zero is not exactly zero"}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        L.orc_rot.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.orc_rot.restype = ctypes.c_int
+        L.orc_update.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, dp, dp, dp, ctypes.c_int,
+                                                      dp, ctypes.c_int, dp, ctypes.c_int,
+                                                      ctypes.POINTER(_Counts)]
+        L.orc_update.restype = ctypes.c_int
+        L.orc_generate.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp, dp, ctypes.POINTER(_RotList),
+                                                        ctypes.POINTER(_RotList), ctypes.POINTER(_Counts)]
+        L.orc_generate.restype = ctypes.c_int
+        L.orc_project.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, dp, ctypes.c_int, dp,
+                                                       ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        L.orc_project.restype = None
+        L.orc_apply_rows.argtypes = [dp, ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int,
+                                     ctypes.POINTER(_RotList)]
+        L.orc_apply_rows.restype = None
+        L.orc_free_list.argtypes = [ctypes.POINTER(_RotList)]
+        L.orc_free_list.restype = None
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_jacobi_sv.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+        L.orc_jacobi_sv.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.array(a, dtype=np.float64, order="F", copy=True)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def rot(f: float, g: float):
+    """Returns (applied, c, s, r) for [c s; -s c][f; g] = [r; 0]."""
+    c, s, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ok = lib().orc_rot(float(f), float(g), ctypes.byref(c), ctypes.byref(s), ctypes.byref(r))
+    return bool(ok), c.value, s.value, r.value
+
+
+def _counts_dict(cnt):
+    return {
+        "left": {PHASES[i]: int(cnt.left[i]) for i in range(4)},
+        "right": {PHASES[i]: int(cnt.right[i]) for i in range(4)},
+        "total": int(sum(cnt.left) + sum(cnt.right)),
+        "band_violations": int(cnt.band_violations),
+        "zero_violations": int(cnt.zero_violations),
+    }
+
+
+def update(Q, d, e, P, B, C, check=True):
+    """Returns (Q+, d+, e+, P+, counts) for A + B C^T with A = Q diag-band(d, e) P^T."""
+    Q = _f64(Q); P = _f64(P); d = _f64(d); e = _f64(e)
+    m, n = Q.shape[0], P.shape[0]
+    B = _f64(np.asarray(B, dtype=np.float64).reshape(m, -1))
+    C = _f64(np.asarray(C, dtype=np.float64).reshape(n, -1))
+    r = B.shape[1]
+    if e.size == 0:
+        e = np.zeros(1)
+    cnt = _Counts()
+    rc = lib().orc_update(m, n, r, _dp(Q), m, _dp(d), _dp(e), _dp(P), n, _dp(B), m, _dp(C), n,
+                          ctypes.byref(cnt))
+    if rc != 0 and check:
+        raise OracleError(_ERR.get(rc, str(rc)) + f" ({_counts_dict(cnt)})")
+    return Q, d, e[: n - 1], P, _counts_dict(cnt)
+
+
+class RotationList:
+    """Rotations in generation order: pair (a, a+1) with 1-based a."""
+
+    def __init__(self, raw: _RotList):
+        k = raw.count
+        if k:
+            self.c = np.ctypeslib.as_array(raw.c, shape=(k,)).copy()
+            self.s = np.ctypeslib.as_array(raw.s, shape=(k,)).copy()
+            self.a = np.ctypeslib.as_array(raw.a, shape=(k,)).copy()
+            self.phase = np.ctypeslib.as_array(raw.phase, shape=(k,)).copy()
+        else:
+            self.c = np.zeros(0); self.s = np.zeros(0)
+            self.a = np.zeros(0, np.int32); self.phase = np.zeros(0, np.int8)
+
+    def __len__(self):
+        return len(self.c)
+
+    def _raw(self):
+        raw = _RotList()
+        raw.count = len(self)
+        raw.cap = len(self)
+        self._keep = (np.ascontiguousarray(self.c), np.ascontiguousarray(self.s),
+                      np.ascontiguousarray(self.a, dtype=np.int32),
+                      np.ascontiguousarray(self.phase, dtype=np.int8))
+        raw.c = _dp(self._keep[0]); raw.s = _dp(self._keep[1])
+        raw.a = self._keep[2].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        raw.phase = self._keep[3].ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+        return raw
+
+
+def project(Q, P, B, C):
+    """U = Q^T B, V = P^T C with the oracle's plain loops."""
+    Q = _f64(Q); P = _f64(P)
+    m, n = Q.shape[0], P.shape[0]
+    B = _f64(np.asarray(B, dtype=np.float64).reshape(m, -1))
+    C = _f64(np.asarray(C, dtype=np.float64).reshape(n, -1))
+    r = B.shape[1]
+    U = np.zeros((m, r), order="F"); V = np.zeros((n, r), order="F")
+    lib().orc_project(m, n, r, _dp(Q), m, _dp(P), n, _dp(B), m, _dp(C), n, _dp(U), _dp(V))
+    return U, V
+
+
+def generate(m, n, d, e, U, V, check=True):
+    """The reduction alone: returns (d+, e+, left RotationList, right RotationList, counts)."""
+    d = _f64(d); e = _f64(e) if n > 1 else np.zeros(1)
+    U = _f64(np.asarray(U, dtype=np.float64).reshape(m, -1))
+    V = _f64(np.asarray(V, dtype=np.float64).reshape(n, -1))
+    r = U.shape[1]
+    L, R, cnt = _RotList(), _RotList(), _Counts()
+    rc = lib().orc_generate(m, n, r, _dp(d), _dp(e), _dp(U), _dp(V), ctypes.byref(L),
+                            ctypes.byref(R), ctypes.byref(cnt))
+    try:
+        if rc != 0 and check:
+            raise OracleError(_ERR.get(rc, str(rc)) + f" ({_counts_dict(cnt)})")
+        return d, e[: n - 1], RotationList(L), RotationList(R), _counts_dict(cnt)
+    finally:
+        lib().orc_free_list(ctypes.byref(L))
+        lib().orc_free_list(ctypes.byref(R))
+
+
+def apply_rows(X, rows, rotlist: RotationList):
+    """Returns a copy of X with the rotations applied to the given (0-based) rows."""
+    X = _f64(X)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    raw = rotlist._raw()
+    lib().orc_apply_rows(_dp(X), X.shape[0], X.shape[1],
+                         rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(rows),
+                         ctypes.byref(raw))
+    return X
+
+
+def jacobi_sv(X, max_sweeps=60):
+    """Singular values of a small matrix by one-sided (Hestenes) Jacobi, sorted descending."""
+    X = _f64(X)
+    rows, cols = X.shape
+    if rows < cols:
+        X = _f64(X.T)
+        rows, cols = cols, rows
+    sv = np.zeros(cols)
+    sweeps = lib().orc_jacobi_sv(_dp(X), rows, cols, _dp(sv), max_sweeps)
+    if sweeps < 0:
+        raise OracleError("Jacobi did not converge")
+    return np.sort(sv)[::-1]
+
+
+def bidiag_dense(d, e, rows=None):
+    """The bidiagonal as a dense (rows x n) matrix; rows defaults to n."""
+    n = len(d)
+    rows = n if rows is None else rows
+    M = np.zeros((rows, n))
+    M[np.arange(n), np.arange(n)] = d
+    if n > 1:
+        M[np.arange(n - 1), np.arange(1, n)] = e
+    return M
