@@ -1,0 +1,150 @@
+/*
+ * bdu.h -- C ABI of the GB300 bidiagonal-update library (libbdu.so).
+ *
+ * The library keeps a bidiagonal factorization A = Q * Bd * P^T resident on
+ * one GPU and updates it under low-rank changes A+ = A + B * C^T with the
+ * Givens bidiagonal update (BGU) of Brust & Saunders, "Fast and Accurate
+ * SVD-Type Updating in Streaming Data":
+ *   - the factorization and its notation: Sec. 1, Eq. bidiag (Q m x m and
+ *     P n x n orthogonal, Bd upper bidiagonal with diagonal alpha_i = d[i]
+ *     and superdiagonal beta_i = e[i]);
+ *   - the update model: Eq. main (B m x r, C n x r) and Sec. 3.2, Eqs. rk1,
+ *     bidiagsubproblem, bidiagplus (b+ = Q^T b, c+ = P^T c, Q+ = Q Q1,
+ *     P+ = P P1);
+ *   - the reduction of Bd + b+ c+^T with Givens rotations and bulge chasing:
+ *     Sec. 3.4, Algorithm 2 (Eqs. giv, giv1, gfill), including the m > n
+ *     "spike" and the zero-entry handling.
+ * Rank r is processed as r rank-1 steps (Sec. 3.2).  The rotation schedule is
+ * fixed (the first right vector P(:,1) is never rotated), which makes Bd+
+ * unique up to signs; in the FP64 form every result is bit-identical to the
+ * library's CPU reference of the same schedule.
+ *
+ * Conventions for every entry point:
+ *   - matrices are column-major, double precision on the host side;
+ *   - requirement m >= n >= 1;
+ *   - host pointers are copied in or out and stay owned by the caller; all
+ *     device memory is owned by the handle (see bdu_set_allocator);
+ *   - functions return a bdu_status and never abort; the message of the most
+ *     recent failure of a handle is available from bdu_last_error;
+ *   - after BDU_ECUDA or BDU_ETIMEOUT a handle is poisoned: only bdu_read,
+ *     bdu_last_error and bdu_destroy are accepted afterwards;
+ *   - a handle is used by one host thread at a time (BDU_EBUSY otherwise).
+ */
+#ifndef BDU_H
+#define BDU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdu_ctx *bdu_handle;
+
+typedef enum {
+  BDU_OK = 0,
+  BDU_EINVAL = 1,    /* bad argument (null pointer, m < n, r < 0, NaN/Inf input, ...) */
+  BDU_ENOMEM = 2,    /* device allocation failed; the handle stays usable */
+  BDU_ECUDA = 3,     /* CUDA runtime error; handle poisoned */
+  BDU_ETIMEOUT = 4,  /* a bounded device-side wait expired; handle poisoned */
+  BDU_ENOTORTH = 5,  /* orthogonality check failed beyond repair */
+  BDU_EBUSY = 6,     /* handle in use by another thread */
+  BDU_EPOISONED = 7, /* handle poisoned by an earlier failure */
+  BDU_EINTERNAL = 8  /* a device-side invariant check failed (band or schedule) */
+} bdu_status;
+
+/* Storage/arithmetic form of Q and P. */
+enum {
+  BDU_FP64 = 0, /* Q, P in FP64; every step in FP64 (bit-identical to the CPU reference) */
+  BDU_MIXED = 1 /* Q, P stored and rotated in FP32; projection accumulated, rotations
+                   generated and Bd kept in FP64 */
+};
+
+typedef struct {
+  int precision;      /* BDU_FP64 (default) or BDU_MIXED */
+  int nb;             /* panel width of the blocked apply; 0 = library choice */
+  double reorth_tol;  /* BDU_MIXED: re-orthogonalize Q (P) when the estimated
+                         ||Q^T Q - I||_2 exceeds this; 0 = never (default 1e-6) */
+  int check_every;    /* BDU_MIXED: updates between orthogonality estimates (default 10) */
+  void *cuda_stream;  /* cudaStream_t used for all work; NULL = library-owned stream */
+  int device;         /* CUDA device ordinal (default 0) */
+} bdu_options;
+
+typedef struct {
+  int64_t updates;          /* rank-1 columns processed */
+  int64_t rot_left[4];      /* left rotations (on Q) by phase: spike, 1, 2, 3 */
+  int64_t rot_right[4];     /* right rotations (on P) by phase */
+  int64_t chase_steps;      /* synchronous steps of the bulge-chase engine */
+  int64_t reorth_q, reorth_p; /* re-orthogonalizations performed */
+  double ortho_q, ortho_p;  /* last estimate of ||Q^T Q - I||_2, ||P^T P - I||_2 (-1 = none) */
+} bdu_stats_t;
+
+/* Fills *opt with the defaults listed above. */
+void bdu_default_options(bdu_options *opt);
+
+/* Creates a handle holding A = Q diag-band(d, e) P^T on the GPU.
+ *   Q: m*m host doubles (column-major), P: n*n, d: n, e: n-1 (may be NULL
+ *   when n == 1).  Q and P are assumed orthogonal (not checked: O(m^3)).
+ *   opt may be NULL (defaults).
+ * Errors: BDU_EINVAL (null pointers, m < n, n < 1, non-finite input),
+ *         BDU_ENOMEM, BDU_ECUDA.  On error *h is set to NULL. */
+bdu_status bdu_create(bdu_handle *h, int64_t m, int64_t n, const double *Q, const double *d,
+                      const double *e, const double *P, const bdu_options *opt);
+
+/* A+ = A + B C^T with host matrices B (m*r) and C (n*r), column-major
+ * (Eq. main).  The call returns once the work is queued on the handle's
+ * stream; host buffers are consumed before return.  r == 0 is a no-op.
+ * Errors: BDU_EINVAL (null pointer with r > 0, non-finite input), BDU_ENOMEM,
+ *         BDU_ECUDA, BDU_EBUSY, BDU_EPOISONED. */
+bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r);
+
+/* As bdu_update with B and C already in device memory (FP64, column-major,
+ * leading dimensions m and n).  The buffers must stay valid until the work on
+ * the handle's stream has completed. */
+bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r);
+
+/* Waits for all queued work and reports device-side failures
+ * (BDU_ETIMEOUT, BDU_EINTERNAL, BDU_ECUDA). */
+bdu_status bdu_sync(bdu_handle h);
+
+/* Copies the current factorization to host buffers (any may be NULL):
+ * Q m*m, d n, e n-1, P n*n.  Synchronizes the handle's stream. */
+bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P);
+
+/* Copies the rotations of the most recent rank-1 column to host buffers, in
+ * the order in which they are applied: side 0 = left rotations (on Q),
+ * side 1 = right rotations (on P).  Each rotation is (c[k], s[k], a[k]) with
+ * a 1-based pair (a, a+1) and pair update x_a <- c x_a + s x_b,
+ * x_b <- -s x_a + c x_b (Eqs. giv, giv1).  *count receives the number of
+ * rotations; at most cap are written.  Synchronizes. */
+bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
+                              int64_t cap, int64_t *count);
+
+/* Statistics since creation.  Synchronizes. */
+bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out);
+
+/* Releases all device memory of the handle.  NULL is accepted. */
+void bdu_destroy(bdu_handle h);
+
+/* Message for the most recent failure on h (or of a failed bdu_create when
+ * h is NULL; thread-local).  Never NULL. */
+const char *bdu_last_error(bdu_handle h);
+
+/* Replaces the device allocator used by handles created afterwards
+ * (process-wide).  alloc(bytes, device, ctx) returns a device pointer or
+ * NULL; release(ptr, device, ctx) frees it.  Passing NULL for both restores
+ * cudaMalloc/cudaFree.  Lets a host framework (e.g. PyTorch's caching
+ * allocator) own the memory, and lets tests inject allocation failures. */
+typedef void *(*bdu_alloc_fn)(size_t bytes, int device, void *ctx);
+typedef void (*bdu_free_fn)(void *ptr, int device, void *ctx);
+void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int bdu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDU_H */

@@ -1,0 +1,228 @@
+"""ctypes binding of libbdu (include/bdu.h): argument marshalling only.
+
+Every step of the update runs in the library's CUDA kernels.  Loading fails
+loudly when libbdu.so is missing; there is no other implementation to fall
+back to.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+FP64, MIXED = 0, 1
+STATUS = {0: "BDU_OK", 1: "BDU_EINVAL", 2: "BDU_ENOMEM", 3: "BDU_ECUDA", 4: "BDU_ETIMEOUT",
+          5: "BDU_ENOTORTH", 6: "BDU_EBUSY", 7: "BDU_EPOISONED", 8: "BDU_EINTERNAL"}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bdu.h")
+
+
+class BduError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int64), ("rot_left", ctypes.c_int64 * 4),
+                ("rot_right", ctypes.c_int64 * 4), ("chase_steps", ctypes.c_int64),
+                ("reorth_q", ctypes.c_int64), ("reorth_p", ctypes.c_int64),
+                ("ortho_q", ctypes.c_double), ("ortho_p", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libbdu.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libbdu.so not found at {_build.LIB}; run paper_2509_02840_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    dp = ctypes.POINTER(ctypes.c_double)
+    H = ctypes.c_void_p
+    L.bdu_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.bdu_default_options.restype = None
+    L.bdu_create.argtypes = [ctypes.POINTER(H), ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
+                             ctypes.POINTER(Options)]
+    L.bdu_create.restype = ctypes.c_int
+    L.bdu_update.argtypes = [H, dp, dp, ctypes.c_int64]
+    L.bdu_update.restype = ctypes.c_int
+    L.bdu_update_dev.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.bdu_update_dev.restype = ctypes.c_int
+    L.bdu_sync.argtypes = [H]
+    L.bdu_sync.restype = ctypes.c_int
+    L.bdu_read.argtypes = [H, dp, dp, dp, dp]
+    L.bdu_read.restype = ctypes.c_int
+    L.bdu_read_rotations.argtypes = [H, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.bdu_read_rotations.restype = ctypes.c_int
+    L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
+    L.bdu_stats.restype = ctypes.c_int
+    L.bdu_destroy.argtypes = [H]
+    L.bdu_destroy.restype = None
+    L.bdu_last_error.argtypes = [H]
+    L.bdu_last_error.restype = ctypes.c_char_p
+    L.bdu_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ctypes.c_void_p]
+    L.bdu_set_allocator.restype = None
+    L.bdu_version.argtypes = []
+    L.bdu_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in include/bdu.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bdu_[a-z_0-9]+)\s*\(", text)) - {"bdu_alloc_fn", "bdu_free_fn"})
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(L, h, code):
+    if code != 0:
+        msg = L.bdu_last_error(h)
+        raise BduError(code, msg.decode() if msg else "")
+
+
+_keep_alloc = []
+
+
+def set_allocator(alloc=None, free=None):
+    """Installs Python callables alloc(bytes, device) -> int and free(ptr, device)
+    as the device allocator of handles created afterwards; None restores cudaMalloc."""
+    L = load()
+    if alloc is None:
+        L.bdu_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        _keep_alloc.clear()
+        return
+    fa = ALLOC_FN(lambda nbytes, dev, ctx: alloc(int(nbytes), int(dev)) or None)
+    ff = FREE_FN(lambda ptr, dev, ctx: free(int(ptr), int(dev)))
+    _keep_alloc[:] = [fa, ff]
+    L.bdu_set_allocator(fa, ff, None)
+
+
+def use_torch_allocator():
+    """Routes the library's device memory through PyTorch's caching allocator."""
+    import torch
+
+    def alloc(nbytes, dev):
+        return int(torch.cuda.caching_allocator_alloc(nbytes, device=dev))
+
+    def free(ptr, dev):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)
+
+
+class Factorization:
+    """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
+
+    def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
+                 check_every=None):
+        L = load()
+        Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
+        self.m, self.n = Q.shape[0], P.shape[0]
+        if e.size == 0:
+            e = np.zeros(1)
+        opt = Options()
+        L.bdu_default_options(ctypes.byref(opt))
+        opt.precision = int(precision)
+        opt.device = int(device)
+        if reorth_tol is not None:
+            opt.reorth_tol = float(reorth_tol)
+        if check_every is not None:
+            opt.check_every = int(check_every)
+        if stream is not None:
+            opt.cuda_stream = ctypes.c_void_p(int(stream))
+        h = ctypes.c_void_p()
+        code = L.bdu_create(ctypes.byref(h), self.m, self.n, _dp(Q), _dp(d), _dp(e), _dp(P), ctypes.byref(opt))
+        if code != 0:
+            raise BduError(code, L.bdu_last_error(None).decode())
+        self._h = h
+        self._L = L
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bdu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def update(self, B, C):
+        B = _f64(np.asarray(B, dtype=np.float64).reshape(self.m, -1))
+        C = _f64(np.asarray(C, dtype=np.float64).reshape(self.n, -1))
+        if B.shape[1] != C.shape[1]:
+            raise ValueError("B and C need the same number of columns")
+        _check(self._L, self._h, self._L.bdu_update(self._h, _dp(B), _dp(C), B.shape[1]))
+
+    def update_dev(self, ptrB: int, ptrC: int, r: int):
+        """B, C as device pointers (FP64, column-major, leading dimensions m and n)."""
+        _check(self._L, self._h, self._L.bdu_update_dev(self._h, ctypes.c_void_p(ptrB), ctypes.c_void_p(ptrC), int(r)))
+
+    def sync(self):
+        _check(self._L, self._h, self._L.bdu_sync(self._h))
+
+    def read(self):
+        m, n = self.m, self.n
+        Q = np.zeros((m, m), order="F"); P = np.zeros((n, n), order="F")
+        d = np.zeros(n); e = np.zeros(max(n - 1, 1))
+        _check(self._L, self._h, self._L.bdu_read(self._h, _dp(Q), _dp(d), _dp(e), _dp(P)))
+        return Q, d, e[: n - 1], P
+
+    def read_bidiagonal(self):
+        n = self.n
+        d = np.zeros(n); e = np.zeros(max(n - 1, 1))
+        _check(self._L, self._h, self._L.bdu_read(self._h, None, _dp(d), _dp(e), None))
+        return d, e[: n - 1]
+
+    def read_rotations(self, side):
+        cnt = ctypes.c_int64()
+        _check(self._L, self._h, self._L.bdu_read_rotations(self._h, side, None, None, None, 0, ctypes.byref(cnt)))
+        k = cnt.value
+        c = np.zeros(max(k, 1)); s = np.zeros(max(k, 1)); a = np.zeros(max(k, 1), dtype=np.int32)
+        _check(self._L, self._h, self._L.bdu_read_rotations(
+            self._h, side, _dp(c), _dp(s), a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), k, ctypes.byref(cnt)))
+        return c[:k], s[:k], a[:k]
+
+    def stats(self):
+        st = Stats()
+        _check(self._L, self._h, self._L.bdu_stats(self._h, ctypes.byref(st)))
+        return {"updates": st.updates, "rot_left": list(st.rot_left), "rot_right": list(st.rot_right),
+                "chase_steps": st.chase_steps, "reorth_q": st.reorth_q, "reorth_p": st.reorth_p,
+                "ortho_q": st.ortho_q, "ortho_p": st.ortho_p}

@@ -1,0 +1,500 @@
+// Host side of the C ABI declared in include/bdu.h: handle lifecycle,
+// argument validation, device memory, and the order of the kernels of one
+// update (Sec. 3.2: project, reduce, compose).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bdu_internal.cuh"
+
+namespace bdu {
+cudaError_t launch_project_nz(int precision, const void *X, int64_t ld, int nrow, int ncol,
+                              const double *B, int64_t ldb, int r, double *U, int64_t ldu,
+                              int32_t *nz_ws, cudaStream_t s);
+}
+
+using namespace bdu;
+
+namespace {
+
+// ---------------------------------------------------------------- allocator
+std::atomic<bdu_alloc_fn> g_alloc{nullptr};
+std::atomic<bdu_free_fn> g_free{nullptr};
+std::atomic<void *> g_alloc_ctx{nullptr};
+
+thread_local char t_create_err[512] = "";
+
+struct Alloc {
+  bdu_alloc_fn fa;
+  bdu_free_fn ff;
+  void *ctx;
+  int device;
+  void *get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (fa) return fa(bytes, device, ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void *p) {
+    if (!p) return;
+    if (ff) ff(p, device, ctx);
+    else cudaFree(p);
+  }
+};
+
+}  // namespace
+
+struct bdu_ctx {
+  int64_t m, n, N;
+  bdu_options opt;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  Alloc al;
+  std::vector<void *> blocks;
+  // factorization
+  void *Q, *P;   // FP64 or FP32 (opt.precision)
+  double *band;  // band_doubles(m, n)
+  // per-update workspace (grown on demand)
+  int64_t rcap;
+  double *dB, *dC, *U, *V;
+  int32_t *nzB, *nzC;
+  // rotation stream of one rank-1 column
+  RotStream st;
+  int *status;
+  unsigned long long *counters;
+  double *scratch64;  // for conversions in read (mixed form)
+  // bookkeeping
+  int64_t updates;
+  bool poisoned;
+  std::atomic<int> busy;
+  char err[512];
+};
+
+namespace {
+
+size_t esize(const bdu_ctx *h) { return h->opt.precision == BDU_FP64 ? sizeof(double) : sizeof(float); }
+
+bdu_status fail(bdu_ctx *h, bdu_status code, const char *fmt, ...) {
+  char *buf = h ? h->err : t_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  if (h && (code == BDU_ECUDA || code == BDU_ETIMEOUT || code == BDU_EINTERNAL)) h->poisoned = true;
+  return code;
+}
+
+bdu_status cuda_fail(bdu_ctx *h, cudaError_t e, const char *what) {
+  return fail(h, BDU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dev_alloc(bdu_ctx *h, size_t bytes) {
+  void *p = h->al.get(bytes);
+  if (p) h->blocks.push_back(p);
+  return p;
+}
+
+void dev_free(bdu_ctx *h, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->blocks.size(); i++)
+    if (h->blocks[i] == p) {
+      h->blocks[i] = h->blocks.back();
+      h->blocks.pop_back();
+      break;
+    }
+  h->al.put(p);
+}
+
+bool all_finite(const double *x, int64_t count) {
+  for (int64_t i = 0; i < count; i++)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+struct Guard {
+  bdu_ctx *h;
+  bool ok;
+  explicit Guard(bdu_ctx *hh) : h(hh), ok(false) {
+    int expect = 0;
+    ok = h->busy.compare_exchange_strong(expect, 1);
+  }
+  ~Guard() {
+    if (ok) h->busy.store(0);
+  }
+};
+
+bdu_status ensure_rank_workspace(bdu_ctx *h, int64_t r) {
+  if (r <= h->rcap) return BDU_OK;
+  double *dB = (double *)h->al.get(sizeof(double) * h->m * r);
+  double *dC = (double *)h->al.get(sizeof(double) * h->n * r);
+  double *U = (double *)h->al.get(sizeof(double) * h->m * r);
+  double *V = (double *)h->al.get(sizeof(double) * h->n * r);
+  int32_t *nzB = (int32_t *)h->al.get(sizeof(int32_t) * (h->m * r + r));
+  int32_t *nzC = (int32_t *)h->al.get(sizeof(int32_t) * (h->n * r + r));
+  if (!dB || !dC || !U || !V || !nzB || !nzC) {
+    h->al.put(dB); h->al.put(dC); h->al.put(U); h->al.put(V); h->al.put(nzB); h->al.put(nzC);
+    return fail(h, BDU_ENOMEM, "device allocation for a rank-%lld update failed", (long long)r);
+  }
+  dev_free(h, h->dB); dev_free(h, h->dC); dev_free(h, h->U); dev_free(h, h->V);
+  dev_free(h, h->nzB); dev_free(h, h->nzC);
+  for (void *p : {(void *)dB, (void *)dC, (void *)U, (void *)V, (void *)nzB, (void *)nzC})
+    h->blocks.push_back(p);
+  h->dB = dB; h->dC = dC; h->U = U; h->V = V; h->nzB = nzB; h->nzC = nzC;
+  h->rcap = r;
+  return BDU_OK;
+}
+
+bdu_status check_device_status(bdu_ctx *h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronizing the handle's stream");
+  if (st & ERR_STEPS) return fail(h, BDU_ETIMEOUT, "the bulge-chase engine exceeded its step budget");
+  if (st) return fail(h, BDU_EINTERNAL, "device invariant check failed (status bits 0x%x)", st);
+  return BDU_OK;
+}
+
+// One update with B, C already in device memory.
+bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
+  const int m = (int)h->m, n = (int)h->n;
+  cudaStream_t s = h->stream;
+  cudaError_t e;
+  // K1: U = Q^T B, V = P^T C with the current factors
+  e = launch_project_nz(h->opt.precision, h->Q, m, m, m, dB, m, (int)r, h->U, m, h->nzB, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "projection of B");
+  e = launch_project_nz(h->opt.precision, h->P, n, n, n, dC, n, (int)r, h->V, n, h->nzC, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "projection of C");
+  BandPtrs bp = band_ptrs(h->band, m, n);
+  for (int64_t k = 0; k < r; k++) {
+    // u = U(:,k), v = V(:,k) (1-based in the band buffer)
+    e = cudaMemcpyAsync(bp.u + 1, h->U + k * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bp.v + 1, h->V + k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Ln, 0, sizeof(int32_t) * h->st.T, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Rn, 0, sizeof(int32_t) * h->st.T, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "staging a rank-1 column");
+    ChaseArgs a;
+    a.m = m; a.n = n; a.band = bp;
+    a.rx = (int)(r - k - 1);
+    a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
+    a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
+    a.st = h->st; a.status = h->status; a.counters = h->counters;
+    e = launch_chase(a, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+    // K3: Q <- Q prod G^T, P <- P prod H
+    e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
+    e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
+    h->updates++;
+  }
+  return BDU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bdu_default_options(bdu_options *opt) {
+  if (!opt) return;
+  opt->precision = BDU_FP64;
+  opt->nb = 0;
+  opt->reorth_tol = 1e-6;
+  opt->check_every = 10;
+  opt->cuda_stream = nullptr;
+  opt->device = 0;
+}
+
+int bdu_version(void) { return 100; }
+
+void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx) {
+  g_alloc.store(alloc);
+  g_free.store(release);
+  g_alloc_ctx.store(ctx);
+}
+
+const char *bdu_last_error(bdu_handle h) { return h ? h->err : t_create_err; }
+
+void bdu_destroy(bdu_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void *p : h->blocks) h->al.put(p);
+  h->blocks.clear();
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, const double *d,
+                      const double *e, const double *P, const bdu_options *opt) {
+  if (!out) return fail(nullptr, BDU_EINVAL, "bdu_create: output handle pointer is NULL");
+  *out = nullptr;
+  if (n < 1 || m < n) return fail(nullptr, BDU_EINVAL, "bdu_create: need m >= n >= 1 (m=%lld n=%lld)", (long long)m, (long long)n);
+  if (m > (1LL << 20)) return fail(nullptr, BDU_EINVAL, "bdu_create: m=%lld exceeds the supported 2^20", (long long)m);
+  if (!Q || !d || !P || (n > 1 && !e)) return fail(nullptr, BDU_EINVAL, "bdu_create: NULL input pointer");
+  bdu_options o;
+  bdu_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != BDU_FP64 && o.precision != BDU_MIXED)
+    return fail(nullptr, BDU_EINVAL, "bdu_create: unknown precision %d", o.precision);
+  if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
+    return fail(nullptr, BDU_EINVAL, "bdu_create: non-finite value in Q, d, e or P");
+
+  bdu_ctx *h = new (std::nothrow) bdu_ctx();
+  if (!h) return fail(nullptr, BDU_ENOMEM, "bdu_create: host allocation failed");
+  h->m = m; h->n = n; h->N = (m > n) ? n + 1 : n;
+  h->opt = o; h->device = o.device;
+  h->busy.store(0);
+  h->al = Alloc{g_alloc.load(), g_free.load(), g_alloc_ctx.load(), o.device};
+  cudaError_t ce = cudaSetDevice(o.device);
+  if (ce != cudaSuccess) {
+    fail(nullptr, BDU_ECUDA, "cudaSetDevice(%d): %s", o.device, cudaGetErrorString(ce));
+    delete h;
+    return BDU_ECUDA;
+  }
+  if (o.cuda_stream) {
+    h->stream = (cudaStream_t)o.cuda_stream;
+    h->own_stream = false;
+  } else {
+    ce = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+      fail(nullptr, BDU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(ce));
+      delete h;
+      return BDU_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  const size_t es = esize(h);
+  const int T = num_tasks(m, n), cap = task_cap(n);
+  const size_t tc = (size_t)T * cap;
+  h->Q = dev_alloc(h, es * m * m);
+  h->P = dev_alloc(h, es * n * n);
+  h->band = (double *)dev_alloc(h, sizeof(double) * band_doubles(m, n));
+  h->st.T = T; h->st.cap = cap;
+  h->st.Lc = (double *)dev_alloc(h, sizeof(double) * tc);
+  h->st.Ls = (double *)dev_alloc(h, sizeof(double) * tc);
+  h->st.Rc = (double *)dev_alloc(h, sizeof(double) * tc);
+  h->st.Rs = (double *)dev_alloc(h, sizeof(double) * tc);
+  h->st.La = (int32_t *)dev_alloc(h, sizeof(int32_t) * tc);
+  h->st.Ra = (int32_t *)dev_alloc(h, sizeof(int32_t) * tc);
+  h->st.Ln = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
+  h->st.Rn = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
+  h->st.Sc = (double *)dev_alloc(h, sizeof(double) * (m + 1));
+  h->st.Ss = (double *)dev_alloc(h, sizeof(double) * (m + 1));
+  h->st.Sa = (int32_t *)dev_alloc(h, sizeof(int32_t) * (m + 1));
+  h->st.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
+  h->status = (int *)dev_alloc(h, sizeof(int) * 4);
+  h->counters = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * 16);
+  if (o.precision == BDU_MIXED) h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
+  bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
+            h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
+            h->status && h->counters && (o.precision == BDU_FP64 || h->scratch64);
+  if (!ok) {
+    fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (m=%lld n=%lld)", (long long)m, (long long)n);
+    bdu_destroy(h);
+    return BDU_ENOMEM;
+  }
+  if (ensure_rank_workspace(h, 1) != BDU_OK) {
+    fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (workspace)");
+    bdu_destroy(h);
+    return BDU_ENOMEM;
+  }
+  // band: diagonal d, superdiagonal e; row 1 kept densely
+  const int64_t nb = band_doubles(m, n);
+  std::vector<double> hb(nb, 0.0);
+  BandPtrs hp = band_ptrs(hb.data(), m, n);
+  hp.r1[1] = d[0];
+  if (n > 1) hp.r1[2] = e[0];
+  for (int64_t i = 2; i <= n; i++) hp.dg[2][i] = d[i - 1];
+  for (int64_t i = 2; i <= n - 1; i++) hp.dg[3][i] = e[i - 1];
+  ce = cudaMemcpyAsync(h->band, hb.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess) {
+    if (o.precision == BDU_FP64) {
+      ce = cudaMemcpyAsync(h->Q, Q, sizeof(double) * m * m, cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->P, P, sizeof(double) * n * n, cudaMemcpyHostToDevice, h->stream);
+    } else {
+      ce = cudaMemcpyAsync(h->scratch64, Q, sizeof(double) * m * m, cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(h->scratch64, (float *)h->Q, m * m, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->scratch64, P, sizeof(double) * n * n, cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(h->scratch64, (float *)h->P, n * n, h->stream);
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 16, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->st.Sn, 0, sizeof(int32_t) * 4, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) {
+    fail(nullptr, BDU_ECUDA, "bdu_create: %s", cudaGetErrorString(ce));
+    bdu_destroy(h);
+    return BDU_ECUDA;
+  }
+  h->err[0] = 0;
+  *out = h;
+  return BDU_OK;
+}
+
+static bdu_status update_common(bdu_handle h, const double *B, const double *C, int64_t r, bool host) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure: %s", h->err);
+  if (r < 0) return fail(h, BDU_EINVAL, "negative rank %lld", (long long)r);
+  if (r == 0) return BDU_OK;
+  if (!B || !C) return fail(h, BDU_EINVAL, "NULL update pointer");
+  if (r > 4096) return fail(h, BDU_EINVAL, "rank %lld exceeds 4096", (long long)r);
+  if (host && (!all_finite(B, h->m * r) || !all_finite(C, h->n * r)))
+    return fail(h, BDU_EINVAL, "non-finite value in B or C");
+  cudaError_t ce = cudaSetDevice(h->device);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaSetDevice");
+  bdu_status st = ensure_rank_workspace(h, r);
+  if (st != BDU_OK) return st;
+  const double *dB = B, *dC = C;
+  if (host) {
+    ce = cudaMemcpyAsync(h->dB, B, sizeof(double) * h->m * r, cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->dC, C, sizeof(double) * h->n * r, cudaMemcpyHostToDevice, h->stream);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "copying B, C to the device");
+    dB = h->dB; dC = h->dC;
+  }
+  return run_update(h, dB, dC, r);
+}
+
+bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r) {
+  return update_common(h, B, C, r, true);
+}
+
+bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r) {
+  return update_common(h, dB, dC, r, false);
+}
+
+bdu_status bdu_sync(bdu_handle h) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
+  cudaSetDevice(h->device);
+  return check_device_status(h);
+}
+
+bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  cudaSetDevice(h->device);
+  bdu_status st = BDU_OK;
+  if (!h->poisoned) st = check_device_status(h);
+  const int64_t m = h->m, n = h->n;
+  cudaError_t ce = cudaSuccess;
+  auto fetch = [&](void *src, double *dst, int64_t count) {
+    if (!dst || ce != cudaSuccess) return;
+    if (h->opt.precision == BDU_FP64) {
+      ce = cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream);
+    } else {
+      ce = launch_convert_f32_to_f64((const float *)src, h->scratch64, count, h->stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(dst, h->scratch64, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    }
+  };
+  fetch(h->Q, Q, m * m);
+  fetch(h->P, P, n * n);
+  if (d || e) {
+    std::vector<double> hb(band_doubles(m, n));
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(hb.data(), h->band, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce == cudaSuccess) {
+      BandPtrs hp = band_ptrs(hb.data(), m, n);
+      if (d) {
+        d[0] = hp.r1[1];
+        for (int64_t i = 2; i <= n; i++) d[i - 1] = hp.dg[2][i];
+      }
+      if (e && n > 1) {
+        e[0] = hp.r1[2];
+        for (int64_t i = 2; i <= n - 1; i++) e[i - 1] = hp.dg[3][i];
+      }
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read");
+  return st;
+}
+
+bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
+                              int64_t cap, int64_t *count) {
+  if (!h || !count || (side != 0 && side != 1)) return fail(h, BDU_EINVAL, "bdu_read_rotations: bad argument");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  cudaSetDevice(h->device);
+  cudaError_t ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_rotations");
+  const RotStream &st = h->st;
+  const size_t tc = (size_t)st.T * st.cap;
+  std::vector<int32_t> cnt(st.T + 1, 0);
+  std::vector<double> hc(tc), hs(tc);
+  std::vector<int32_t> ha(tc);
+  ce = cudaMemcpy(cnt.data(), side == 0 ? st.Ln : st.Rn, sizeof(int32_t) * st.T, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(hc.data(), side == 0 ? st.Lc : st.Rc, sizeof(double) * tc, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(hs.data(), side == 0 ? st.Ls : st.Rs, sizeof(double) * tc, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(ha.data(), side == 0 ? st.La : st.Ra, sizeof(int32_t) * tc, cudaMemcpyDeviceToHost);
+  int32_t ns = 0;
+  std::vector<double> sc, ss;
+  std::vector<int32_t> sa;
+  if (ce == cudaSuccess && side == 0 && h->m > h->n) {
+    ce = cudaMemcpy(&ns, st.Sn, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    sc.resize(ns + 1); ss.resize(ns + 1); sa.resize(ns + 1);
+    if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sc.data(), st.Sc, sizeof(double) * ns, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(ss.data(), st.Ss, sizeof(double) * ns, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sa.data(), st.Sa, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost);
+  }
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_rotations");
+  int64_t k = 0;
+  auto put = [&](double cc, double sv, int32_t aa) {
+    if (k < cap) {
+      if (c) c[k] = cc;
+      if (s) s[k] = sv;
+      if (a) a[k] = aa;
+    }
+    k++;
+  };
+  for (int32_t q = 0; q < ns; q++) put(sc[q], ss[q], sa[q]);
+  for (int t = 0; t < st.T; t++)
+    for (int32_t q = 0; q < cnt[t] && q < st.cap; q++) {
+      const size_t i = (size_t)t * st.cap + q;
+      put(hc[i], hs[i], ha[i]);
+    }
+  *count = k;
+  return BDU_OK;
+}
+
+bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
+  if (!h || !out) return fail(h, BDU_EINVAL, "bdu_stats: bad argument");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  cudaSetDevice(h->device);
+  unsigned long long c[16];
+  cudaError_t ce = cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_stats");
+  memset(out, 0, sizeof(*out));
+  out->updates = h->updates;
+  for (int q = 0; q < 4; q++) {
+    out->rot_left[q] = (int64_t)c[q];
+    out->rot_right[q] = (int64_t)c[4 + q];
+  }
+  out->chase_steps = (int64_t)c[8];
+  out->ortho_q = out->ortho_p = -1.0;
+  return BDU_OK;
+}
+
+}  // extern "C"

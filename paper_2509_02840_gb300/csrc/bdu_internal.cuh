@@ -1,0 +1,94 @@
+// Internal declarations of libbdu (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bdu.h"
+
+namespace bdu {
+
+// Device-side error bits written to the status word.
+enum : int {
+  ERR_BAND = 1,      // a write outside the stored band, or a nonzero where the schedule leaves 0
+  ERR_CAP = 2,       // a chase produced more rotations than its record slot holds
+  ERR_STEPS = 4,     // the chase engine exceeded its step budget (no progress)
+  ERR_SCHEDULE = 8,  // an op found a zero where the schedule guarantees a nonzero
+};
+
+// The working core M = band + u v^T of one rank-1 step, in global memory.
+// 1-based arrays.  dg[o+2][i] = M(i, i+o) for rows i >= 2 and offsets
+// o = -2..3; row 1 is kept densely in r1[j] = M(1, j), j = 1..n, in every
+// phase.  u has m+2 entries (the spike works on rows n+1..m), v has n+2.
+struct BandPtrs {
+  double *dg[6];
+  double *r1;
+  double *v;
+  double *u;
+};
+
+// Layout of the band buffer: 6 diagonals of length N+2, r1 (n+2), v (n+2),
+// u (m+2), all contiguous.
+inline int64_t band_doubles(int64_t m, int64_t n) {
+  int64_t N = (m > n) ? n + 1 : n;
+  return 6 * (N + 2) + 2 * (n + 2) + (m + 2);
+}
+inline BandPtrs band_ptrs(double *base, int64_t m, int64_t n) {
+  int64_t N = (m > n) ? n + 1 : n;
+  BandPtrs b;
+  for (int o = 0; o < 6; o++) b.dg[o] = base + o * (N + 2);
+  b.r1 = base + 6 * (N + 2);
+  b.v = b.r1 + (n + 2);
+  b.u = b.v + (n + 2);
+  return b;
+}
+
+// Rotation records of one rank-1 column, grouped by chase ("task") in the
+// order in which they must be applied.  Task t's left rotations are
+// Lc/Ls/La[t*cap + 0 .. Ln[t]-1] (pairs (a, a+1), 1-based), likewise right.
+// The spike chain (m > n) precedes all tasks on the left side.
+struct RotStream {
+  int T;    // number of tasks
+  int cap;  // record slots per task and side
+  double *Lc, *Ls, *Rc, *Rs;
+  int32_t *La, *Ra, *Ln, *Rn;
+  double *Sc, *Ss;
+  int32_t *Sa, *Sn;  // spike records; Sn[0] = count
+};
+
+// Number of chases of the schedule for an m x n problem.
+inline int num_tasks(int64_t m, int64_t n) {
+  int64_t N = (m > n) ? n + 1 : n;
+  int64_t p1 = N - 1;
+  int64_t p2 = n > 2 ? n - 2 : 0;
+  int64_t ilast = (N == n + 1) ? n : n - 1;
+  return (int)(p1 + p2 + 2 * ilast);
+}
+inline int task_cap(int64_t n) { return (int)(n / 2 + 4); }
+
+struct ChaseArgs {
+  int m, n;
+  BandPtrs band;      // global memory
+  double *Ux;         // later columns of U (rx of them, leading dimension m), or null
+  double *Vx;         // later columns of V (leading dimension n)
+  int rx;
+  RotStream st;
+  int *status;        // device error word (ERR_* bits)
+  unsigned long long *counters;  // [0..3] left by phase, [4..7] right by phase, [8] steps
+};
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s);
+
+cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, int ncol,
+                           const double *B, int64_t ldb, int r, double *U, int64_t ldu,
+                           cudaStream_t s);
+
+cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
+                         const RotStream &st, int side, bool with_spike, cudaStream_t s);
+
+cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, int64_t count,
+                                      cudaStream_t s);
+cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, int64_t count,
+                                      cudaStream_t s);
+
+}  // namespace bdu

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports what include/bdu.h declares,
+and rejects invalid arguments before touching a GPU (no GPU needed)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2509_02840_gb300 import bdu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return bdu.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = bdu.declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults(lib):
+    assert lib.bdu_version() >= 100
+    o = bdu.Options()
+    lib.bdu_default_options(ctypes.byref(o))
+    assert o.precision == bdu.FP64 and o.nb == 0 and o.device == 0
+    assert o.reorth_tol == pytest.approx(1e-6) and o.check_every == 10
+
+
+def _create(lib, m, n, Q, d, e, P):
+    h = ctypes.c_void_p()
+    dp = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    code = lib.bdu_create(ctypes.byref(h), m, n, dp(Q), dp(d), dp(e), dp(P), None)
+    return code, h
+
+
+def test_create_rejects_bad_arguments_without_a_gpu(lib):
+    I4 = np.eye(4); I3 = np.eye(3); d = np.ones(4); e = np.ones(3)
+    code, h = _create(lib, 3, 4, I3, d, e, I4)          # m < n
+    assert code == 1 and not h.value
+    assert b"m >= n" in lib.bdu_last_error(None)
+    code, _ = _create(lib, 4, 0, I4, d, e, I4)          # n < 1
+    assert code == 1
+    code, _ = _create(lib, 4, 4, None, d, e, I4)        # NULL Q
+    assert code == 1
+    code, _ = _create(lib, 4, 4, I4, d, None, I4)       # NULL e with n > 1
+    assert code == 1
+    bad = I4.copy(); bad[1, 2] = np.nan
+    code, _ = _create(lib, 4, 4, bad, d, e, I4)         # non-finite
+    assert code == 1 and b"non-finite" in lib.bdu_last_error(None)
+    dinf = d.copy(); dinf[0] = np.inf
+    code, _ = _create(lib, 4, 4, I4, dinf, e, I4)
+    assert code == 1
+
+
+def test_null_handle_calls_are_rejected(lib):
+    assert lib.bdu_update(None, None, None, 1) == 1
+    assert lib.bdu_sync(None) == 1
+    assert lib.bdu_read(None, None, None, None, None) == 1
+    lib.bdu_destroy(None)  # accepted
+    assert lib.bdu_last_error(None) is not None
