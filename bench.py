@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark: rank-1 bidiagonal updates per second at m = n = 4096.
+
+Workload (the recommender stream): A = Q Bd P^T with Q, P products of 8
+Householder reflectors, d ~ U(1, 10), e ~ N(0, 1); each step is one rank-1
+"set item column" update A + b e_j^T with b a ratings column (2% of the rows,
+values 1..5) and j = h mod n.  A step runs the whole hot path: projection,
+FP64 rotation generation and bulge chasing, and the application of the
+rotations to Q and P.
+
+The headline form is the mixed one (Q, P in FP32; generation and Bd in FP64);
+the plain FP64 form is measured on the same workload and reported beside it
+with both forms' residuals.
+
+Timing: per-step CUDA events on the library's stream (the stream the kernels
+run on) after W warm-up steps, with an L2 flush (a 512 MiB write) before every
+timed step outside the events; `value` is device-resident throughput (B, C
+already in HBM, bdu_update_dev), `e2e` goes through bdu_update with pinned
+host buffers and reads the updated bidiagonal back every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+With N > 1 (launched by torchrun) every rank updates its own factorization:
+the path does not shard, so ranks are independent replicas (weak scaling).
+The reference arm times the CPU oracle (the library's plain FP64 reference
+implementation) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rank-1 updates/s at m=n=4096 (mixed form; FP64 form beside it)"
+UNIT = "updates/s"
+M = N = 4096
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--oracle-rows", type=int, default=256,
+                    help="rows of Q and P the CPU oracle applies in its bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=4096,
+                    help="m = n of the workload (4096 is the benchmark; smaller sizes are for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="mixed form only: no FP64 form, e2e or CPU baseline (profiling runs)")
+    a = ap.parse_args()
+    global M, N
+    M = N = a.size
+    return a
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+def workload(rank, steps):
+    from paper_2509_02840_gb300 import inputs as I
+    Q, d, e, P = I.factorization(M, N, config=1, which=rank)
+    ups = [I.recommender_update(M, N, h + 1000 * rank, config=1) for h in range(steps)]
+    return Q, d, e, P, ups
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP32 FMA peak from unit counts and the maximum clock: 152 SMs x 128 FP32
+# lanes x 2 flops x 2070 MHz.  FP64: 152 SMs x 2 FP64 FMA per clock x 2 flops
+# x 2070 MHz (GB300's FP64 rate).
+ALU_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+ALU_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Algorithmic work per rotation: 10 multiplications and 10 additions on the band
+# (Sec. 3.4), plus the rotation itself (2 multiplications, 1 addition, 1 square
+# root, 2 divisions counted as one flop each).
+CHASE_FLOPS_PER_ROTATION = 26
+
+
+def roofline(st, precision, rotations_per_update, launches_per_update):
+    """Roofline object of the dominant kernel group of one update."""
+    ms = {"chase": st["ms_chase"], "apply": st["ms_apply_q"] + st["ms_apply_p"], "project": st["ms_project"]}
+    nup = max(st["timed_updates"], 1)
+    dom = max(ms, key=ms.get)
+    if dom == "chase":
+        per_launch_ms = ms["chase"] / nup
+        flops = CHASE_FLOPS_PER_ROTATION * rotations_per_update
+        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        return {"kernel": "k_chase (FP64 rotation generation + bulge chase)", "bound": "alu",
+                "achieved": ach, "peak": ALU_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP64_TFLOPS,
+                "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
+                "share": ms["chase"] / sum(ms.values())}
+    # apply: algorithmic bytes = one read + one write of Q and P per rank-1 column
+    es = 8 if precision == 0 else 4
+    per_launch_ms = ms["apply"] / max(st["apply_launches"], 1)
+    bytes_per_launch = (2 * M * M * es + 2 * N * N * es) / 2
+    flops_per_launch = 6 * rotations_per_update / 2 * M
+    if precision == 1:
+        ach = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+        return {"kernel": "k_apply_slab (FP32 column-pair rotations)", "bound": "alu", "achieved": ach,
+                "peak": ALU_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP32_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "algorithmic_bytes": bytes_per_launch, "share": ms["apply"] / sum(ms.values())}
+    ach = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    return {"kernel": "k_apply_slab (FP64 column-pair rotations)", "bound": "alu", "achieved": ach,
+            "peak": ALU_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP64_TFLOPS, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
+            "share": ms["apply"] / sum(ms.values())}
+
+
+def residual(F, A0_parts, ups):
+    """||A+ - Q Bd P^T||_F / ||A+||_F with A+ accumulated in FP64."""
+    import numpy as np
+    Q0, d0, e0, P0 = A0_parts
+    A = Q0 @ (np.diag(d0) + np.diag(e0, 1)) @ P0.T
+    for B, C in ups:
+        A += B @ C.T
+    Q, d, e, P = F.read()
+    R = Q @ (np.diag(d) + np.diag(e, 1)) @ P.T
+    return float(np.linalg.norm(A - R) / np.linalg.norm(A))
+
+
+# --------------------------------------------------------------------------
+# CPU oracle: a bounded sample of the same workload
+# --------------------------------------------------------------------------
+def oracle_sample(rows_sample, updates=1):
+    """Full rotation generation of one update plus the apply for `rows_sample`
+    rows of Q and of P (rows are independent), extrapolated to all rows."""
+    import numpy as np
+    import oracle as O
+    Q, d, e, P, ups = workload(0, updates)
+    secs = []
+    for B, C in ups:
+        t0 = time.perf_counter()
+        U, V = O.project(Q, P, B, C)
+        d2, e2, L, R, _ = O.generate(M, N, d, e, U, V)
+        t1 = time.perf_counter()
+        rows = np.arange(rows_sample)
+        O.apply_rows(Q, rows, L)
+        O.apply_rows(P, rows, R)
+        t2 = time.perf_counter()
+        secs.append((t1 - t0) + (t2 - t1) * (M / rows_sample))
+        d, e = d2, e2
+    per = statistics.mean(secs)
+    return {"value": 1.0 / per, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"{updates} full m=n=4096 recommender update(s): projection and all "
+                       f"~25M rotations generated; rotations applied to {rows_sample} of 4096 rows "
+                       f"of Q and of P and extrapolated linearly (rows are independent)"),
+            "seconds_per_update": per}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = [oracle_sample(args.oracle_rows, 1)["seconds_per_update"] for _ in range(args.warmup)]
+    t = [oracle_sample(args.oracle_rows, 1)["seconds_per_update"] for _ in range(args.steps)]
+    import oracle as O
+    per = statistics.mean(t)
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / per, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "recommender stream m=n=4096, rank-1 set-item-column updates",
+                                            "m": M, "n": N, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": 1.0 / per, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"per step: one full update's generation + apply on {args.oracle_rows} rows of Q and P, extrapolated"},
+            "e2e": {"value": 1.0 / per, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2509_02840_gb300 import bdu
+    bdu.load()
+    K, W = args.steps, args.warmup
+    Q, d, e, P, ups = workload(rank, W + K + args.e2e_steps + 1 + args.fp64_steps)
+    stream = torch.cuda.Stream()
+    dev_ups = []
+    with torch.cuda.stream(stream):
+        for B, C in ups:
+            dev_ups.append((torch.from_numpy(np.asfortranarray(B).reshape(-1, order="F")).cuda(),
+                            torch.from_numpy(np.asfortranarray(C).reshape(-1, order="F")).cuda()))
+    stream.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(F, seq):
+        times = []
+        for Bd, Cd in seq:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                F.update_dev(Bd.data_ptr(), Cd.data_ptr(), 1)
+                ev1.record(stream)
+            times.append((ev0, ev1))
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    # ---- mixed form (headline) -------------------------------------------
+    Fm = bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, stream=stream.cuda_stream, device=local)
+    timed_steps(Fm, dev_ups[:W])
+    st0 = Fm.stats()
+    Fm.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms = timed_steps(Fm, dev_ups[W:W + K])
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = Fm.stats()
+    rot_per_update = (sum(st["rot_left"]) + sum(st["rot_right"]) - sum(st0["rot_left"]) - sum(st0["rot_right"])) / K
+    launches = (st["launches"] - st0["launches"])
+    roof = roofline(st, 1, rot_per_update, launches / K)
+    res_mixed = residual(Fm, (Q, d, e, P), ups[:W + K])
+
+    if args.quick:
+        Fm.close()
+        line = {"metric": METRIC, "value": world * K / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"recommender stream m=n={M} (quick profiling run)", "m": M, "n": N},
+                "roofline": roof, "clocks": clk, "gpu_launches": launches,
+                "kernel_ms_per_update": {k: st["ms_" + k] / max(st["timed_updates"], 1)
+                                         for k in ("project", "chase", "apply_q", "apply_p")}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+
+    # ---- e2e through the host-pointer ABI (pinned buffers, result read back)
+    e2e_seq = ups[W + K:W + K + args.e2e_steps]
+    pinned = []
+    for B, C in e2e_seq:
+        pb = torch.from_numpy(np.asfortranarray(B).reshape(-1, order="F")).pin_memory()
+        pc = torch.from_numpy(np.asfortranarray(C).reshape(-1, order="F")).pin_memory()
+        pinned.append((pb, pc))
+    Fm.set_timing(False)
+    dbuf = np.zeros(N); ebuf = np.zeros(N)
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    Fm.sync()
+    t0 = time.perf_counter()
+    for pb, pc in pinned:
+        code = Fm._L.bdu_update(Fm._h, ctypes.cast(pb.data_ptr(), dp), ctypes.cast(pc.data_ptr(), dp), 1)
+        bdu._check(Fm._L, Fm._h, code)
+        code = Fm._L.bdu_read(Fm._h, None, dbuf.ctypes.data_as(dp), ebuf.ctypes.data_as(dp), None)
+        bdu._check(Fm._L, Fm._h, code)
+    e2e_s = (time.perf_counter() - t0) / len(pinned)
+    Fm.close()
+
+    # ---- plain FP64 form on the same workload ------------------------------
+    F64 = bdu.Factorization(Q, d, e, P, precision=bdu.FP64, stream=stream.cuda_stream, device=local)
+    timed_steps(F64, dev_ups[:1])
+    ms64 = timed_steps(F64, dev_ups[1:1 + args.fp64_steps])
+    res64 = residual(F64, (Q, d, e, P), ups[:1 + args.fp64_steps])
+    F64.close()
+
+    if dist:
+        dist.barrier()
+    value = world * K / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (Q, P storage and apply) + f64 (projection, rotations, Bd)",
+        "data": "synthetic",
+        "config": {"workload": f"recommender stream m=n={M}, rank-1 set-item-column updates (2% ratings column, c=e_j)",
+                   "m": M, "n": N, "rank": 1, "form": "mixed", "parallelism": f"replicas x{world}",
+                   "l2": "flushed before every timed step (512 MiB write)"},
+        "latency_ms": {"p50": statistics.median(ms), "p99": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
+                       "max": max(ms)},
+        "fp64_form": {"value": 1e3 / statistics.mean(ms64), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
+                      "steps": len(ms64), "relative_residual": res64},
+        "mixed_relative_residual": res_mixed,
+        "mixed_vs_fp64_speedup": (1e3 / statistics.mean(ms)) / (1e3 / statistics.mean(ms64)),
+        "kernel_ms_per_update": {"project": st["ms_project"] / max(st["timed_updates"], 1),
+                                 "chase": st["ms_chase"] / max(st["timed_updates"], 1),
+                                 "apply_q": st["ms_apply_q"] / max(st["timed_updates"], 1),
+                                 "apply_p": st["ms_apply_p"] / max(st["timed_updates"], 1)},
+        "rotations_per_update": rot_per_update,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (M + N), "d2h_bytes_per_step": 8 * (2 * N - 1),
+                "path": "bdu_update (pinned host B, C) + bdu_read of d, e per step, wall clock"},
+        "gpu_launches": launches,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args.oracle_rows, 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,13 @@ typedef struct {
   int64_t chase_steps;      /* synchronous steps of the bulge-chase engine */
   int64_t reorth_q, reorth_p; /* re-orthogonalizations performed */
   double ortho_q, ortho_p;  /* last estimate of ||Q^T Q - I||_2, ||P^T P - I||_2 (-1 = none) */
+  int64_t launches;         /* CUDA kernels launched by the library so far */
+  int64_t timed_updates;    /* updates covered by the timings below (see bdu_set_timing) */
+  double ms_project;        /* device time of the projection kernels (K1) */
+  double ms_chase;          /* device time of rotation generation / bulge chasing (K2) */
+  double ms_apply_q;        /* device time of the rotation apply to Q (K3) */
+  double ms_apply_p;        /* device time of the rotation apply to P (K3) */
+  int64_t apply_launches;   /* apply-kernel launches covered by ms_apply_q + ms_apply_p */
 } bdu_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -123,6 +130,11 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
 
 /* Statistics since creation.  Synchronizes. */
 bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out);
+
+/* Enables (on != 0) or disables per-kernel timing with CUDA events recorded
+ * on the handle's stream around each kernel group; the accumulated device
+ * times are reported by bdu_stats.  Off by default. */
+bdu_status bdu_set_timing(bdu_handle h, int on);
 
 /* Releases all device memory of the handle.  NULL is accepted. */
 void bdu_destroy(bdu_handle h);

@@ -33,7 +33,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("updates", ctypes.c_int64), ("rot_left", ctypes.c_int64 * 4),
                 ("rot_right", ctypes.c_int64 * 4), ("chase_steps", ctypes.c_int64),
                 ("reorth_q", ctypes.c_int64), ("reorth_p", ctypes.c_int64),
-                ("ortho_q", ctypes.c_double), ("ortho_p", ctypes.c_double)]
+                ("ortho_q", ctypes.c_double), ("ortho_p", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("timed_updates", ctypes.c_int64),
+                ("ms_project", ctypes.c_double), ("ms_chase", ctypes.c_double),
+                ("ms_apply_q", ctypes.c_double), ("ms_apply_p", ctypes.c_double),
+                ("apply_launches", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
@@ -76,6 +80,8 @@ def load(build_if_missing: bool = True):
     L.bdu_read_rotations.restype = ctypes.c_int
     L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
     L.bdu_stats.restype = ctypes.c_int
+    L.bdu_set_timing.argtypes = [H, ctypes.c_int]
+    L.bdu_set_timing.restype = ctypes.c_int
     L.bdu_destroy.argtypes = [H]
     L.bdu_destroy.restype = None
     L.bdu_last_error.argtypes = [H]
@@ -225,4 +231,10 @@ class Factorization:
         _check(self._L, self._h, self._L.bdu_stats(self._h, ctypes.byref(st)))
         return {"updates": st.updates, "rot_left": list(st.rot_left), "rot_right": list(st.rot_right),
                 "chase_steps": st.chase_steps, "reorth_q": st.reorth_q, "reorth_p": st.reorth_p,
-                "ortho_q": st.ortho_q, "ortho_p": st.ortho_p}
+                "ortho_q": st.ortho_q, "ortho_p": st.ortho_p, "launches": st.launches,
+                "timed_updates": st.timed_updates, "ms_project": st.ms_project,
+                "ms_chase": st.ms_chase, "ms_apply_q": st.ms_apply_q,
+                "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches}
+
+    def set_timing(self, on=True):
+        _check(self._L, self._h, self._L.bdu_set_timing(self._h, 1 if on else 0))

@@ -75,6 +75,13 @@ struct bdu_ctx {
   double *scratch64;  // for conversions in read (mixed form)
   // bookkeeping
   int64_t updates;
+  int64_t launches;
+  bool timing;
+  // pending (start, stop, which) event triples; which: 0 project, 1 chase, 2 apply Q, 3 apply P
+  struct Ev { cudaEvent_t a, b; int which; };
+  std::vector<Ev> pending;
+  double ms[4];
+  int64_t timed_updates, apply_launches;
   bool poisoned;
   std::atomic<int> busy;
   char err[512];
@@ -154,6 +161,39 @@ bdu_status ensure_rank_workspace(bdu_ctx *h, int64_t r) {
   return BDU_OK;
 }
 
+// Kernel-group timing: an event pair around each group, resolved at sync.
+struct Timer {
+  bdu_ctx *h;
+  int which;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer(bdu_ctx *hh, int w) : h(hh), which(w) {
+    if (!h->timing) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecord(a, h->stream);
+  }
+  ~Timer() {
+    if (!a) return;
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({a, b, which});
+  }
+};
+
+void resolve_timers(bdu_ctx *h) {
+  for (auto &ev : h->pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(ev.b) == cudaSuccess && cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess)
+      h->ms[ev.which] += t;
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  cudaGetLastError();
+  h->pending.clear();
+}
+
 bdu_status check_device_status(bdu_ctx *h) {
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -169,11 +209,19 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   const int m = (int)h->m, n = (int)h->n;
   cudaStream_t s = h->stream;
   cudaError_t e;
+  if (h->timing) {
+    h->timed_updates += r;
+    if (h->pending.size() > 4096) resolve_timers(h);
+  }
   // K1: U = Q^T B, V = P^T C with the current factors
-  e = launch_project_nz(h->opt.precision, h->Q, m, m, m, dB, m, (int)r, h->U, m, h->nzB, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "projection of B");
-  e = launch_project_nz(h->opt.precision, h->P, n, n, n, dC, n, (int)r, h->V, n, h->nzC, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "projection of C");
+  {
+    Timer tm(h, 0);
+    e = launch_project_nz(h->opt.precision, h->Q, m, m, m, dB, m, (int)r, h->U, m, h->nzB, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "projection of B");
+    e = launch_project_nz(h->opt.precision, h->P, n, n, n, dC, n, (int)r, h->V, n, h->nzC, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "projection of C");
+    h->launches += 4;
+  }
   BandPtrs bp = band_ptrs(h->band, m, n);
   for (int64_t k = 0; k < r; k++) {
     // u = U(:,k), v = V(:,k) (1-based in the band buffer)
@@ -189,13 +237,24 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
     a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
     a.st = h->st; a.status = h->status; a.counters = h->counters;
-    e = launch_chase(a, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+    {
+      Timer tm(h, 1);
+      e = launch_chase(a, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+    }
     // K3: Q <- Q prod G^T, P <- P prod H
-    e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
-    e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
+    {
+      Timer tm(h, 2);
+      e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
+    }
+    {
+      Timer tm(h, 3);
+      e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
+    }
+    h->launches += 3;
+    if (h->timing) h->apply_launches += 2;
     h->updates++;
   }
   return BDU_OK;
@@ -229,6 +288,7 @@ void bdu_destroy(bdu_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  resolve_timers(h);
   for (void *p : h->blocks) h->al.put(p);
   h->blocks.clear();
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -494,6 +554,23 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   }
   out->chase_steps = (int64_t)c[8];
   out->ortho_q = out->ortho_p = -1.0;
+  resolve_timers(h);
+  out->launches = h->launches;
+  out->timed_updates = h->timed_updates;
+  out->ms_project = h->ms[0];
+  out->ms_chase = h->ms[1];
+  out->ms_apply_q = h->ms[2];
+  out->ms_apply_p = h->ms[3];
+  out->apply_launches = h->apply_launches;
+  return BDU_OK;
+}
+
+bdu_status bdu_set_timing(bdu_handle h, int on) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  cudaSetDevice(h->device);
+  h->timing = on != 0;
   return BDU_OK;
 }
 
