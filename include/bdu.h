@@ -152,6 +152,35 @@ typedef void *(*bdu_alloc_fn)(size_t bytes, int device, void *ctx);
 typedef void (*bdu_free_fn)(void *ptr, int device, void *ctx);
 void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx);
 
+/* Allocation-free FP64 rank-1 update of a factorization held in the caller's
+ * own device memory.  The paper has no counterpart; this entry point exists
+ * for callers that cannot allocate device memory: a host framework that
+ * reserves the whole GPU for its own allocator and forbids foreign cudaMalloc
+ * calls, a latency-critical loop in which an allocation (which may
+ * synchronize the device) is not acceptable, or an embedding in which the
+ * library may not own memory.
+ *
+ * All pointers are device pointers on the current device, FP64, column-major:
+ * Q m*m, d n, e n-1 (may be NULL when n == 1), P n*n are read and replaced by
+ * the factorization of A + b c^T; b (m) and c (n) are read.  The result is
+ * bit-identical to bdu_update on a handle with the same data.  stream is a
+ * cudaStream_t (NULL = the legacy default stream); the call returns after
+ * the update has completed on it.
+ *
+ * Limits: m <= 1024 and n <= 256 (BDU_EINVAL beyond them, before any device
+ * work), as well as m >= n >= 1.  Every intermediate lives in one fixed
+ * __device__ array of the library (about 5.5 MB, held by every GPU that loads
+ * the library until the process exits); no cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current, so
+ * that first call should come before any stream capture.  All calls share the
+ * array and each call clears what must start at zero; calls that overlap on
+ * the GPU (from several host threads or unordered streams) race on it.
+ * Errors: BDU_EINVAL, BDU_ECUDA, BDU_ETIMEOUT, BDU_EINTERNAL (status codes
+ * only; bdu_last_error is not updated). */
+bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, double *d, double *e,
+                                    double *P, const double *b, const double *c, void *stream);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bdu_version(void);
 
