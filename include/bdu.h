@@ -69,6 +69,8 @@ typedef struct {
   int check_every;    /* BDU_MIXED: updates between orthogonality estimates (default 10) */
   void *cuda_stream;  /* cudaStream_t used for all work; NULL = library-owned stream */
   int device;         /* CUDA device ordinal (default 0) */
+  int engine;         /* bulge-chase engine: 0 = by size (default), 1 = one thread block,
+                         2 = a 16-block cluster; all give identical results */
 } bdu_options;
 
 typedef struct {

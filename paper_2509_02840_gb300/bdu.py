@@ -26,7 +26,8 @@ class BduError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -149,7 +150,7 @@ class Factorization:
     """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
-                 check_every=None):
+                 check_every=None, engine=0):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -159,6 +160,7 @@ class Factorization:
         L.bdu_default_options(ctypes.byref(opt))
         opt.precision = int(precision)
         opt.device = int(device)
+        opt.engine = int(engine)
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:

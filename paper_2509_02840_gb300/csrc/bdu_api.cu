@@ -237,6 +237,8 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
     a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
     a.st = h->st; a.status = h->status; a.counters = h->counters;
+    a.fast = (h->opt.precision == BDU_MIXED) ? 1 : 0;
+    a.engine = h->opt.engine;
     {
       Timer tm(h, 1);
       e = launch_chase(a, s);
@@ -272,6 +274,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->check_every = 10;
   opt->cuda_stream = nullptr;
   opt->device = 0;
+  opt->engine = 0;
 }
 
 int bdu_version(void) { return 100; }
@@ -307,6 +310,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   if (opt) o = *opt;
   if (o.precision != BDU_FP64 && o.precision != BDU_MIXED)
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown precision %d", o.precision);
+  if (o.engine < 0 || o.engine > 2)
+    return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
     return fail(nullptr, BDU_EINVAL, "bdu_create: non-finite value in Q, d, e or P");
 
@@ -355,10 +360,16 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->st.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
   h->status = (int *)dev_alloc(h, sizeof(int) * 4);
   h->counters = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * 16);
-  if (o.precision == BDU_MIXED) h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
+  if (o.precision == BDU_MIXED) {
+    h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
+    h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
+    h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
+    h->st.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
+  }
   bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
             h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
-            h->status && h->counters && (o.precision == BDU_FP64 || h->scratch64);
+            h->status && h->counters &&
+            (o.precision == BDU_FP64 || (h->scratch64 && h->st.Lf && h->st.Rf && h->st.Sf));
   if (!ok) {
     fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (m=%lld n=%lld)", (long long)m, (long long)n);
     bdu_destroy(h);

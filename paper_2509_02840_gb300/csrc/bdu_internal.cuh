@@ -53,6 +53,8 @@ struct RotStream {
   int32_t *La, *Ra, *Ln, *Rn;
   double *Sc, *Ss;
   int32_t *Sa, *Sn;  // spike records; Sn[0] = count
+  // FP32 copies (c, s) of the records for the mixed form; null in the FP64 form
+  float2 *Lf, *Rf, *Sf;
 };
 
 // Number of chases of the schedule for an m x n problem.
@@ -74,6 +76,8 @@ struct ChaseArgs {
   RotStream st;
   int *status;        // device error word (ERR_* bits)
   unsigned long long *counters;  // [0..3] left by phase, [4..7] right by phase, [8] steps
+  int fast;           // 1: fused multiply-add / Newton rotation arithmetic (mixed form)
+  int engine;         // 0: by size, 1: one CTA, 2: thread-block cluster
 };
 
 // Launchers (return the launch error, if any).

@@ -5,13 +5,23 @@
 // starts with one rotation and pushes the bulge it creates down the band.
 // Chases are generated in a fixed order (the schedule below) and every chase
 // moves monotonically down the band, so chase t may run concurrently with
-// chase t-1 as long as it stays a few positions behind it.  The engine
-// assigns one chase per thread and advances all runnable chases by one
-// rotation per synchronous step; a chase runs only when the nearest earlier
-// unfinished chase is at least D positions ahead (D = 3 between phase-1
-// chases, 4 otherwise).  This keeps every band cell's read/write order
-// identical to the sequential algorithm, so the result is bit-identical to a
-// one-rotation-at-a-time execution.
+// chase t-1 as long as it stays a few positions behind it.  The engine gives
+// each chase to one thread and advances all runnable chases by one rotation
+// per synchronous step; a chase runs only when the nearest earlier unfinished
+// chase is at least D positions ahead (D = 3 between phase-1 chases, 2 from
+// the last phase-2 chase to a phase-3 one, 4 otherwise).  This keeps every
+// band cell's read/write order identical to the sequential algorithm, so the
+// result equals a one-rotation-at-a-time execution.
+//
+// Two engines share the chase logic:
+//   * one CTA (small n): the band sits in that CTA's shared memory when it
+//     fits, else in global memory; steps are separated by __syncthreads;
+//   * a thread-block cluster of 16 CTAs (large n): the band's rows are
+//     partitioned over the CTAs' shared memories and reached through
+//     distributed shared memory; chases are dealt round-robin to the CTAs, and
+//     steps are separated by cluster barriers.  This multiplies the FP64
+//     throughput available to the chases (GB300 issues about two FP64 FMAs
+//     per SM per clock).
 //
 // Schedule (1-based; N = n+1 if m > n else n):
 //   spike:    j = m..n+2: left (j-1, j) zeroing u(j)             [one thread]
@@ -28,151 +38,158 @@
 //   chase_lower(k): left (k+1, k+2) zeroing M(k+2, k); right (k+3, k+4)
 //             zeroing M(k+1, k+4); k += 3, while the bulge exists.
 //
-// Arithmetic: every multiply, add, divide and square root is a separately
-// rounded IEEE operation (__dmul_rn, __dadd_rn, __ddiv_rn, __dsqrt_rn), never
-// a fused multiply-add, so each value is fully determined by its inputs.
+// Arithmetic.  Exact (FP64 form): every multiply, add, divide and square root
+// is a separately rounded IEEE operation (__dmul_rn, __dadd_rn, __ddiv_rn,
+// __dsqrt_rn), never a fused multiply-add, so each value is fully determined
+// by its inputs.  Fast (mixed form, where Q and P are FP32 anyway): fused
+// multiply-adds, and 1/sqrt(f^2 + g^2) from an FP32 seed refined by one
+// third-order Newton step in FP64 (error well below an FP64 ulp), which
+// avoids the long-latency FP64 division and square-root sequences.
 #include <climits>
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "bdu_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace bdu {
 namespace {
 
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 256;
+// Stand-ins for band entries outside the stored diagonals: g_zero_sink[0]
+// always reads 0; g_zero_sink[1] is the address writes to such entries go to
+// (they are dropped, and a nonzero one is reported).  Never written.
+__device__ double g_zero_sink[2];  // the fully inlined chase code holds ~250 registers per thread
+constexpr int kMaxCluster = 16;
 
 enum Kind : int { P1 = 0, P2 = 1, P3B = 2, P3C = 3 };
-// states
 enum : int { S_L0 = 0, S_R1 = 1, S_L1 = 2, S_A = 3, S_B = 4, S_C = 5, S_CL = 6, S_CR = 7, S_P2 = 8 };
 
+// ----------------------------------------------------------------------------
+// rotation arithmetic
+// ----------------------------------------------------------------------------
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+// x != 0 and |x| compared through the bit pattern, on the integer pipes
+__device__ __forceinline__ bool nz(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ unsigned long long absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 
 // Rotation generator (Eqs. giv, giv1, zero handling of Sec. 3.4):
-// [c s; -s c][f; g] = [r; 0].  Returns false when g == 0 (no rotation).
-// r = sign(f) hypot(f, g), evaluated with power-of-two safe scaling.
-__device__ __forceinline__ bool rotg(double f, double g, double &c, double &s, double &r) {
-  if (g == 0.0) return false;
-  if (f == 0.0) {
-    c = 0.0; s = 1.0; r = g;
-    return true;
-  }
-  double af = fabs(f), ag = fabs(g);
-  double amax = af > ag ? af : ag;
-  double sigma = 1.0;
-  if (amax > 0x1p500) sigma = 0x1p-600;
-  else if (amax < 0x1p-500) sigma = 0x1p600;
-  double fs = mul(f, sigma), gs = mul(g, sigma);
-  double h = __dsqrt_rn(add(mul(fs, fs), mul(gs, gs)));
-  double rs = copysign(h, f);
-  c = __ddiv_rn(fs, rs);
-  s = __ddiv_rn(gs, rs);
-  r = __ddiv_rn(rs, sigma);
-  return true;
+// [c s; -s c][f; g] = [r; 0], c >= 0, r = sign(f) hypot(f, g).  Returns false
+// when g == 0 (no rotation); f == 0 gives c = 0, s = 1, r = g.  hypot uses
+// power-of-two safe scaling.  Written without branches on the common path so
+// that the lanes of a warp share its (long-latency) FP64 instructions.
+__device__ __forceinline__ bool rotg_exact(double f, double g, double &c, double &s, double &r) {
+  const unsigned long long bf = absbits(f), bg = absbits(g);
+  const unsigned long long bm = bf > bg ? bf : bg;  // |x| order = bit-pattern order
+  const double sigma = bm > 0x5F30000000000000ULL ? 0x1p-600 : (bm < 0x20B0000000000000ULL ? 0x1p600 : 1.0);
+  const double fs = mul(f, sigma), gs = mul(g, sigma);
+  const double h = __dsqrt_rn(add(mul(fs, fs), mul(gs, gs)));
+  const double rs = copysign(h, f);
+  const bool fz = bf == 0;
+  const double den = fz ? 1.0 : rs;
+  c = fz ? 0.0 : __ddiv_rn(fs, den);
+  s = fz ? 1.0 : __ddiv_rn(gs, den);
+  r = fz ? g : __ddiv_rn(rs, sigma);
+  return bg != 0;
 }
 
-struct Core {
-  double *dg[6];
-  double *r1, *u, *v;
-  int N, n;
-  int *err;
-  double *Ux, *Vx;
-  int rx, m;
+// Same rotation from y ~ 1/sqrt(f^2 + g^2): both inputs are scaled exactly by
+// the power of two that brings the larger into [0.5, 1), so q = f^2 + g^2 lies
+// in [0.25, 2) and fits FP32; y0 = rsqrtf(q) (about 23 bits) is refined by
+// y = y0 (1 + e/2 + 3e^2/8) with e = 1 - q y0^2 (third-order Newton step).
+// Inputs outside [2^-1021, 2^1022) take the exact path.
+__device__ __forceinline__ bool rotg_fast(double f, double g, double &c, double &s, double &r) {
+  const unsigned long long bf = absbits(f), bg = absbits(g);
+  const int ex = (int)((bf > bg ? bf : bg) >> 52);
+  if ((ex < 2 || ex > 2044) && bg != 0) return rotg_exact(f, g, c, s, r);
+  const int exs = ex < 2 ? 2 : ex;  // keeps sigma finite when f = g = 0
+  const double sigma = __longlong_as_double((long long)(2045 - exs) << 52);  // 2^(1022-ex)
+  const double inv = __longlong_as_double((long long)(exs + 1) << 52);       // 1/sigma
+  const double fs = f * sigma, gs = g * sigma;
+  const double q = fma(fs, fs, gs * gs);
+  double y = (double)rsqrtf((float)q);
+  const double e = fma(-(q * y), y, 1.0);
+  y = fma(y * e, fma(0.375, e, 0.5), y);
+  const bool fz = bf == 0;
+  const double fa = __longlong_as_double((long long)absbits(fs));                 // |fs|
+  const double gsg = __longlong_as_double(__double_as_longlong(gs) ^
+                                          (__double_as_longlong(f) & (long long)0x8000000000000000ULL));  // sign(f) gs
+  const double qy = q * y;
+  c = fz ? 0.0 : fa * y;
+  s = fz ? 1.0 : gsg * y;
+  r = fz ? g : __longlong_as_double(__double_as_longlong(qy * inv) ^
+                                    (__double_as_longlong(f) & (long long)0x8000000000000000ULL));
+  return bg != 0;
+}
 
-  __device__ __forceinline__ bool inband(int i, int j) const {
-    if (i < 1 || i > N || j < 1 || j > n) return false;
-    if (i == 1) return true;
-    int o = j - i;
-    return o >= -2 && o <= 3;
+template <bool FAST> struct Arith;
+template <> struct Arith<false> {
+  static __device__ __forceinline__ bool rot(double f, double g, double &c, double &s, double &r) {
+    return rotg_exact(f, g, c, s, r);
   }
-  __device__ __forceinline__ double get(int i, int j) const {
-    if (!inband(i, j)) return 0.0;
-    return (i == 1) ? r1[j] : dg[j - i + 2][i];
+  static __device__ __forceinline__ double px(double c, double s, double x, double y) { return add(mul(c, x), mul(s, y)); }
+  static __device__ __forceinline__ double py(double c, double s, double x, double y) { return add(mul(-s, x), mul(c, y)); }
+};
+template <> struct Arith<true> {
+  static __device__ __forceinline__ bool rot(double f, double g, double &c, double &s, double &r) {
+    return rotg_fast(f, g, c, s, r);
   }
-  __device__ __forceinline__ void put(int i, int j, double x) {
-    if (!inband(i, j)) {
-      if (x != 0.0) atomicOr(err, ERR_BAND);
-      return;
-    }
-    if (i == 1) r1[j] = x;
-    else dg[j - i + 2][i] = x;
+  static __device__ __forceinline__ double px(double c, double s, double x, double y) { return fma(c, x, s * y); }
+  static __device__ __forceinline__ double py(double c, double s, double x, double y) { return fma(c, y, -(s * x)); }
+};
+
+// ----------------------------------------------------------------------------
+// cell stores.  Band cells: dg[j-i+2] at row i >= 2 (offsets -2..3); row 1 is
+// dense (r1[j]); u(1..N), v(1..n).
+// ----------------------------------------------------------------------------
+struct LocalStore {
+  double *dg0;  // diagonal o starts at dg0 + (o+2) * ld
+  int ld;
+  double *r1, *u, *v;
+  __device__ __forceinline__ double *cell(int i, int j) const {
+    return (i == 1) ? r1 + j : dg0 + (size_t)(j - i + 2) * ld + i;
   }
+  static __device__ __forceinline__ double load(const double *p) { return *p; }
+  __device__ __forceinline__ double *uptr(int i) const { return u + i; }
+  __device__ __forceinline__ double *vptr(int j) const { return v + j; }
+};
+
+// The band in global memory, shared by the CTAs of a cluster.  The ~3 MB of
+// band, row 1, u and v stay in L2; loads bypass L1 (ld.global.cg) so that each
+// step sees the writes other SMs made in earlier steps, which the cluster
+// barrier between steps orders.
+struct GlobalStore {
+  double *dg0;  // diagonal o starts at dg0 + (o+2) * ld
+  int ld;
+  double *r1, *u, *v;
+  __device__ __forceinline__ double *cell(int i, int j) const {
+    return (i == 1) ? r1 + j : dg0 + (size_t)(j - i + 2) * ld + i;
+  }
+  __device__ __forceinline__ double *uptr(int i) const { return u + i; }
+  __device__ __forceinline__ double *vptr(int j) const { return v + j; }
+  static __device__ __forceinline__ double load(const double *p) { return __ldcg(p); }
 };
 
 struct Rec {
   double *c, *s;
   int32_t *a;
+  float2 *f;  // FP32 copy of (c, s), or null
   int cnt, cap;
   int *err;
   __device__ __forceinline__ void push(double cc, double ss, int aa) {
     if (cnt < cap) {
       c[cnt] = cc; s[cnt] = ss; a[cnt] = aa;
+      if (f) f[cnt] = make_float2((float)cc, (float)ss);
     } else {
       atomicOr(err, ERR_CAP);
     }
     cnt++;
   }
 };
-
-// Left rotation on rows (a, a+1) over columns [jlo, jhi]; the eliminated entry
-// is (a+1, ec) and the pivot (a, ec).  ec == 0: the eliminated entry is u(a+1)
-// and the pivot u(a) (start of a phase-1 chase).
-__device__ __forceinline__ void rows_op(Core &K, Rec &rec, int a, double c, double s, double r,
-                                        int jlo, int jhi, int ec) {
-  if (jlo < 1) jlo = 1;
-  if (jhi > K.n) jhi = K.n;
-  for (int j = jlo; j <= jhi; j++) {
-    double x = K.get(a, j), y = K.get(a + 1, j);
-    K.put(a, j, add(mul(c, x), mul(s, y)));
-    K.put(a + 1, j, add(mul(-s, x), mul(c, y)));
-  }
-  if (ec > 0) {
-    K.put(a, ec, r);
-    K.put(a + 1, ec, 0.0);
-  } else {
-    K.u[a] = r;
-    K.u[a + 1] = 0.0;
-  }
-  for (int t = 0; t < K.rx; t++) {
-    double *U = K.Ux + (size_t)t * K.m - 1;
-    double x = U[a], y = U[a + 1];
-    U[a] = add(mul(c, x), mul(s, y));
-    U[a + 1] = add(mul(-s, x), mul(c, y));
-  }
-  rec.push(c, s, a);
-}
-
-// Right rotation on columns (a, a+1) over rows [ilo, ihi] (and row 1 when
-// with_row1); the eliminated entry is (er, a+1) and the pivot (er, a).
-__device__ __forceinline__ void cols_op(Core &K, Rec &rec, int a, double c, double s, double r,
-                                        int ilo, int ihi, int er, bool with_row1, bool rot_v) {
-  if (ilo < 1) ilo = 1;
-  if (ihi > K.N) ihi = K.N;
-  if (with_row1 && ilo > 1) {
-    double x = K.get(1, a), y = K.get(1, a + 1);
-    K.put(1, a, add(mul(c, x), mul(s, y)));
-    K.put(1, a + 1, add(mul(-s, x), mul(c, y)));
-  }
-  for (int i = ilo; i <= ihi; i++) {
-    double x = K.get(i, a), y = K.get(i, a + 1);
-    K.put(i, a, add(mul(c, x), mul(s, y)));
-    K.put(i, a + 1, add(mul(-s, x), mul(c, y)));
-  }
-  K.put(er, a, r);
-  K.put(er, a + 1, 0.0);
-  if (rot_v) {
-    double x = K.v[a], y = K.v[a + 1];
-    K.v[a] = add(mul(c, x), mul(s, y));
-    K.v[a + 1] = add(mul(-s, x), mul(c, y));
-  }
-  for (int t = 0; t < K.rx; t++) {
-    double *V = K.Vx + (size_t)t * K.n - 1;
-    double x = V[a], y = V[a + 1];
-    V[a] = add(mul(c, x), mul(s, y));
-    V[a + 1] = add(mul(-s, x), mul(c, y));
-  }
-  rec.push(c, s, a);
-}
 
 struct Task {
   int t;      // task id (>= T: slot exhausted)
@@ -203,100 +220,200 @@ __device__ __forceinline__ void task_init(Task &k, int t, int T, int N, int n) {
   }
 }
 
-__device__ __forceinline__ void chase_start(Core &K, Task &k, int kk) {
-  k.ii = kk;
-  if (kk + 2 <= K.N && K.get(kk + 2, kk) != 0.0) {
-    k.st = S_CL;
-    k.pos = kk + 1;
-  } else {
-    k.done = true;
-  }
-}
+// ----------------------------------------------------------------------------
+// the chase logic, shared by both engines
+// ----------------------------------------------------------------------------
+template <class Store, bool FAST>
+struct Chaser {
+  using A = Arith<FAST>;
+  Store S;
+  int N, n, m;
+  int *err;
+  double *Ux, *Vx;
+  int rx;
+  double *zero;  // a cell that always reads 0: stands for entries outside the band
+  double *sink;  // a cell that absorbs writes to entries outside the band
 
-// Runs one op of task k.  Left rotations go to recL, right ones to recR.
-__device__ void run_op(Core &K, Task &k, Rec &recL, Rec &recR, int &nl, int &nr) {
-  const int n = K.n, N = K.N;
-  double c, s, r;
-  switch (k.st) {
-    case S_L0: {  // P1 start: left (j-1, j) zeroing u(j)
-      int a = k.p - 1;
-      if (!rotg(K.u[a], K.u[a + 1], c, s, r)) { k.done = true; return; }
-      rows_op(K, recL, a, c, s, r, a, a + 2, 0); nl++;
-      int i = k.p - 1;
-      k.ii = i; k.st = S_R1;
-      if (!(i + 2 <= n && K.get(i, i + 2) != 0.0)) { k.done = true; return; }
-      k.pos = i + 1;
+  __device__ __forceinline__ bool inband(int i, int j) const {
+    if (i < 1 || i > N || j < 1 || j > n) return false;
+    if (i == 1) return true;
+    const int o = j - i;
+    return o >= -2 && o <= 3;
+  }
+  __device__ __forceinline__ double *rd(int i, int j) const { return inband(i, j) ? S.cell(i, j) : zero; }
+  __device__ __forceinline__ double *wr(int i, int j) const { return inband(i, j) ? S.cell(i, j) : sink; }
+  __device__ __forceinline__ double get(int i, int j) const { return Store::load(rd(i, j)); }
+  __device__ __forceinline__ void store(double *p, double x) {
+    if (p == sink) {
+      if (nz(x)) atomicOr(err, ERR_BAND);
       return;
     }
-    case S_R1: {  // P1: right (i+1, i+2) zeroing M(i, i+2)
-      int i = k.ii, a = i + 1;
-      if (!rotg(K.get(i, i + 1), K.get(i, i + 2), c, s, r)) { atomicOr(K.err, ERR_SCHEDULE); k.done = true; return; }
-      cols_op(K, recR, a, c, s, r, a - 1, a + 2, i, false, true); nr++;
-      if (i + 3 <= N && K.get(i + 3, i + 1) != 0.0) { k.st = S_L1; k.pos = i + 2; return; }
-      i += 2; k.ii = i;
-      if (!(i + 2 <= n && K.get(i, i + 2) != 0.0)) { k.done = true; return; }
-      k.pos = i + 1;
-      return;
-    }
-    case S_L1: {  // P1: left (i+2, i+3) zeroing M(i+3, i+1)
-      int i = k.ii, a = i + 2;
-      if (!rotg(K.get(i + 2, i + 1), K.get(i + 3, i + 1), c, s, r)) { atomicOr(K.err, ERR_SCHEDULE); k.done = true; return; }
-      rows_op(K, recL, a, c, s, r, a - 1, a + 2, i + 1); nl++;
-      i += 2; k.ii = i; k.st = S_R1;
-      if (!(i + 2 <= n && K.get(i, i + 2) != 0.0)) { k.done = true; return; }
-      k.pos = i + 1;
-      return;
-    }
-    case S_P2: {  // P2: right (j-1, j) zeroing M(1, j)
-      int j = k.p, a = j - 1;
-      if (rotg(K.get(1, j - 1), K.get(1, j), c, s, r)) {
-        cols_op(K, recR, a, c, s, r, a - 1, a + 2, 1, true, false); nr++;
-      }
-      chase_start(K, k, j - 1);
-      return;
-    }
-    case S_A: {  // P3b (a): left (i, i+1) zeroing M(i+1, i)
-      int i = k.p;
-      k.st = S_B;
-      if (i + 1 <= N && rotg(K.get(i, i), K.get(i + 1, i), c, s, r)) {
-        rows_op(K, recL, i, c, s, r, i, i + 3, i); nl++;
-      }
-      if (i + 3 <= n) { k.pos = i + 2; return; }
-      k.done = true;
-      return;
-    }
-    case S_B: {  // P3b (b): right (i+2, i+3) zeroing M(i, i+3)
-      int i = k.p;
-      if (!rotg(K.get(i, i + 2), K.get(i, i + 3), c, s, r)) { k.done = true; return; }
-      cols_op(K, recR, i + 2, c, s, r, i, i + 4, i, false, false); nr++;
-      chase_start(K, k, i + 2);
-      return;
-    }
-    case S_C: {  // P3c (c): right (i+1, i+2) zeroing M(i, i+2)
-      int i = k.p;
-      if (i + 2 > n) { k.done = true; return; }
-      if (!rotg(K.get(i, i + 1), K.get(i, i + 2), c, s, r)) { k.done = true; return; }
-      cols_op(K, recR, i + 1, c, s, r, i, i + 3, i, false, false); nr++;
-      chase_start(K, k, i + 1);
-      return;
-    }
-    case S_CL: {  // chase_lower: left (k+1, k+2) zeroing M(k+2, k)
-      int kk = k.ii, a = kk + 1;
-      if (!rotg(K.get(kk + 1, kk), K.get(kk + 2, kk), c, s, r)) { atomicOr(K.err, ERR_SCHEDULE); k.done = true; return; }
-      rows_op(K, recL, a, c, s, r, a - 1, a + 3, kk); nl++;
-      if (kk + 4 <= n && K.get(kk + 1, kk + 4) != 0.0) { k.st = S_CR; k.pos = kk + 3; return; }
-      chase_start(K, k, kk + 3);
-      return;
-    }
-    case S_CR: {  // chase_lower: right (k+3, k+4) zeroing M(k+1, k+4)
-      int kk = k.ii, a = kk + 3;
-      if (!rotg(K.get(kk + 1, kk + 3), K.get(kk + 1, kk + 4), c, s, r)) { atomicOr(K.err, ERR_SCHEDULE); k.done = true; return; }
-      cols_op(K, recR, a, c, s, r, a - 2, a + 2, kk + 1, false, false); nr++;
-      chase_start(K, k, kk + 3);
-      return;
+    *p = x;
+  }
+
+  __device__ __forceinline__ void rotate_extra(double *X, int ld, int a, double c, double s) {
+    for (int t = 0; t < rx; t++) {
+      double *U = X + (size_t)t * ld - 1;
+      const double xu = Store::load(U + a), yu = Store::load(U + a + 1);
+      U[a] = A::px(c, s, xu, yu);
+      U[a + 1] = A::py(c, s, xu, yu);
     }
   }
-}
+
+  // One rotation, described by its geometry:
+  //   rows (left rotation on rows a, a+1) over columns lo..lo+w-1, or
+  //   cols (right rotation on columns a, a+1) over rows lo..lo+w-1;
+  //   src 0: the entry eliminated is the second of the first pair, i.e.
+  //          (a+1, lo) or (lo, a+1); src 1: u(a+1) against u(a); src 2: row
+  //          1's (1, a+1) against (1, a) (row 1 rotates besides the w rows);
+  //   withv: v(a), v(a+1) rotate too (phase-1 right rotations).
+  // The extra pair (u, row 1 or v) takes the last of the five pair slots,
+  // which these ops leave free (w <= 4 whenever one is needed).  Every lane of
+  // a warp runs the same instruction sequence whatever its op -- on GB300 each
+  // FP64 warp instruction occupies its SM sub-partition's FP64 unit for tens of
+  // cycles however many lanes are active, so lanes must share them: addresses
+  // are formed first (entries outside the band read a zero cell and write to a
+  // sink), all loads are issued together, and the rotation and the pair
+  // updates are branch-free.  Returns false (nothing written) when the entry to
+  // eliminate is already zero; last receives the new value of (a, lo+w-1)
+  // (rows) or (lo+w-1, a) (cols), the bulge the chase looks at next.
+  __device__ __forceinline__ bool exec(bool isrows, int a, int lo, int w, int src, bool withv, Rec &recL,
+                                       Rec &recR, double &last) {
+    double *pa[5], *pb[5];
+    double x[5], y[5];
+    const bool extra = (src != 0) || withv;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      const bool in = q < w;
+      const int i0 = isrows ? a : lo + q, j0 = isrows ? lo + q : a;
+      const int i1 = isrows ? a + 1 : lo + q, j1 = isrows ? lo + q : a + 1;
+      pa[q] = in ? rd(i0, j0) : zero;
+      pb[q] = in ? rd(i1, j1) : zero;
+    }
+    if (extra) {
+      if (src == 1) { pa[4] = S.uptr(a); pb[4] = S.uptr(a + 1); }
+      else if (src == 2) { pa[4] = S.cell(1, a); pb[4] = S.cell(1, a + 1); }
+      else { pa[4] = S.vptr(a); pb[4] = S.vptr(a + 1); }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; q++) { x[q] = Store::load(pa[q]); y[q] = Store::load(pb[q]); }
+    const double f = src == 0 ? x[0] : x[4], g = src == 0 ? y[0] : y[4];
+    double c, s, r;
+    if (!A::rot(f, g, c, s, r)) return false;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      const double nx = A::px(c, s, x[q], y[q]), ny = A::py(c, s, x[q], y[q]);
+      x[q] = nx; y[q] = ny;
+    }
+    if (src == 0) { x[0] = r; y[0] = 0.0; }
+    else { x[4] = r; y[4] = 0.0; }
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      const bool in = q < w;
+      const int i0 = isrows ? a : lo + q, j0 = isrows ? lo + q : a;
+      const int i1 = isrows ? a + 1 : lo + q, j1 = isrows ? lo + q : a + 1;
+      double *qa = in ? wr(i0, j0) : sink, *qb = in ? wr(i1, j1) : sink;
+      if (q == 4 && extra) { qa = pa[4]; qb = pb[4]; }
+      store(qa, x[q]);
+      store(qb, y[q]);
+    }
+    if (isrows) {
+      rotate_extra(Ux, m, a, c, s);
+      recL.push(c, s, a);
+    } else {
+      rotate_extra(Vx, n, a, c, s);
+      recR.push(c, s, a);
+    }
+    last = w == 3 ? x[2] : (w == 4 ? x[3] : x[4]);
+    return true;
+  }
+
+  __device__ __forceinline__ void chase_start(Task &k, int kk, double bulge) {
+    k.ii = kk;
+    if (kk + 2 <= N && nz(bulge)) {
+      k.st = S_CL;
+      k.pos = kk + 1;
+    } else {
+      k.done = true;
+    }
+  }
+
+  // Runs one op of task k: the geometry of its next rotation (integer logic),
+  // the rotation itself (one shared code path), then the chase's next state.
+  // Left rotations go to recL, right ones to recR.
+  __device__ __forceinline__ void run_op(Task &k, Rec &recL, Rec &recR, int &nl, int &nr) {
+    // ---- plan
+    bool isrows = false, withv = false, doit = true;
+    int a = 0, lo = 0, w = 4, src = 0;
+    switch (k.st) {
+      case S_L0: isrows = true; a = k.p - 1; lo = a; w = 3; src = 1; break;                    // left (j-1, j) on u
+      case S_R1: a = k.ii + 1; lo = k.ii; w = 4; withv = true; break;                            // right (i+1, i+2)
+      case S_L1: isrows = true; a = k.ii + 2; lo = k.ii + 1; w = 4; break;                       // left (i+2, i+3)
+      case S_P2: a = k.p - 1; if (a - 1 == 1) { lo = 1; } else { lo = a - 1; src = 2; } w = 4; break;  // right (j-1, j), row 1
+      case S_A: isrows = true; a = k.p; lo = a; w = 4; doit = (k.p + 1 <= N); break;             // left (i, i+1)
+      case S_B: a = k.p + 2; lo = k.p; w = 5; break;                                             // right (i+2, i+3)
+      case S_C: a = k.p + 1; lo = k.p; w = 4; doit = (k.p + 2 <= n); break;                      // right (i+1, i+2)
+      case S_CL: isrows = true; a = k.ii + 1; lo = k.ii; w = 5; break;                           // left (k+1, k+2)
+      case S_CR: a = k.ii + 3; lo = k.ii + 1; w = 5; break;                                      // right (k+3, k+4)
+    }
+    // ---- rotate
+    double b = 0.0;
+    const bool ok = doit && exec(isrows, a, lo, w, src, withv, recL, recR, b);
+    if (ok) { if (isrows) nl++; else nr++; }
+    // ---- advance
+    switch (k.st) {
+      case S_L0: {
+        const int i = k.p - 1;
+        k.ii = i; k.st = S_R1;
+        if (!ok || !(i + 2 <= n && nz(b))) { k.done = true; return; }
+        k.pos = i + 1;
+        return;
+      }
+      case S_R1: {
+        int i = k.ii;
+        if (!ok) { atomicOr(err, ERR_SCHEDULE); k.done = true; return; }
+        if (i + 3 <= N && nz(b)) { k.st = S_L1; k.pos = i + 2; return; }
+        i += 2; k.ii = i;
+        if (!(i + 2 <= n && nz(get(i, i + 2)))) { k.done = true; return; }
+        k.pos = i + 1;
+        return;
+      }
+      case S_L1: {
+        if (!ok) { atomicOr(err, ERR_SCHEDULE); k.done = true; return; }
+        const int i = k.ii + 2;
+        k.ii = i; k.st = S_R1;
+        if (!(i + 2 <= n && nz(b))) { k.done = true; return; }
+        k.pos = i + 1;
+        return;
+      }
+      case S_P2: chase_start(k, k.p - 1, ok ? b : 0.0); return;
+      case S_A:
+        k.st = S_B;
+        if (k.p + 3 <= n) { k.pos = k.p + 2; return; }
+        k.done = true;
+        return;
+      case S_B:
+        if (!ok) { k.done = true; return; }
+        chase_start(k, k.p + 2, b);
+        return;
+      case S_C:
+        if (!ok) { k.done = true; return; }
+        chase_start(k, k.p + 1, b);
+        return;
+      case S_CL: {
+        const int kk = k.ii;
+        if (!ok) { atomicOr(err, ERR_SCHEDULE); k.done = true; return; }
+        if (kk + 4 <= n && nz(b)) { k.st = S_CR; k.pos = kk + 3; return; }
+        chase_start(k, kk + 3, get(kk + 5, kk + 3));
+        return;
+      }
+      case S_CR:
+        if (!ok) { atomicOr(err, ERR_SCHEDULE); k.done = true; return; }
+        chase_start(k, k.ii + 3, b);
+        return;
+    }
+  }
+};
 
 // Required lead of chase u over chase t (u < t) in positions.
 __device__ __forceinline__ int lag(int ku, int kt, bool adjacent) {
@@ -311,84 +428,110 @@ __device__ __forceinline__ int kind_of(int t, int p1, int p2) {
   return ((t - p1 - p2) & 1) ? P3C : P3B;
 }
 
+// Logical slot l (chases t with (t / CS) % S == l) lives on thread l: the
+// running chases, a window of consecutive ids, stay packed in few warps.  On
+// GB300 an SM's FP64 unit is shared by all its warps and each FP64 warp
+// instruction holds it for about 16 cycles whatever the number of active
+// lanes, so the cost of a step grows with the number of warps that have a
+// running chase, not with the number of chases.
+__device__ __forceinline__ int thread_slot(int th, int) { return th; }
+
 // status word of a slot: x = task id held, y = pos << 2 | started << 1 | done
 __device__ __forceinline__ int2 enc(const Task &k) {
   int pos = k.done ? 0 : (k.pos > (INT_MAX >> 3) ? (INT_MAX >> 3) : k.pos);
   return make_int2(k.t, (pos << 2) | (k.started ? 2 : 0) | (k.done ? 1 : 0));
 }
 
-__global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs A, int use_smem) {
+// The spike (m > n): one sequential chain on u in global memory.
+template <bool FAST>
+__device__ void run_spike(const ChaseArgs &Ar, unsigned long long *cnt0) {
+  using A = Arith<FAST>;
+  const int m = Ar.m, n = Ar.n;
+  int ns = 0;
+  double *u = Ar.band.u;
+  for (int j = m; j >= n + 2; j--) {
+    double c, s, r;
+    if (!A::rot(u[j - 1], u[j], c, s, r)) continue;
+    u[j - 1] = r;
+    u[j] = 0.0;
+    for (int t = 0; t < Ar.rx; t++) {
+      double *U = Ar.Ux + (size_t)t * m - 1;
+      const double x = U[j - 1], y = U[j];
+      U[j - 1] = A::px(c, s, x, y);
+      U[j] = A::py(c, s, x, y);
+    }
+    Ar.st.Sc[ns] = c; Ar.st.Ss[ns] = s; Ar.st.Sa[ns] = j - 1;
+    if (Ar.st.Sf) Ar.st.Sf[ns] = make_float2((float)c, (float)s);
+    ns++;
+  }
+  Ar.st.Sn[0] = ns;
+  *cnt0 = ns;
+}
+
+__device__ __forceinline__ void bind_rec(const ChaseArgs &Ar, const Task &k, Rec &recL, Rec &recR) {
+  const int cap = Ar.st.cap;
+  if (k.t < Ar.st.T) {
+    const size_t o = (size_t)k.t * cap;
+    recL.c = Ar.st.Lc + o; recL.s = Ar.st.Ls + o; recL.a = Ar.st.La + o;
+    recR.c = Ar.st.Rc + o; recR.s = Ar.st.Rs + o; recR.a = Ar.st.Ra + o;
+    recL.f = Ar.st.Lf ? Ar.st.Lf + o : nullptr;
+    recR.f = Ar.st.Rf ? Ar.st.Rf + o : nullptr;
+    recL.cnt = recR.cnt = 0;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// engine 1: one CTA
+// ----------------------------------------------------------------------------
+template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs Ar, int use_smem) {
   extern __shared__ double sh[];
   __shared__ int2 st[2][kMaxThreads];
   __shared__ int front[3];
   __shared__ int p1done, ndone;
   __shared__ unsigned long long cnt[9];
 
-  const int m = A.m, n = A.n, N = (m > n) ? n + 1 : n;
+  const int m = Ar.m, n = Ar.n, N = (m > n) ? n + 1 : n;
   const int S = blockDim.x, me = threadIdx.x;
-  const int T = A.st.T, cap = A.st.cap;
+  const int T = Ar.st.T;
   const int p1 = N - 1, p2 = n > 2 ? n - 2 : 0;
 
   if (me < 9) cnt[me] = 0;
-
-  // ---- spike (m > n): one sequential chain on u in global memory ----------
-  if (me == 0) {
-    int ns = 0;
-    double *u = A.band.u;
-    for (int j = m; j >= n + 2; j--) {
-      double c, s, r;
-      if (!rotg(u[j - 1], u[j], c, s, r)) continue;
-      u[j - 1] = r;
-      u[j] = 0.0;
-      for (int t = 0; t < A.rx; t++) {
-        double *U = A.Ux + (size_t)t * m - 1;
-        double x = U[j - 1], y = U[j];
-        U[j - 1] = add(mul(c, x), mul(s, y));
-        U[j] = add(mul(-s, x), mul(c, y));
-      }
-      A.st.Sc[ns] = c; A.st.Ss[ns] = s; A.st.Sa[ns] = j - 1;
-      ns++;
-    }
-    A.st.Sn[0] = ns;
-    cnt[0] = ns;
-  }
+  __syncthreads();
+  if (me == 0) run_spike<FAST>(Ar, &cnt[0]);
   __syncthreads();
 
-  // ---- working copy of the band: shared memory when it fits ---------------
-  Core K;
-  K.N = N; K.n = n; K.m = m; K.err = A.status;
-  K.Ux = A.Ux; K.Vx = A.Vx; K.rx = A.rx;
+  __shared__ double zero_cell, sink_cell;
+  if (me == 0) { zero_cell = 0.0; sink_cell = 0.0; }
+  Chaser<LocalStore, FAST> K;
+  K.zero = &zero_cell; K.sink = &sink_cell;
+  K.N = N; K.n = n; K.m = m; K.err = Ar.status;
+  K.Ux = Ar.Ux; K.Vx = Ar.Vx; K.rx = Ar.rx;
+  const int64_t nband = 6 * (int64_t)(N + 2) + 2 * (int64_t)(n + 2) + (N + 2);
+  K.S.ld = N + 2;
   if (use_smem) {
     double *p = sh;
-    for (int o = 0; o < 6; o++) { K.dg[o] = p; p += N + 2; }
-    K.r1 = p; p += n + 2;
-    K.v = p; p += n + 2;
-    K.u = p;
-    const int64_t cnt_band = 6 * (int64_t)(N + 2) + 2 * (int64_t)(n + 2) + (N + 2);
-    const double *src = A.band.dg[0];
-    for (int64_t q = me; q < cnt_band; q += S) sh[q] = src[q];
+    K.S.dg0 = p; p += 6 * (N + 2);
+    K.S.r1 = p; p += n + 2;
+    K.S.v = p; p += n + 2;
+    K.S.u = p;
+    const double *src = Ar.band.dg[0];
+    for (int64_t q = me; q < nband; q += S) sh[q] = src[q];
   } else {
-    for (int o = 0; o < 6; o++) K.dg[o] = A.band.dg[o];
-    K.r1 = A.band.r1; K.v = A.band.v; K.u = A.band.u;
+    K.S.dg0 = Ar.band.dg[0];
+    K.S.r1 = Ar.band.r1; K.S.v = Ar.band.v; K.S.u = Ar.band.u;
   }
 
-  // ---- engine ---------------------------------------------------------------
+  const int myslot = thread_slot(me, S);
   Task k;
-  task_init(k, me, T, N, n);
+  task_init(k, myslot, T, N, n);
   Rec recL, recR;
-  recL.cap = recR.cap = cap;
-  recL.err = recR.err = A.status;
+  recL.f = recR.f = nullptr;
+  recL.cap = recR.cap = Ar.st.cap;
+  recL.err = recR.err = Ar.status;
   int nl = 0, nr = 0;
-  auto bind = [&]() {
-    if (k.t < T) {
-      recL.c = A.st.Lc + (size_t)k.t * cap; recL.s = A.st.Ls + (size_t)k.t * cap; recL.a = A.st.La + (size_t)k.t * cap;
-      recR.c = A.st.Rc + (size_t)k.t * cap; recR.s = A.st.Rs + (size_t)k.t * cap; recR.a = A.st.Ra + (size_t)k.t * cap;
-      recL.cnt = recR.cnt = 0;
-      nl = nr = 0;
-    }
-  };
-  bind();
-  st[0][me] = enc(k);
+  bind_rec(Ar, k, recL, recR);
+  st[0][myslot] = enc(k);
   if (me == 0) {
     front[0] = 0; front[1] = INT_MAX; front[2] = INT_MAX;
     p1done = 0; ndone = 0;
@@ -403,15 +546,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs A, int use_smem
     const int p1d = p1done, nd = ndone;
     __syncthreads();
     if (!fold_done && p1d == p1) {
-      // fold: row 1 += u(1) v^T
-      double u1 = K.u[1];
-      for (int j = me + 1; j <= n; j += S) K.r1[j] = add(K.r1[j], mul(u1, K.v[j]));
+      const double u1 = *K.S.uptr(1);
+      for (int j = me + 1; j <= n; j += S) K.S.r1[j] = Arith<FAST>::px(1.0, u1, K.S.r1[j], K.S.v[j]);
       __syncthreads();
       fold_done = true;
     }
     if (fold_done && nd == T) break;
     if (step >= max_steps) {
-      if (me == 0) atomicOr(A.status, ERR_STEPS);
+      if (me == 0) atomicOr(Ar.status, ERR_STEPS);
       break;
     }
     const int rd = step & 1, wr = rd ^ 1;
@@ -420,72 +562,255 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs A, int use_smem
     const int fr = front[f_rd];
     if (!k.done) {
       const int t = k.t;
-      bool ok = true;
-      if (t >= p1 && !fold_done) ok = false;
+      bool ok = !(t >= p1 && !fold_done);
       if (ok) {
         const int lim = (t >= p1) ? p1 : 0;
         const int stop = fr > lim ? fr : lim;
         const int kt = kind_of(t, p1, p2);
         for (int u = t - 1; u >= stop; u--) {
           int2 w = st[rd][u % S];
-          if (w.x < u) { ok = false; break; }   // its slot still holds an older chase
-          if (w.x > u || (w.y & 1)) continue;   // finished
+          if (w.x < u) { ok = false; break; }    // its slot still holds an older chase
+          if (w.x > u || (w.y & 1)) continue;    // finished
           if (!(w.y & 2)) { ok = false; break; } // not started
           ok = (w.y >> 2) >= k.pos + lag(kind_of(u, p1, p2), kt, u == t - 1);
           break;
         }
       }
       if (ok) {
-        run_op(K, k, recL, recR, nl, nr);
+        K.run_op(k, recL, recR, nl, nr);
         k.started = true;
         if (k.done) {
-          A.st.Ln[t] = nl;
-          A.st.Rn[t] = nr;
+          Ar.st.Ln[t] = nl;
+          Ar.st.Rn[t] = nr;
           atomicAdd(&cnt[k.phase], (unsigned long long)nl);
           atomicAdd(&cnt[4 + k.phase], (unsigned long long)nr);
           if (t < p1) atomicAdd(&p1done, 1);
           atomicAdd(&ndone, 1);
           task_init(k, t + S, T, N, n);
-          bind();
+          nl = nr = 0;
+          bind_rec(Ar, k, recL, recR);
         }
       }
     }
-    if (!k.done) atomicMin(&front[f_wr], k.t);
-    st[wr][me] = enc(k);
+    {
+      const int mn = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);
+      if ((me & 31) == 0 && mn != INT_MAX) atomicMin(&front[f_wr], mn);
+    }
+    st[wr][myslot] = enc(k);
   }
   __syncthreads();
   if (me == 0) {
     cnt[8] = step;
-    for (int q = 0; q < 9; q++) atomicAdd(&A.counters[q], cnt[q]);
+    for (int q = 0; q < 9; q++) atomicAdd(&Ar.counters[q], cnt[q]);
   }
   if (use_smem) {
-    const int64_t cnt_band = 6 * (int64_t)(N + 2) + 2 * (int64_t)(n + 2) + (N + 2);
-    double *dst = A.band.dg[0];
-    for (int64_t q = me; q < cnt_band; q += S) dst[q] = sh[q];
+    double *dst = Ar.band.dg[0];
+    for (int64_t q = me; q < nband; q += S) dst[q] = sh[q];
   }
+}
+
+// ----------------------------------------------------------------------------
+// engine 2: a thread-block cluster
+// ----------------------------------------------------------------------------
+// The band stays in global memory (L2); chase t runs on CTA t % CS, logical
+// slot (t / CS) % S.  Step protocol: a cluster barrier opens every step, so
+// all band writes and status words of the previous step are visible.  At the
+// end of a step every CTA pushes (asynchronous remote stores) its status words
+// into the next CTA's mirror -- chase t-1 always lives on the CTA before chase
+// t's -- and its counters (chases done, phase-1 chases done, lowest
+// unfinished chase) into every CTA's inbox, so that the reads on a step's
+// critical path are local.  Totals are one step old, which is conservative.
+template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase_cluster(ChaseArgs Ar) {
+  __shared__ int2 st[2][kMaxThreads];    // this CTA's chase status words
+  __shared__ int2 pred[2][kMaxThreads];  // mirror of the previous CTA's status words
+  __shared__ int inbox[2][kMaxCluster][4];  // every CTA's counters: done, p1done, min unfinished
+  __shared__ int my_done, my_p1, my_min[2];
+  __shared__ unsigned long long cnt[9];
+
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int cta = (int)cl.block_rank();
+  const int m = Ar.m, n = Ar.n, N = (m > n) ? n + 1 : n;
+  const int S = blockDim.x, me = threadIdx.x;
+  const int T = Ar.st.T;
+  const int p1 = N - 1, p2 = n > 2 ? n - 2 : 0;
+  const int next = (cta + 1) % CS;
+
+  if (me < 9) cnt[me] = 0;
+  __syncthreads();
+  if (cta == 0 && me == 0) run_spike<FAST>(Ar, &cnt[0]);
+  cl.sync();  // spike done (global u)
+
+  Chaser<GlobalStore, FAST> K;
+  K.zero = &g_zero_sink[0]; K.sink = &g_zero_sink[1];
+  K.S.dg0 = Ar.band.dg[0]; K.S.ld = N + 2;
+  K.S.r1 = Ar.band.r1; K.S.u = Ar.band.u; K.S.v = Ar.band.v;
+  K.N = N; K.n = n; K.m = m; K.err = Ar.status;
+  K.Ux = Ar.Ux; K.Vx = Ar.Vx; K.rx = Ar.rx;
+
+  int2 *pred_next = cl.map_shared_rank(&pred[0][0], next);
+  const int stride = CS * S;
+  const int myslot = thread_slot(me, S);
+  Task k;
+  task_init(k, cta + CS * myslot, T, N, n);
+  Rec recL, recR;
+  recL.f = recR.f = nullptr;
+  recL.cap = recR.cap = Ar.st.cap;
+  recL.err = recR.err = Ar.status;
+  int nl = 0, nr = 0;
+  bind_rec(Ar, k, recL, recR);
+  st[0][myslot] = enc(k);
+  pred_next[myslot] = enc(k);  // slot 0 of the next CTA's mirror
+  if (me == 0) {
+    my_done = 0; my_p1 = 0; my_min[0] = INT_MAX; my_min[1] = INT_MAX;
+    for (int c = 0; c < CS; c++) {
+      int *ib = cl.map_shared_rank(&inbox[1][cta][0], c);
+      ib[0] = 0; ib[1] = 0; ib[2] = cta;
+    }
+  }
+  bool fold_done = false;
+  const long long max_steps = 64LL * (n + 16) + 4096;
+  long long step = 0;
+  for (;; step++) {
+    cl.sync();  // every write of the previous step is visible cluster-wide
+    const int rd = step & 1, wr = rd ^ 1;
+    // cluster totals at the end of the previous step (inbox slot wr)
+    int sd = 0, sp1 = 0, fr = INT_MAX;
+    for (int c = 0; c < CS; c++) {
+      sd += inbox[wr][c][0];
+      sp1 += inbox[wr][c][1];
+      fr = min(fr, inbox[wr][c][2]);
+    }
+    if (fr == INT_MAX) fr = T;
+    if (!fold_done && sp1 == p1) {
+      // fold: row 1 += u(1) v^T, the columns split over the cluster's threads
+      const double u1 = __ldcg(K.S.u + 1);
+      for (int j = cta * S + me + 1; j <= n; j += CS * S)
+        K.S.r1[j] = Arith<FAST>::px(1.0, u1, __ldcg(K.S.r1 + j), __ldcg(K.S.v + j));
+      cl.sync();
+      fold_done = true;
+    }
+    if (fold_done && sd == T) break;
+    if (step >= max_steps) {
+      if (me == 0) atomicOr(Ar.status, ERR_STEPS);
+      break;
+    }
+    if (!k.done) {
+      const int t = k.t;
+      bool ok = !(t >= p1 && !fold_done);
+      if (ok) {
+        const int lim = (t >= p1) ? p1 : 0;
+        const int stop = fr > lim ? fr : lim;
+        const int kt = kind_of(t, p1, p2);
+        for (int u = t - 1; u >= stop; u--) {
+          int2 w;
+          if (u == t - 1) {
+            w = pred[rd][(u / CS) % S];  // local mirror of the previous CTA
+          } else {
+            const int2 *su = cl.map_shared_rank(&st[0][0], u % CS);
+            w = su[rd * kMaxThreads + (u / CS) % S];
+          }
+          if (w.x < u) { ok = false; break; }
+          if (w.x > u || (w.y & 1)) continue;
+          if (!(w.y & 2)) { ok = false; break; }
+          ok = (w.y >> 2) >= k.pos + lag(kind_of(u, p1, p2), kt, u == t - 1);
+          break;
+        }
+      }
+      if (ok) {
+        K.run_op(k, recL, recR, nl, nr);
+        k.started = true;
+        if (k.done) {
+          Ar.st.Ln[t] = nl;
+          Ar.st.Rn[t] = nr;
+          atomicAdd(&cnt[k.phase], (unsigned long long)nl);
+          atomicAdd(&cnt[4 + k.phase], (unsigned long long)nr);
+          if (t < p1) atomicAdd(&my_p1, 1);
+          atomicAdd(&my_done, 1);
+          task_init(k, t + stride, T, N, n);
+          nl = nr = 0;
+          bind_rec(Ar, k, recL, recR);
+        }
+      }
+    }
+    {
+      const int mn = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);
+      if ((me & 31) == 0 && mn != INT_MAX) atomicMin(&my_min[rd], mn);
+    }
+    const int2 w = enc(k);
+    st[wr][myslot] = w;
+    pred_next[wr * kMaxThreads + myslot] = w;  // push to the next CTA's mirror
+    __syncthreads();
+    if (me < CS) {
+      // push this CTA's counters into every CTA's inbox (slot rd)
+      int *ib = cl.map_shared_rank(&inbox[rd][cta][0], me);
+      ib[0] = my_done;
+      ib[1] = my_p1;
+      ib[2] = my_min[rd];
+    }
+    __syncthreads();
+    if (me == 0) my_min[wr] = INT_MAX;
+  }
+  if (me == 0) {
+    if (cta == 0) cnt[8] = step;
+    for (int q = 0; q < 9; q++)
+      if (cnt[q]) atomicAdd(&Ar.counters[q], cnt[q]);
+  }
+  cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+template <bool FAST>
+cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
+  const int n = a.n, m = a.m;
+  const int N = (m > n) ? n + 1 : n;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (a.engine != 1 && (a.engine == 2 || n >= 512)) {
+    // cluster engine
+    const int CS = kMaxCluster;
+    const size_t dyn = 0;
+    int threads = ((n / 3 + 16) / CS + 31) / 32 * 32;
+    if (threads < 64) threads = 64;
+    if (threads > kMaxThreads) threads = kMaxThreads;
+    cudaError_t e = cudaFuncSetAttribute(k_chase_cluster<FAST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_chase_cluster<FAST>, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  int threads = ((n / 3 + 16 + 31) / 32) * 32;
+  if (threads < 32) threads = 32;
+  if (threads > kMaxThreads) threads = kMaxThreads;
+  const size_t smem = sizeof(double) * (6 * (size_t)(N + 2) + 2 * (size_t)(n + 2) + (N + 2));
+  const size_t static_smem = sizeof(int2) * 2 * kMaxThreads + 64 + 9 * 8;
+  const int use_smem = (smem + static_smem + 1024 <= (size_t)optin) ? 1 : 0;
+  const size_t dyn = use_smem ? smem : 0;
+  if (use_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_chase<FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k_chase<FAST><<<1, threads, dyn, s>>>(a, use_smem);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s) {
-  const int n = a.n, m = a.m;
-  const int N = (m > n) ? n + 1 : n;
-  int threads = ((n / 3 + 16 + 31) / 32) * 32;
-  if (threads < 32) threads = 32;
-  if (threads > kMaxThreads) threads = kMaxThreads;
-  const size_t smem = sizeof(double) * (6 * (size_t)(N + 2) + 2 * (size_t)(n + 2) + (N + 2));
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t static_smem = sizeof(int2) * 2 * kMaxThreads + 64 + 9 * 8;
-  int use_smem = (smem + static_smem + 1024 <= (size_t)optin) ? 1 : 0;
-  size_t dyn = use_smem ? smem : 0;
-  if (use_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-  }
-  k_chase<<<1, threads, dyn, s>>>(a, use_smem);
-  return cudaGetLastError();
+  return a.fast ? launch_engine<true>(a, s) : launch_engine<false>(a, s);
 }
 
 }  // namespace bdu

@@ -159,7 +159,7 @@ extern "C" bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, 
   cudaStream_t s = (cudaStream_t)stream;
   double *band = (double *)(base + L.band);
   BandPtrs bp = band_ptrs(band, m, n);
-  RotStream st;
+  RotStream st{};  // FP32 copies stay null: this entry point is FP64 only
   st.T = num_tasks(m, n);
   st.cap = task_cap(n);
   st.Lc = (double *)(base + L.Lc); st.Ls = (double *)(base + L.Ls);
@@ -188,7 +188,7 @@ extern "C" bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, 
     ce = launch_project_nz(BDU_FP64, P, n, (int)n, (int)n, c, n, 1, bp.v + 1, n,
                            (int32_t *)(base + L.nz_c), s);
   if (ce == cudaSuccess) {
-    ChaseArgs a;
+    ChaseArgs a{};  // exact arithmetic, engine chosen by size
     a.m = (int)m; a.n = (int)n; a.band = bp;
     a.Ux = nullptr; a.Vx = nullptr; a.rx = 0;
     a.st = st; a.status = status; a.counters = counters;
