@@ -133,6 +133,14 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
 /* Statistics since creation.  Synchronizes. */
 bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out);
 
+/* Estimates ||Q^T Q - I||_2 and ||P^T P - I||_2 by power iteration (the
+ * check the paper applies to long update streams, Sec. 4.2) and stores them
+ * in the statistics; q_est / p_est may be NULL.  In the mixed form the same
+ * check runs automatically every check_every updates and re-orthogonalizes a
+ * factor (X <- X (3I - X^T X) / 2, FP64 products) whose estimate exceeds
+ * reorth_tol.  Synchronizes. */
+bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est);
+
 /* Enables (on != 0) or disables per-kernel timing with CUDA events recorded
  * on the handle's stream around each kernel group; the accumulated device
  * times are reported by bdu_stats.  Off by default. */

@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True):
     L.bdu_read_rotations.restype = ctypes.c_int
     L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
     L.bdu_stats.restype = ctypes.c_int
+    L.bdu_check_orthogonality.argtypes = [H, dp, dp]
+    L.bdu_check_orthogonality.restype = ctypes.c_int
     L.bdu_set_timing.argtypes = [H, ctypes.c_int]
     L.bdu_set_timing.restype = ctypes.c_int
     L.bdu_destroy.argtypes = [H]
@@ -237,6 +239,11 @@ class Factorization:
                 "timed_updates": st.timed_updates, "ms_project": st.ms_project,
                 "ms_chase": st.ms_chase, "ms_apply_q": st.ms_apply_q,
                 "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches}
+
+    def check_orthogonality(self):
+        q = ctypes.c_double(); p = ctypes.c_double()
+        _check(self._L, self._h, self._L.bdu_check_orthogonality(self._h, ctypes.byref(q), ctypes.byref(p)))
+        return q.value, p.value
 
     def set_timing(self, on=True):
         _check(self._L, self._h, self._L.bdu_set_timing(self._h, 1 if on else 0))

@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "bdu_internal.cuh"
 
 namespace bdu {
@@ -73,6 +75,13 @@ struct bdu_ctx {
   int *status;
   unsigned long long *counters;
   double *scratch64;  // for conversions in read (mixed form)
+  // orthogonality control (mixed form)
+  void *cublas;           // created on first use
+  double *ortho_ws;       // 3*m+1 doubles
+  double *rx_E, *rx_W;    // m*m doubles each, allocated on the first re-orthogonalization
+  int64_t since_check;
+  double ortho[2];        // last estimates for Q, P (-1 = none)
+  int64_t reorth[2];
   // bookkeeping
   int64_t updates;
   int64_t launches;
@@ -204,6 +213,61 @@ bdu_status check_device_status(bdu_ctx *h) {
   return BDU_OK;
 }
 
+// Estimate ||X^T X - I||_2 for Q (which = 0) or P (which = 1).
+bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
+  const int k = (int)(which == 0 ? h->m : h->n);
+  cudaError_t e = launch_ortho_probe(h->opt.precision, which == 0 ? h->Q : h->P, k, h->ortho_ws, 20, h->stream);
+  double acc = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, h->ortho_ws + 3 * k, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
+  *est = sqrt(acc);
+  h->ortho[which] = *est;
+  return BDU_OK;
+}
+
+bdu_status reorth_factor(bdu_ctx *h, int which) {
+  const int64_t k = which == 0 ? h->m : h->n;
+  if (!h->cublas) {
+    cublasHandle_t hb;
+    if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, BDU_ENOMEM, "cublasCreate failed");
+    h->cublas = hb;
+  }
+  if (!h->rx_E) {
+    h->rx_E = (double *)dev_alloc(h, sizeof(double) * h->m * h->m);
+    h->rx_W = (double *)dev_alloc(h, sizeof(double) * h->m * h->m);
+    if (!h->rx_E || !h->rx_W) {
+      dev_free(h, h->rx_E); dev_free(h, h->rx_W);
+      h->rx_E = h->rx_W = nullptr;
+      return fail(h, BDU_ENOMEM, "re-orthogonalization workspace allocation failed");
+    }
+  }
+  cudaError_t e = launch_reorth((float *)(which == 0 ? h->Q : h->P), (int)k, h->scratch64, h->rx_E, h->rx_W,
+                                h->cublas, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "re-orthogonalization");
+  h->reorth[which]++;
+  return BDU_OK;
+}
+
+// Mixed form: every check_every updates, probe both factors and re-orthogonalize
+// a factor whose estimate exceeds reorth_tol.
+bdu_status maybe_reorth(bdu_ctx *h, int64_t r) {
+  if (h->opt.precision != BDU_MIXED || h->opt.check_every <= 0) return BDU_OK;
+  h->since_check += r;
+  if (h->since_check < h->opt.check_every) return BDU_OK;
+  h->since_check = 0;
+  for (int which = 0; which < 2; which++) {
+    double est = 0.0;
+    bdu_status st = probe_factor(h, which, &est);
+    if (st != BDU_OK) return st;
+    if (h->opt.reorth_tol > 0.0 && est > h->opt.reorth_tol) {
+      st = reorth_factor(h, which);
+      if (st != BDU_OK) return st;
+    }
+  }
+  return BDU_OK;
+}
+
 // One update with B, C already in device memory.
 bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
   const int m = (int)h->m, n = (int)h->n;
@@ -259,7 +323,7 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     if (h->timing) h->apply_launches += 2;
     h->updates++;
   }
-  return BDU_OK;
+  return maybe_reorth(h, r);
 }
 
 }  // namespace
@@ -292,6 +356,7 @@ void bdu_destroy(bdu_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   resolve_timers(h);
+  if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
   for (void *p : h->blocks) h->al.put(p);
   h->blocks.clear();
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -360,6 +425,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->st.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
   h->status = (int *)dev_alloc(h, sizeof(int) * 4);
   h->counters = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * 16);
+  h->ortho[0] = h->ortho[1] = -1.0;
+  h->ortho_ws = (double *)dev_alloc(h, sizeof(double) * (3 * m + 8));
   if (o.precision == BDU_MIXED) {
     h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
     h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
@@ -368,7 +435,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   }
   bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
             h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
-            h->status && h->counters &&
+            h->status && h->counters && h->ortho_ws &&
             (o.precision == BDU_FP64 || (h->scratch64 && h->st.Lf && h->st.Rf && h->st.Sf));
   if (!ok) {
     fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (m=%lld n=%lld)", (long long)m, (long long)n);
@@ -564,7 +631,10 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
     out->rot_right[q] = (int64_t)c[4 + q];
   }
   out->chase_steps = (int64_t)c[8];
-  out->ortho_q = out->ortho_p = -1.0;
+  out->ortho_q = h->ortho[0];
+  out->ortho_p = h->ortho[1];
+  out->reorth_q = h->reorth[0];
+  out->reorth_p = h->reorth[1];
   resolve_timers(h);
   out->launches = h->launches;
   out->timed_updates = h->timed_updates;
@@ -573,6 +643,21 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   out->ms_apply_q = h->ms[2];
   out->ms_apply_p = h->ms[3];
   out->apply_launches = h->apply_launches;
+  return BDU_OK;
+}
+
+bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
+  cudaSetDevice(h->device);
+  double e0 = 0.0, e1 = 0.0;
+  bdu_status st = probe_factor(h, 0, &e0);
+  if (st == BDU_OK) st = probe_factor(h, 1, &e1);
+  if (st != BDU_OK) return st;
+  if (q_est) *q_est = e0;
+  if (p_est) *p_est = e1;
   return BDU_OK;
 }
 

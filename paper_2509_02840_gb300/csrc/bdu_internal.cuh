@@ -90,6 +90,10 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s);
 
+cudaError_t launch_ortho_probe(int precision, const void *X, int k, double *ws, int iters, cudaStream_t s);
+cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, void *cublas_handle,
+                          cudaStream_t s);
+
 cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, int64_t count,
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, int64_t count,

@@ -1,0 +1,65 @@
+"""Orthogonality control of the mixed form: the probe's estimate of
+||X^T X - I||_2 and the re-orthogonalization that keeps a long FP32 stream
+within the stated tolerances (singular values within 1e-5 relative of the
+exact ones, ||Q^T Q - I||_2 <= 1e-5)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_02840_gb300 import bdu, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def test_probe_estimates_the_spectral_norm():
+    m = n = 300
+    Q, d, e, P = I.factorization(m, n, config=0, which=2)
+    g = np.random.default_rng(0)
+    u = g.standard_normal(m); v = g.standard_normal(m)
+    Qp = Q + 3e-6 * np.outer(u / np.linalg.norm(u), v / np.linalg.norm(v))
+    exact = np.linalg.norm(Qp.T @ Qp - np.eye(m), 2)
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.FP64) as F:
+        q_est, p_est = F.check_orthogonality()
+        st = F.stats()
+    assert 0.9 * exact <= q_est <= 1.0001 * exact
+    assert p_est < 1e-12
+    assert st["ortho_q"] == q_est
+
+
+def test_block_stream_with_reorthogonalization():
+    """Rank-8 block updates (the mixed-form configuration, scaled to m=2048,
+    n=512): re-orthogonalization fires and the tolerances hold."""
+    m, n, r = 2048, 512, 8
+    Q, d, e, P = I.factorization(m, n, config=2)
+    A = Q @ O.bidiag_dense(d, e, m) @ P.T
+    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, reorth_tol=1e-6, check_every=8) as F:
+        for h in range(6):
+            B, C = I.block_update(m, n, h, config=2, r=r)
+            A += B @ C.T
+            F.update(B, C)
+        Qg, dg, eg, Pg = F.read()
+        st = F.stats()
+    assert st["reorth_q"] + st["reorth_p"] >= 1
+    sv_g = np.linalg.svd(O.bidiag_dense(dg, eg), compute_uv=False)
+    sv_A = np.linalg.svd(A, compute_uv=False)[:n]
+    assert np.max(np.abs(sv_g - sv_A)) / sv_A[0] <= 1e-5
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(m), 2) <= 1e-5
+    assert np.linalg.norm(Pg.T @ Pg - np.eye(n), 2) <= 1e-5
+    R = Qg @ O.bidiag_dense(dg, eg, m) @ Pg.T
+    assert np.linalg.norm(A - R) / np.linalg.norm(A) <= 1e-4
+
+
+def test_reorthogonalization_reduces_the_error():
+    m = n = 256
+    Q, d, e, P = I.factorization(m, n, config=0, which=9)
+    g = np.random.default_rng(1)
+    Qp = Q + 2e-5 * g.standard_normal((m, m)) / np.sqrt(m)
+    before = np.linalg.norm(Qp.T @ Qp - np.eye(m), 2)
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-7, check_every=1) as F:
+        B, C = I.dense_update(m, n, 0, config=0)
+        F.update(B, C)
+        Qg, _, _, _ = F.read()
+        st = F.stats()
+    assert st["reorth_q"] == 1
+    after = np.linalg.norm(Qg.T @ Qg - np.eye(m), 2)
+    assert after < 0.2 * before and after < 5e-6
