@@ -113,6 +113,21 @@ bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r)
  * the handle's stream has completed. */
 bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r);
 
+/* Batched update of many resident factorizations (any mix of m, n and rank):
+ * for every i, A_i + B_i C_i^T with device pointers dB[i] (m_i x r[i]) and
+ * dC[i] (n_i x r[i]), FP64 column-major.  Rank 1 steps are taken in rounds
+ * (round k serves the items with r[i] > k); each round is one launch of each
+ * kernel kind -- projection (first round), staging, bulge chasing (one thread
+ * block per factorization) and a fused apply whose blocks cover the row slabs
+ * of every Q and P in the round.  The results are identical to bdu_update_dev
+ * on each handle.  All handles must share a device and precision and appear
+ * once.  stream: cudaStream_t for the batch (NULL = the first handle's); the
+ * batch is ordered after each handle's queued work and each handle's later
+ * work after the batch.  Errors: BDU_EINVAL, BDU_EBUSY, BDU_EPOISONED,
+ * BDU_ENOMEM, BDU_ECUDA. */
+bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
+                            const int64_t *r, void *stream);
+
 /* Waits for all queued work and reports device-side failures
  * (BDU_ETIMEOUT, BDU_EINTERNAL, BDU_ECUDA). */
 bdu_status bdu_sync(bdu_handle h);

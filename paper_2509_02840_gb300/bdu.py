@@ -81,6 +81,9 @@ def load(build_if_missing: bool = True):
     L.bdu_read_rotations.restype = ctypes.c_int
     L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
     L.bdu_stats.restype = ctypes.c_int
+    L.bdu_update_batch.argtypes = [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                   ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    L.bdu_update_batch.restype = ctypes.c_int
     L.bdu_check_orthogonality.argtypes = [H, dp, dp]
     L.bdu_check_orthogonality.restype = ctypes.c_int
     L.bdu_set_timing.argtypes = [H, ctypes.c_int]
@@ -146,6 +149,21 @@ def use_torch_allocator():
         torch.cuda.caching_allocator_delete(ptr)
 
     set_allocator(alloc, free)
+
+
+def update_batch(factorizations, ptrB, ptrC, ranks, stream=None):
+    """Batched update (bdu_update_batch): ptrB[i], ptrC[i] are device pointers
+    (FP64, column-major) of factorization i's update of rank ranks[i]."""
+    L = load()
+    k = len(factorizations)
+    hs = (ctypes.c_void_p * k)(*[f._h for f in factorizations])
+    bs = (ctypes.c_void_p * k)(*[int(p) for p in ptrB])
+    cs = (ctypes.c_void_p * k)(*[int(p) for p in ptrC])
+    rs = (ctypes.c_int64 * k)(*[int(r) for r in ranks])
+    code = L.bdu_update_batch(hs, k, bs, cs, rs, ctypes.c_void_p(int(stream)) if stream else None)
+    if code != 0:
+        msg = L.bdu_last_error(hs[0]) if k else L.bdu_last_error(None)
+        raise BduError(code, msg.decode() if msg else "")
 
 
 class Factorization:

@@ -82,6 +82,9 @@ struct bdu_ctx {
   int64_t since_check;
   double ortho[2];        // last estimates for Q, P (-1 = none)
   int64_t reorth[2];
+  // descriptor workspace of batched updates led by this handle
+  void *batch_ws;
+  size_t batch_ws_bytes;
   // bookkeeping
   int64_t updates;
   int64_t launches;
@@ -326,6 +329,13 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   return maybe_reorth(h, r);
 }
 
+struct BatchGuard {
+  std::vector<bdu_ctx *> held;
+  ~BatchGuard() {
+    for (bdu_ctx *h : held) h->busy.store(0);
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -513,6 +523,155 @@ bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r)
 
 bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r) {
   return update_common(h, dB, dC, r, false);
+}
+
+bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
+                            const int64_t *r, void *stream) {
+  if (count < 0) return fail(nullptr, BDU_EINVAL, "bdu_update_batch: negative count");
+  if (count == 0) return BDU_OK;
+  if (!hs || !dB || !dC || !r) return fail(nullptr, BDU_EINVAL, "bdu_update_batch: NULL argument");
+  for (int i = 0; i < count; i++) {
+    if (!hs[i]) return fail(nullptr, BDU_EINVAL, "bdu_update_batch: NULL handle at %d", i);
+    if (r[i] < 0 || r[i] > 4096) return fail(hs[i], BDU_EINVAL, "bdu_update_batch: bad rank %lld", (long long)r[i]);
+    if (r[i] > 0 && (!dB[i] || !dC[i])) return fail(hs[i], BDU_EINVAL, "bdu_update_batch: NULL update pointer");
+    if (hs[i]->opt.precision != hs[0]->opt.precision || hs[i]->device != hs[0]->device)
+      return fail(hs[i], BDU_EINVAL, "bdu_update_batch: handles differ in precision or device");
+    for (int j = 0; j < i; j++)
+      if (hs[j] == hs[i]) return fail(hs[i], BDU_EINVAL, "bdu_update_batch: handle %d repeated", i);
+  }
+  BatchGuard bg;
+  for (int i = 0; i < count; i++) {
+    int expect = 0;
+    if (!hs[i]->busy.compare_exchange_strong(expect, 1)) return fail(hs[i], BDU_EBUSY, "handle in use by another thread");
+    bg.held.push_back(hs[i]);
+    if (hs[i]->poisoned) return fail(hs[i], BDU_EPOISONED, "handle poisoned by an earlier failure");
+  }
+  bdu_ctx *h0 = hs[0];
+  const int precision = h0->opt.precision;
+  cudaError_t ce = cudaSetDevice(h0->device);
+  if (ce != cudaSuccess) return cuda_fail(h0, ce, "cudaSetDevice");
+  cudaStream_t s = stream ? (cudaStream_t)stream : h0->stream;
+  int64_t max_r = 0;
+  for (int i = 0; i < count; i++) {
+    bdu_status st = ensure_rank_workspace(hs[i], r[i] > 0 ? r[i] : 1);
+    if (st != BDU_OK) return st;
+    if (r[i] > max_r) max_r = r[i];
+  }
+  // order the batch after each handle's pending work
+  for (int i = 0; i < count; i++)
+    if (hs[i]->stream != s) {
+      cudaEvent_t ev;
+      ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventRecord(ev, hs[i]->stream);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev, 0);
+      cudaEventDestroy(ev);
+      if (ce != cudaSuccess) return cuda_fail(hs[i], ce, "ordering a batch");
+    }
+  // descriptor workspace
+  const size_t need = sizeof(ChaseArgs) * count + sizeof(ApplyItem) * 2 * count + sizeof(ProjItem) * 2 * count +
+                      sizeof(int) * (2 * count + 2) + sizeof(double *) * 2 * count + 1024;
+  if (h0->batch_ws_bytes < need) {
+    void *p = dev_alloc(h0, need);
+    if (!p) return fail(h0, BDU_ENOMEM, "batch descriptor allocation failed");
+    dev_free(h0, h0->batch_ws);
+    h0->batch_ws = p;
+    h0->batch_ws_bytes = need;
+  }
+  char *ws = (char *)h0->batch_ws;
+  ChaseArgs *d_chase = (ChaseArgs *)ws;
+  ApplyItem *d_apply = (ApplyItem *)(ws + sizeof(ChaseArgs) * count);
+  ProjItem *d_proj = (ProjItem *)((char *)d_apply + sizeof(ApplyItem) * 2 * count);
+  int *d_first = (int *)((char *)d_proj + sizeof(ProjItem) * 2 * count);
+  const double **d_cols = (const double **)(((uintptr_t)(d_first + 2 * count + 2) + 15) & ~(uintptr_t)15);
+
+  // K1: projections of all items, one launch
+  std::vector<ProjItem> proj;
+  int max_nrow = 0;
+  for (int i = 0; i < count; i++) {
+    if (r[i] == 0) continue;
+    bdu_ctx *h = hs[i];
+    proj.push_back({h->Q, (int)h->m, (int)h->m, (int)r[i], dB[i], h->U, h->nzB});
+    proj.push_back({h->P, (int)h->n, (int)h->n, (int)r[i], dC[i], h->V, h->nzC});
+    if (h->m > max_nrow) max_nrow = (int)h->m;
+  }
+  if (proj.empty()) return BDU_OK;
+  ce = cudaMemcpyAsync(d_proj, proj.data(), sizeof(ProjItem) * proj.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = launch_project_batch(precision, d_proj, (int)proj.size(), max_nrow, max_nrow, (int)max_r, s);
+  if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched projection");
+
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int esz = precision == BDU_FP64 ? 8 : 4;
+  for (int64_t k = 0; k < max_r; k++) {
+    std::vector<ChaseArgs> chase;
+    std::vector<const double *> cols;  // u columns then v columns
+    std::vector<ApplyItem> apply;
+    std::vector<int> first;
+    int max_n = 0, max_band = 0, slabs = 0;
+    size_t smem = 0;
+    for (int i = 0; i < count; i++) {
+      if (r[i] <= k) continue;
+      bdu_ctx *h = hs[i];
+      const int m = (int)h->m, n = (int)h->n;
+      ChaseArgs a{};
+      a.m = m; a.n = n; a.band = band_ptrs(h->band, m, n);
+      a.rx = (int)(r[i] - k - 1);
+      a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
+      a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
+      a.st = h->st; a.status = h->status; a.counters = h->counters;
+      a.fast = precision == BDU_MIXED ? 1 : 0;
+      a.engine = 1;
+      chase.push_back(a);
+      cols.push_back(h->U + k * m);
+      if (n > max_n) max_n = n;
+      if ((int)band_doubles(m, n) > max_band) max_band = (int)band_doubles(m, n);
+      for (int side = 0; side < 2; side++) {
+        ApplyItem it{};
+        it.X = side == 0 ? h->Q : h->P;
+        it.ld = side == 0 ? m : n;
+        it.nrow = it.ncol = side == 0 ? m : n;
+        apply_geometry(precision, it.ncol, (size_t)optin, &it.R, &it.csw);
+        if (it.R == 0) return fail(h, BDU_EINVAL, "matrix too wide for the batched apply");
+        it.side = side;
+        it.with_spike = (side == 0 && m > n) ? 1 : 0;
+        it.st = h->st;
+        first.push_back(slabs);
+        slabs += (it.nrow + it.R - 1) / it.R;
+        const size_t sm = (size_t)esz * it.csw * it.ncol;
+        if (sm > smem) smem = sm;
+        apply.push_back(it);
+      }
+    }
+    const int nact = (int)chase.size();
+    for (int i = 0; i < count; i++)
+      if (r[i] > k) cols.push_back(hs[i]->V + k * hs[i]->n);
+    first.push_back(slabs);
+    ce = cudaMemcpyAsync(d_chase, chase.data(), sizeof(ChaseArgs) * nact, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_cols, cols.data(), sizeof(double *) * cols.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_apply, apply.data(), sizeof(ApplyItem) * apply.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = launch_stage_batch(d_chase, d_cols, d_cols + nact, nact, s);
+    if (ce == cudaSuccess) ce = launch_chase_batch(d_chase, nact, max_n, max_band, precision == BDU_MIXED, s);
+    if (ce == cudaSuccess) ce = launch_apply_batch(precision, d_apply, d_first, (int)apply.size(), slabs, smem, s);
+    if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched update round");
+    h0->launches += 3;
+  }
+  h0->launches += 2;
+  // each handle's later work waits for the batch
+  cudaEvent_t done;
+  ce = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventRecord(done, s);
+  for (int i = 0; i < count && ce == cudaSuccess; i++)
+    if (hs[i]->stream != s) ce = cudaStreamWaitEvent(hs[i]->stream, done, 0);
+  cudaEventDestroy(done);
+  if (ce != cudaSuccess) return cuda_fail(h0, ce, "ordering after a batch");
+  for (int i = 0; i < count; i++) {
+    hs[i]->updates += r[i];
+    bdu_status st = maybe_reorth(hs[i], r[i]);
+    if (st != BDU_OK) return st;
+  }
+  return BDU_OK;
 }
 
 bdu_status bdu_sync(bdu_handle h) {

@@ -80,6 +80,23 @@ struct ChaseArgs {
   int engine;         // 0: by size, 1: one CTA, 2: thread-block cluster
 };
 
+// One matrix (Q or P of one factorization) for the batched apply.
+struct ApplyItem {
+  void *X;
+  int64_t ld;
+  int nrow, ncol, R, csw, side, with_spike;
+  RotStream st;
+};
+
+// One projection X^T B for the batched projection.
+struct ProjItem {
+  const void *X;
+  int nrow, ncol, r;
+  const double *B;
+  double *U;
+  int32_t *nz;  // nrow*r indices followed by r counts
+};
+
 // Launchers (return the launch error, if any).
 cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s);
 
@@ -89,6 +106,16 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s);
+
+cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
+                               int fast, cudaStream_t s);
+void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
+cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
+                               int total_slabs, size_t smem, cudaStream_t s);
+cudaError_t launch_project_batch(int precision, const ProjItem *d_items, int count, int max_nrow,
+                                 int max_ncol, int max_r, cudaStream_t s);
+cudaError_t launch_stage_batch(const ChaseArgs *d_items, const double *const *d_ucol,
+                               const double *const *d_vcol, int count, cudaStream_t s);
 
 cudaError_t launch_ortho_probe(int precision, const void *X, int k, double *ws, int iters, cudaStream_t s);
 cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, void *cublas_handle,

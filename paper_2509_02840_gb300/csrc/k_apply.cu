@@ -82,14 +82,14 @@ template <> struct Vec<double> {
 // csw = V * (odd count of 16-byte vectors) >= R, so that the columns touched
 // by a stride-3 chase fall in distinct 16-byte bank groups.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_apply_slab(T *__restrict__ X, int64_t ld, int nrow,
-                                                         int ncol, int R, int csw, RotStream st,
-                                                         int side, int with_spike) {
+__device__ __forceinline__ void apply_slab_body(T *__restrict__ X, int64_t ld, int nrow, int ncol, int R,
+                                                int csw, const RotStream &st, int side, int with_spike,
+                                                int slab) {
   using VT = typename Vec<T>::type;
   constexpr int V = Vec<T>::V;
   extern __shared__ __align__(16) unsigned char raw[];
   T *tile = reinterpret_cast<T *>(raw);
-  const int r0 = blockIdx.x * R;
+  const int r0 = slab * R;
   const int rows = min(R, nrow - r0);
   if (rows <= 0) return;
   const int tid = threadIdx.x;
@@ -186,7 +186,64 @@ __global__ void __launch_bounds__(kThreads) k_apply_slab(T *__restrict__ X, int6
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply_slab(T *__restrict__ X, int64_t ld, int nrow,
+                                                         int ncol, int R, int csw, RotStream st,
+                                                         int side, int with_spike) {
+  apply_slab_body<T>(X, ld, nrow, ncol, R, csw, st, side, with_spike, blockIdx.x);
+}
+
+// Many matrices of uneven sizes in one launch: block b works on the slab
+// b - first[i] of item i, where first[] is the prefix sum of the items' slab
+// counts (found by binary search).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply_batch(const ApplyItem *__restrict__ items,
+                                                          const int *__restrict__ first, int count) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const ApplyItem it = items[lo];
+  apply_slab_body<T>((T *)it.X, it.ld, it.nrow, it.ncol, it.R, it.csw, it.st, it.side, it.with_spike,
+                     b - first[lo]);
+}
+
 }  // namespace
+
+// Rows per slab and column stride for an ncol-wide matrix within smem_cap
+// bytes of shared memory, as many rows as fit (at most 64).
+void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw) {
+  const int esz = (precision == BDU_FP64) ? 8 : 4;
+  const int V = 16 / esz;
+  int bestR = 0, bestc = 0;
+  for (int r = V; r <= 64; r += V) {
+    int w = r / V;
+    if ((w & 1) == 0) w++;
+    const int c = w * V;
+    if ((size_t)esz * c * ncol > smem_cap) break;
+    bestR = r; bestc = c;
+  }
+  *R = bestR; *csw = bestc;
+}
+
+cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
+                               int total_slabs, size_t smem, cudaStream_t s) {
+  if (count <= 0 || total_slabs <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (precision == BDU_FP64) {
+    e = cudaFuncSetAttribute(k_apply_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_apply_batch<double><<<total_slabs, kThreads, smem, s>>>(d_items, d_first, count);
+  } else {
+    e = cudaFuncSetAttribute(k_apply_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_apply_batch<float><<<total_slabs, kThreads, smem, s>>>(d_items, d_first, count);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s) {

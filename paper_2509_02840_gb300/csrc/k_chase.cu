@@ -484,7 +484,7 @@ __device__ __forceinline__ void bind_rec(const ChaseArgs &Ar, const Task &k, Rec
 // engine 1: one CTA
 // ----------------------------------------------------------------------------
 template <bool FAST>
-__global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs Ar, int use_smem) {
+__device__ __forceinline__ void engine_cta(const ChaseArgs &Ar, int use_smem) {
   extern __shared__ double sh[];
   __shared__ int2 st[2][kMaxThreads];
   __shared__ int front[3];
@@ -607,6 +607,24 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs Ar, int use_sme
     double *dst = Ar.band.dg[0];
     for (int64_t q = me; q < nband; q += S) dst[q] = sh[q];
   }
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase(ChaseArgs Ar, int use_smem) {
+  engine_cta<FAST>(Ar, use_smem);
+}
+
+// Many independent factorizations, one thread block each (the batched update
+// of resident streams): block b runs the one-CTA engine on items[b]; an item
+// whose band does not fit the launch's dynamic shared memory keeps it in
+// global memory.
+template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase_batch(const ChaseArgs *__restrict__ items,
+                                                             size_t smem_bytes) {
+  const ChaseArgs Ar = items[blockIdx.x];
+  const int N = (Ar.m > Ar.n) ? Ar.n + 1 : Ar.n;
+  const size_t need = sizeof(double) * (6 * (size_t)(N + 2) + 2 * (size_t)(Ar.n + 2) + (N + 2));
+  engine_cta<FAST>(Ar, need <= smem_bytes ? 1 : 0);
 }
 
 // ----------------------------------------------------------------------------
@@ -808,6 +826,31 @@ cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
+                               int fast, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int threads = ((max_n / 3 + 16 + 31) / 32) * 32;
+  if (threads < 32) threads = 32;
+  if (threads > kMaxThreads) threads = kMaxThreads;
+  const size_t static_smem = sizeof(int2) * 2 * kMaxThreads + 256;
+  size_t dyn = sizeof(double) * (size_t)max_band_doubles;
+  if (dyn + static_smem > (size_t)optin) dyn = (size_t)optin - static_smem;
+  cudaError_t e;
+  if (fast) {
+    e = cudaFuncSetAttribute(k_chase_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    k_chase_batch<true><<<count, threads, dyn, s>>>(d_items, dyn);
+  } else {
+    e = cudaFuncSetAttribute(k_chase_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    k_chase_batch<false><<<count, threads, dyn, s>>>(d_items, dyn);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s) {
   return a.fast ? launch_engine<true>(a, s) : launch_engine<false>(a, s);
