@@ -87,6 +87,7 @@ typedef struct {
   double ms_apply_q;        /* device time of the rotation apply to Q (K3) */
   double ms_apply_p;        /* device time of the rotation apply to P (K3) */
   int64_t apply_launches;   /* apply-kernel launches covered by ms_apply_q + ms_apply_p */
+  int64_t device_bytes;     /* device memory currently held by the handle */
 } bdu_stats_t;
 
 /* Fills *opt with the defaults listed above. */

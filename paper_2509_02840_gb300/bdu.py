@@ -38,7 +38,7 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("timed_updates", ctypes.c_int64),
                 ("ms_project", ctypes.c_double), ("ms_chase", ctypes.c_double),
                 ("ms_apply_q", ctypes.c_double), ("ms_apply_p", ctypes.c_double),
-                ("apply_launches", ctypes.c_int64)]
+                ("apply_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
@@ -256,7 +256,8 @@ class Factorization:
                 "ortho_q": st.ortho_q, "ortho_p": st.ortho_p, "launches": st.launches,
                 "timed_updates": st.timed_updates, "ms_project": st.ms_project,
                 "ms_chase": st.ms_chase, "ms_apply_q": st.ms_apply_q,
-                "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches}
+                "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches,
+                "device_bytes": st.device_bytes}
 
     def check_orthogonality(self):
         q = ctypes.c_double(); p = ctypes.c_double()

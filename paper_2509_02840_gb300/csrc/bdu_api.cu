@@ -63,6 +63,7 @@ struct bdu_ctx {
   bool own_stream;
   Alloc al;
   std::vector<void *> blocks;
+  std::vector<size_t> block_bytes;
   // factorization
   void *Q, *P;   // FP64 or FP32 (opt.precision)
   double *band;  // band_doubles(m, n)
@@ -119,7 +120,10 @@ bdu_status cuda_fail(bdu_ctx *h, cudaError_t e, const char *what) {
 
 void *dev_alloc(bdu_ctx *h, size_t bytes) {
   void *p = h->al.get(bytes);
-  if (p) h->blocks.push_back(p);
+  if (p) {
+    h->blocks.push_back(p);
+    h->block_bytes.push_back(bytes);
+  }
   return p;
 }
 
@@ -129,6 +133,8 @@ void dev_free(bdu_ctx *h, void *p) {
     if (h->blocks[i] == p) {
       h->blocks[i] = h->blocks.back();
       h->blocks.pop_back();
+      h->block_bytes[i] = h->block_bytes.back();
+      h->block_bytes.pop_back();
       break;
     }
   h->al.put(p);
@@ -166,8 +172,13 @@ bdu_status ensure_rank_workspace(bdu_ctx *h, int64_t r) {
   }
   dev_free(h, h->dB); dev_free(h, h->dC); dev_free(h, h->U); dev_free(h, h->V);
   dev_free(h, h->nzB); dev_free(h, h->nzC);
-  for (void *p : {(void *)dB, (void *)dC, (void *)U, (void *)V, (void *)nzB, (void *)nzC})
+  const size_t sz[6] = {sizeof(double) * h->m * r, sizeof(double) * h->n * r, sizeof(double) * h->m * r,
+                        sizeof(double) * h->n * r, sizeof(int32_t) * (h->m * r + r), sizeof(int32_t) * (h->n * r + r)};
+  int q = 0;
+  for (void *p : {(void *)dB, (void *)dC, (void *)U, (void *)V, (void *)nzB, (void *)nzC}) {
     h->blocks.push_back(p);
+    h->block_bytes.push_back(sz[q++]);
+  }
   h->dB = dB; h->dC = dC; h->U = U; h->V = V; h->nzB = nzB; h->nzC = nzC;
   h->rcap = r;
   return BDU_OK;
@@ -802,6 +813,9 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   out->ms_apply_q = h->ms[2];
   out->ms_apply_p = h->ms[3];
   out->apply_launches = h->apply_launches;
+  int64_t bytes = 0;
+  for (size_t b : h->block_bytes) bytes += (int64_t)b;
+  out->device_bytes = bytes;
   return BDU_OK;
 }
 
