@@ -154,7 +154,10 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out);
  * in the statistics; q_est / p_est may be NULL.  In the mixed form the same
  * check runs automatically every check_every updates and re-orthogonalizes a
  * factor (X <- X (3I - X^T X) / 2, FP64 products) whose estimate exceeds
- * reorth_tol.  Synchronizes. */
+ * reorth_tol.  The automatic check never makes an update wait: it is only
+ * enqueued, and its result is acted on by the first later update (or batch)
+ * that finds it finished, or else by the next call that synchronizes
+ * (bdu_sync, bdu_read, bdu_stats, this call).  Synchronizes. */
 bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est);
 
 /* Enables (on != 0) or disables per-kernel timing with CUDA events recorded

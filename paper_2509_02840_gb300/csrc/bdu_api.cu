@@ -82,6 +82,11 @@ struct bdu_ctx {
   double *rx_E, *rx_W;    // m*m doubles each, allocated on the first re-orthogonalization
   int64_t since_check;
   double ortho[2];        // last estimates for Q, P (-1 = none)
+  // automatic check in flight: the two squared estimates land in probe_host
+  // (pinned) and probe_ev marks their arrival; acted on once it has fired
+  double *probe_host;
+  cudaEvent_t probe_ev;
+  bool probe_pending;
   int64_t reorth[2];
   // descriptor workspace of batched updates led by this handle
   void *batch_ws;
@@ -227,12 +232,19 @@ bdu_status check_device_status(bdu_ctx *h) {
   return BDU_OK;
 }
 
-// Estimate ||X^T X - I||_2 for Q (which = 0) or P (which = 1).
-bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
+// Enqueues the estimate of ||X^T X - I||_2 for Q (which = 0) or P (which = 1):
+// the power iteration, then a copy of the squared estimate to *dst.
+cudaError_t enqueue_probe(bdu_ctx *h, int which, double *dst) {
   const int k = (int)(which == 0 ? h->m : h->n);
   cudaError_t e = launch_ortho_probe(h->opt.precision, which == 0 ? h->Q : h->P, k, h->ortho_ws, 20, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->ortho_ws + 3 * k, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  return e;
+}
+
+// The same estimate, waited for.
+bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
   double acc = 0.0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, h->ortho_ws + 3 * k, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = enqueue_probe(h, which, &acc);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
   *est = sqrt(acc);
@@ -263,22 +275,53 @@ bdu_status reorth_factor(bdu_ctx *h, int which) {
   return BDU_OK;
 }
 
-// Mixed form: every check_every updates, probe both factors and re-orthogonalize
-// a factor whose estimate exceeds reorth_tol.
-bdu_status maybe_reorth(bdu_ctx *h, int64_t r) {
-  if (h->opt.precision != BDU_MIXED || h->opt.check_every <= 0) return BDU_OK;
-  h->since_check += r;
-  if (h->since_check < h->opt.check_every) return BDU_OK;
-  h->since_check = 0;
+// Acts on a finished automatic check: records both estimates and
+// re-orthogonalizes a factor whose estimate exceeds reorth_tol.
+bdu_status resolve_probe(bdu_ctx *h) {
+  h->probe_pending = false;
   for (int which = 0; which < 2; which++) {
-    double est = 0.0;
-    bdu_status st = probe_factor(h, which, &est);
-    if (st != BDU_OK) return st;
+    const double est = sqrt(h->probe_host[which]);
+    h->ortho[which] = est;
     if (h->opt.reorth_tol > 0.0 && est > h->opt.reorth_tol) {
-      st = reorth_factor(h, which);
+      bdu_status st = reorth_factor(h, which);
       if (st != BDU_OK) return st;
     }
   }
+  return BDU_OK;
+}
+
+// Waits for an automatic check still in flight and acts on it (at every call
+// that synchronizes, so that what it returns reflects the check).
+bdu_status settle_probe(bdu_ctx *h) {
+  if (!h->probe_pending) return BDU_OK;
+  cudaError_t e = cudaEventSynchronize(h->probe_ev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
+  return resolve_probe(h);
+}
+
+// Mixed form: every check_every updates, probe both factors.  The probe is
+// only enqueued; its result is acted on by the first later update that finds
+// it finished, or by the next synchronizing call, so that no update waits on
+// the host for it.  A check falling due while one is in flight waits for it.
+bdu_status maybe_reorth(bdu_ctx *h, int64_t r) {
+  if (h->opt.precision != BDU_MIXED || h->opt.check_every <= 0) return BDU_OK;
+  if (h->probe_pending) {
+    cudaError_t q = cudaEventQuery(h->probe_ev);
+    if (q == cudaSuccess) {
+      bdu_status st = resolve_probe(h);
+      if (st != BDU_OK) return st;
+    } else if (q != cudaErrorNotReady) {
+      return cuda_fail(h, q, "orthogonality probe");
+    }
+  }
+  h->since_check += r;
+  if (h->since_check < h->opt.check_every || h->probe_pending) return BDU_OK;
+  h->since_check = 0;
+  cudaError_t e = enqueue_probe(h, 0, &h->probe_host[0]);
+  if (e == cudaSuccess) e = enqueue_probe(h, 1, &h->probe_host[1]);
+  if (e == cudaSuccess) e = cudaEventRecord(h->probe_ev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
+  h->probe_pending = true;
   return BDU_OK;
 }
 
@@ -378,6 +421,8 @@ void bdu_destroy(bdu_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   resolve_timers(h);
   if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
+  if (h->probe_ev) cudaEventDestroy(h->probe_ev);
+  if (h->probe_host) cudaFreeHost(h->probe_host);
   for (void *p : h->blocks) h->al.put(p);
   h->blocks.clear();
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -453,6 +498,13 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
     h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
     h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
     h->st.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
+    if (cudaHostAlloc((void **)&h->probe_host, 2 * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->probe_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      fail(nullptr, BDU_ENOMEM, "bdu_create: pinned host cell or event creation failed");
+      bdu_destroy(h);
+      return BDU_ENOMEM;
+    }
   }
   bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
             h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
@@ -691,7 +743,8 @@ bdu_status bdu_sync(bdu_handle h) {
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
   cudaSetDevice(h->device);
-  return check_device_status(h);
+  bdu_status st = settle_probe(h);
+  return st != BDU_OK ? st : check_device_status(h);
 }
 
 bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
@@ -700,7 +753,8 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   cudaSetDevice(h->device);
   bdu_status st = BDU_OK;
-  if (!h->poisoned) st = check_device_status(h);
+  if (!h->poisoned) st = settle_probe(h);
+  if (st == BDU_OK && !h->poisoned) st = check_device_status(h);
   const int64_t m = h->m, n = h->n;
   cudaError_t ce = cudaSuccess;
   auto fetch = [&](void *src, double *dst, int64_t count) {
@@ -790,6 +844,10 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   Guard g(h);
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   cudaSetDevice(h->device);
+  if (!h->poisoned) {
+    bdu_status sp = settle_probe(h);
+    if (sp != BDU_OK) return sp;
+  }
   unsigned long long c[16];
   cudaError_t ce = cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
@@ -826,7 +884,8 @@ bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est) {
   if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
   cudaSetDevice(h->device);
   double e0 = 0.0, e1 = 0.0;
-  bdu_status st = probe_factor(h, 0, &e0);
+  bdu_status st = settle_probe(h);
+  if (st == BDU_OK) st = probe_factor(h, 0, &e0);
   if (st == BDU_OK) st = probe_factor(h, 1, &e1);
   if (st != BDU_OK) return st;
   if (q_est) *q_est = e0;
