@@ -476,7 +476,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->Q = dev_alloc(h, es * m * m);
   h->P = dev_alloc(h, es * n * n);
   h->band = (double *)dev_alloc(h, sizeof(double) * band_doubles(m, n));
-  h->st.T = T; h->st.cap = cap;
+  h->st.T = T; h->st.cap = cap; h->st.p1 = (int)(h->N - 1);
   h->st.Lc = (double *)dev_alloc(h, sizeof(double) * tc);
   h->st.Ls = (double *)dev_alloc(h, sizeof(double) * tc);
   h->st.Rc = (double *)dev_alloc(h, sizeof(double) * tc);
@@ -498,6 +498,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
     h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
     h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
     h->st.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
+    h->st.Lm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
+    h->st.Rm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
     if (cudaHostAlloc((void **)&h->probe_host, 2 * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->probe_ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
@@ -509,7 +511,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
             h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
             h->status && h->counters && h->ortho_ws &&
-            (o.precision == BDU_FP64 || (h->scratch64 && h->st.Lf && h->st.Rf && h->st.Sf));
+            (o.precision == BDU_FP64 || (h->scratch64 && h->st.Lf && h->st.Rf && h->st.Sf && h->st.Lm && h->st.Rm));
   if (!ok) {
     fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (m=%lld n=%lld)", (long long)m, (long long)n);
     bdu_destroy(h);

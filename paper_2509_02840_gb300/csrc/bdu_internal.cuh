@@ -55,6 +55,8 @@ struct RotStream {
   int32_t *Sa, *Sn;  // spike records; Sn[0] = count
   // FP32 copies (c, s) of the records for the mixed form; null in the FP64 form
   float2 *Lf, *Rf, *Sf;
+  int p1;         // chases 0..p1-1 are phase-1 chases (pairs two columns apart)
+  int4 *Lm, *Rm;  // per-chase descriptors for the register-resident FP32 apply (T each), or null
 };
 
 // Number of chases of the schedule for an m x n problem.
@@ -110,6 +112,8 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);
 void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
+cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
+                             bool with_spike, cudaStream_t s);
 cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
                                int total_slabs, size_t smem, cudaStream_t s);
 cudaError_t launch_project_batch(int precision, const ProjItem *d_items, int count, int max_nrow,
