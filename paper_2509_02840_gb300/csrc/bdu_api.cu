@@ -228,6 +228,7 @@ bdu_status check_device_status(bdu_ctx *h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "synchronizing the handle's stream");
   if (st & ERR_STEPS) return fail(h, BDU_ETIMEOUT, "the bulge-chase engine exceeded its step budget");
+  if (st & ERR_APPLY) return fail(h, BDU_ETIMEOUT, "a bounded wait of the rotation apply ran out");
   if (st) return fail(h, BDU_EINTERNAL, "device invariant check failed (status bits 0x%x)", st);
   return BDU_OK;
 }
@@ -368,12 +369,12 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     // K3: Q <- Q prod G^T, P <- P prod H
     {
       Timer tm(h, 2);
-      e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s);
+      e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s, h->status);
       if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
     }
     {
       Timer tm(h, 3);
-      e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s);
+      e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s, h->status);
       if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
     }
     h->launches += 3;
@@ -495,8 +496,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->ortho_ws = (double *)dev_alloc(h, sizeof(double) * (3 * m + 8));
   if (o.precision == BDU_MIXED) {
     h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
-    h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
-    h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * tc);
+    h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
+    h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
     h->st.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
     h->st.Lm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
     h->st.Rm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));

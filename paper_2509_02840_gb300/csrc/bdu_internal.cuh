@@ -13,6 +13,7 @@ enum : int {
   ERR_CAP = 2,       // a chase produced more rotations than its record slot holds
   ERR_STEPS = 4,     // the chase engine exceeded its step budget (no progress)
   ERR_SCHEDULE = 8,  // an op found a zero where the schedule guarantees a nonzero
+  ERR_APPLY = 16,    // a bounded wait of the register-resident apply ran out
 };
 
 // The working core M = band + u v^T of one rank-1 step, in global memory.
@@ -106,14 +107,17 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
                            const double *B, int64_t ldb, int r, double *U, int64_t ldu,
                            cudaStream_t s);
 
+// status: the device error word (needed by the register-resident FP32 path;
+// null selects the shared-memory slab kernel).
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
-                         const RotStream &st, int side, bool with_spike, cudaStream_t s);
+                         const RotStream &st, int side, bool with_spike, cudaStream_t s,
+                         int *status = nullptr);
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);
 void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, cudaStream_t s);
+                             bool with_spike, int *status, cudaStream_t s);
 cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
                                int total_slabs, size_t smem, cudaStream_t s);
 cudaError_t launch_project_batch(int precision, const ProjItem *d_items, int count, int max_nrow,

@@ -246,10 +246,10 @@ cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const in
 }
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
-                         const RotStream &st, int side, bool with_spike, cudaStream_t s) {
+                         const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
   if (precision == BDU_MIXED) {
-    const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, s);
+    const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, s);
     if (e != cudaErrorNotSupported) return e;
   }
   int dev = 0, optin = 0, sms = 1;

@@ -2,26 +2,32 @@
 // rank-1 column to the FP32 columns of Q (left rotations) or P (right
 // rotations) (Sec. 3.2, Eq. bidiagplus).
 //
-// Rows are independent under column rotations.  Each thread owns W = 12
-// consecutive columns (c0 = W * thread) of V = 8 consecutive rows and keeps
-// that V x W block in registers through all the chases of the column: every
-// element is read from and written to global memory once, and a rotation costs
-// four FP32 operations per row and no shared-memory traffic.  A persistent
-// grid walks over the row groups.
+// Rows are independent under column rotations.  Each compute thread owns W
+// consecutive columns (c0 = W * thread) of V consecutive rows and keeps that
+// V x W block in registers through all the chases of the column: every
+// element is read from and written to global memory once, and a rotation
+// costs four FP32 operations per row.  A persistent grid walks over the row
+// groups.
 //
-// The rotations of one chase act on disjoint column pairs (a, a+1); their
-// first columns a increase by a fixed step, 2 in phase 1 and 3 in phases 2
-// and 3, unless a rotation was skipped because the entry it would eliminate
-// was already zero.  Since W is a multiple of 6, where a gap-free chase's
-// pairs fall inside a thread's block depends only on a mod step: five compiled
-// variants cover every such chase, and a thread finds the records of its
-// pairs by index arithmetic.  In two of the variants one pair straddles each
-// edge of the block; both threads owning it compute their half from exchanged
-// values (shuffles inside a warp, shared memory and one barrier across warps).
-// A chase with a gap takes a general path that binary-searches its records.
-// While chase t is applied, each thread copies the coefficients of its pairs
-// in chase t+3 and the descriptor of chase t+6 into its own shared-memory
-// rings with cp.async, so no load latency is exposed.
+// Records.  The rotations of one chase act on disjoint column pairs (a, a+1)
+// whose first columns a increase by a fixed step, 2 in phase 1 and 3 in
+// phases 2 and 3, unless a rotation was skipped because the entry it would
+// eliminate was already zero.  A producer warp streams each chase's FP32
+// coefficients into a ring of shared-memory slots with one bulk copy per
+// chase (full/empty mbarriers per slot), so the compute warps run ahead of
+// one another by up to the ring depth and never wait on global loads.
+//
+// Geometry.  W is a multiple of 6, so where a gap-free chase's pairs fall in a
+// block depends only on a mod step: five compiled variants cover every such
+// chase, and a thread finds its records by index arithmetic.  In two of the
+// variants one pair straddles each edge of every block; both owners compute
+// their half of it from exchanged values: shuffles inside a warp; across two
+// warps, shared memory with a per-layer flag (no block-wide barrier).  A chase
+// with a gap takes a general path that binary-searches its records.  A warp
+// whose columns the chase does not reach skips it.
+//
+// Every wait is bounded; one that runs out sets ERR_APPLY in the status word
+// and the kernel carries on (the result is then reported as invalid).
 //
 // Arithmetic: the generator's FP32 copies of (c, s), x' = fma(c, x, s*y),
 // y' = fma(c, y, -s*x) -- the operations of the shared-memory slab kernel, so
@@ -34,23 +40,50 @@
 namespace bdu {
 namespace {
 
-constexpr int kMaxThreads = 384;  // threads per block: ceil(ncol / W) rounded to warps
-constexpr int kDist = 3;          // chases between a coefficient copy and its use
-constexpr int kDescRing = 8;      // descriptor ring slots (>= 2 kDist + 1, power of two)
-constexpr int kCoefRing = 4;      // coefficient ring slots (>= kDist + 1, power of two)
+constexpr int kMaxThreads = 384;  // compute warps + the producer warp
+constexpr int kMaxCompute = 352;  // compute threads
+constexpr int kSpin = 1 << 22;    // bound on every wait loop
+constexpr size_t kSmemBudget = 200 * 1024;
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy primitives
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar))
+               : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Waits for the completion of the phase with the given parity; false if the
+// bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int i = 0; i < kSpin; i++) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void rot32(float c, float s, float &x, float &y) {
@@ -59,20 +92,24 @@ __device__ __forceinline__ void rot32(float c, float s, float &x, float &y) {
   y = fmaf(c, yo, -s * xo);
 }
 
-// Chase descriptor (one per chase, read by every thread):
-//   x = e0, the record index of the pair starting at column phi (< 0 allowed):
-//       a thread's first pair inside its block is record e0 + c0 / step;
-//   y = count | code << 24, code = 0..4 for a gap-free progression with
-//       (step, first column mod step) = (2,0), (2,1), (3,0), (3,1), (3,2),
-//       5 for a chase with a gap, 7 for an empty one;
-//   z, w = first columns of the chase's first and last pairs.
+constexpr int kEmptyCode = 7;
+
+// ---------------------------------------------------------------------------
+// per-chase descriptors
+// ---------------------------------------------------------------------------
+// x = e0, the record index of the pair starting at column phi (< 0 allowed):
+//     a thread's first pair inside its block is record e0 + c0 / step;
+// y = count | code << 24, code = 0..4 for a gap-free progression with
+//     (step, first column mod step) = (2,0), (2,1), (3,0), (3,1), (3,2),
+//     5 for a chase with a gap, 7 for an empty one;
+// z, w = first columns of the chase's first and last pairs.
 __global__ void k_chase_descriptors(const int32_t *__restrict__ Ca, const int32_t *__restrict__ Cn, int T,
                                     int cap, int p1, int4 *__restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
   const int cnt = min(max(Cn[t], 0), cap);
   if (cnt == 0) {
-    out[t] = make_int4(0, 7 << 24, INT_MAX, INT_MIN);
+    out[t] = make_int4(0, kEmptyCode << 24, INT_MAX, INT_MIN);
     return;
   }
   const int step = t < p1 ? 2 : 3;
@@ -87,10 +124,13 @@ __global__ void k_chase_descriptors(const int32_t *__restrict__ Ca, const int32_
   out[t] = make_int4(e0, cnt | (code << 24), first, last);
 }
 
-// The spike chain: rotations on (a, a+1) with a descending; column a+1 of one
-// rotation is column a of the previous one, kept in a register.  Column a has
-// not been touched by earlier rotations of the chain, so its loads are issued
-// ahead, eight records at a time.
+// ---------------------------------------------------------------------------
+// the spike chain
+// ---------------------------------------------------------------------------
+// Rotations on (a, a+1) with a descending; column a+1 of one rotation is
+// column a of the previous one, kept in a register.  Column a has not been
+// touched by earlier rotations of the chain, so its loads are issued ahead,
+// eight records at a time.
 __global__ void k_apply_spike32(float *__restrict__ X, int64_t ld, int nrow, const float2 *__restrict__ Sf,
                                 const int32_t *__restrict__ Sa, const int32_t *__restrict__ Sn) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,34 +177,89 @@ __global__ void k_apply_spike32(float *__restrict__ X, int64_t ld, int nrow, con
   if (held >= 0) xr[(size_t)held * ld] = hv;
 }
 
-// Exchange of the edge columns with the neighbouring threads: yr = column c0+W
-// (the right neighbour's column 0), xl = column c0-1 (the left neighbour's
-// column W-1), both as they were before this chase.
+// ---------------------------------------------------------------------------
+// the register-resident kernel
+// ---------------------------------------------------------------------------
+// Shared memory of one block, R ring slots:
+//   slot s: the 16-byte chase descriptor, then the chase's records (float2),
+//           the first at index (t * cap) & 1 (copies start on 16-byte units);
+//   full[R], empty[R]: mbarriers;
+//   edges: per slot and compute warp, its column 0 (side 0) and column W-1
+//          (side 1) for the neighbouring warps, V floats each, and a flag per
+//          side naming the layer they belong to.
+struct Layout {
+  int R, rshift, nwc;  // R = 1 << rshift
+  size_t slot_bytes, full, empty, edge, flag, total;
+  void make(int cap, int V, int nwc_) {
+    nwc = nwc_;
+    slot_bytes = 16 + (size_t)((cap + 3) / 2) * 16;  // up to cap + 2 records
+    R = 0;
+    for (int r = 8; r >= 2; r >>= 1) {
+      const size_t edge_b = (size_t)r * nwc * 2 * V * 4, flag_b = (size_t)r * nwc * 2 * 4;
+      const size_t tot = r * slot_bytes + 2 * r * 8 + edge_b + flag_b;
+      if (tot <= kSmemBudget) {
+        R = r;
+        rshift = r == 8 ? 3 : (r == 4 ? 2 : 1);
+        full = r * slot_bytes;
+        empty = full + 8 * r;
+        edge = empty + 8 * r;
+        flag = edge + edge_b;
+        total = flag + flag_b;
+        break;
+      }
+    }
+  }
+};
+
+// Values of the neighbouring columns before this chase: yr = column c0+W,
+// xl = column c0-1.  Across warps through shared memory and flags: a warp
+// publishes its edges before it waits for its neighbours', so no wait cycle
+// can form.
 template <int W, int V>
 __device__ __forceinline__ void exchange(const float (&x)[V][W], float (&xl)[V], float (&yr)[V], float *edge,
-                                         int lane, int warp, int nwarps) {
+                                         volatile int *flag, int slot, int q, int lane, int warp, int nwc,
+                                         bool lact, bool ract, int *status) {
 #pragma unroll
   for (int r = 0; r < V; r++) {
     yr[r] = __shfl_down_sync(0xffffffffu, x[r][0], 1);
     xl[r] = __shfl_up_sync(0xffffffffu, x[r][W - 1], 1);
   }
-  if (lane == 0)
+  const int base = slot * nwc + warp;  // this warp's entries in the slot
+  if (lane == 0 && lact) {
 #pragma unroll
-    for (int r = 0; r < V; r++) edge[warp * V + r] = x[r][0];
-  if (lane == 31)
+    for (int r = 0; r < V; r++) edge[(base * 2 + 0) * V + r] = x[r][0];
+    __threadfence_block();
+    flag[base * 2 + 0] = q;
+  }
+  if (lane == 31 && ract) {
 #pragma unroll
-    for (int r = 0; r < V; r++) edge[(nwarps + warp) * V + r] = x[r][W - 1];
-  __syncthreads();
-  if (lane == 31 && warp + 1 < nwarps)
+    for (int r = 0; r < V; r++) edge[(base * 2 + 1) * V + r] = x[r][W - 1];
+    __threadfence_block();
+    flag[base * 2 + 1] = q;
+  }
+  if (lane == 31 && ract) {
+    const int nb = base + 1;  // the right neighbour's column 0
+    int i = 0;
+    while (flag[nb * 2 + 0] != q && i < kSpin) i++;
+    if (i == kSpin) atomicOr(status, ERR_APPLY);
+    __threadfence_block();
 #pragma unroll
-    for (int r = 0; r < V; r++) yr[r] = edge[(warp + 1) * V + r];
-  if (lane == 0 && warp > 0)
+    for (int r = 0; r < V; r++) yr[r] = edge[(nb * 2 + 0) * V + r];
+  }
+  if (lane == 0 && lact) {
+    const int nb = base - 1;  // the left neighbour's column W-1
+    int i = 0;
+    while (flag[nb * 2 + 1] != q && i < kSpin) i++;
+    if (i == kSpin) atomicOr(status, ERR_APPLY);
+    __threadfence_block();
 #pragma unroll
-    for (int r = 0; r < V; r++) xl[r] = edge[(nwarps + warp - 1) * V + r];
+    for (int r = 0; r < V; r++) xl[r] = edge[(nb * 2 + 1) * V + r];
+  }
+  __syncwarp();
 }
 
-// The halves of the straddling pairs this thread keeps: (c0+W-1, c0+W) gives
-// the new column W-1, (c0-1, c0) the new column 0.
+// The halves of the straddling pairs a thread keeps: (c0+W-1, c0+W) gives the
+// new column W-1, (c0-1, c0) the new column 0.
 template <int W, int V>
 __device__ __forceinline__ void right_half(float (&x)[V][W], float2 g, const float (&yr)[V]) {
 #pragma unroll
@@ -176,56 +271,34 @@ __device__ __forceinline__ void left_half(float (&x)[V][W], float2 g, const floa
   for (int r = 0; r < V; r++) x[r][0] = fmaf(g.x, x[r][0], -g.y * xl[r]);
 }
 
-// Where a gap-free chase of step S, pairs starting at columns = PHI (mod S),
-// meets a block: K pairs inside, and with X one pair across each edge.  Ring
-// slot k+1 holds the coefficients of the thread's k-th pair (record ef + k);
-// k = -1 and k = K are the straddling pairs.
-template <int W, int S, int PHI>
-struct Geo {
-  static constexpr int K = (W - 2 - PHI) / S + 1;
-  static constexpr bool X = ((W - 1) % S) == PHI;
-  static constexpr int kLo = X ? -1 : 0;
-  static constexpr int kHi = X ? K : K - 1;
-};
-
+// A gap-free chase of step S with pairs starting at columns = PHI (mod S):
+// K pairs inside each block (records ef .. ef+K-1) and, with X, one pair
+// across each edge (records ef-1 and ef+K).
 template <int W, int V, int S, int PHI>
-__device__ __forceinline__ void apply_prog(float (&x)[V][W], const float2 *ring, int nth, int ef, int cnt,
-                                           float *edge, int lane, int warp, int nwarps) {
-  using G = Geo<W, S, PHI>;
-  float xl[V], yr[V];
-  if (G::X) exchange<W, V>(x, xl, yr, edge, lane, warp, nwarps);
+__device__ __forceinline__ void apply_prog(float (&x)[V][W], const float2 *rec, int ef, int cnt,
+                                           const float (&xl)[V], const float (&yr)[V]) {
+  constexpr int K = (W - 2 - PHI) / S + 1;
+  constexpr bool X = ((W - 1) % S) == PHI;
 #pragma unroll
-  for (int k = 0; k < G::K; k++) {
+  for (int k = 0; k < K; k++) {
     if ((unsigned)(ef + k) < (unsigned)cnt) {
-      const float2 g = ring[(k + 1) * nth];
+      const float2 g = rec[ef + k];
 #pragma unroll
       for (int r = 0; r < V; r++) rot32(g.x, g.y, x[r][PHI + S * k], x[r][PHI + S * k + 1]);
     }
   }
-  if (G::X) {
-    if ((unsigned)(ef + G::K) < (unsigned)cnt) right_half<W, V>(x, ring[(G::K + 1) * nth], yr);
-    if ((unsigned)(ef - 1) < (unsigned)cnt) left_half<W, V>(x, ring[0], xl);
+  if (X) {
+    if ((unsigned)(ef + K) < (unsigned)cnt) right_half<W, V>(x, rec[ef + K], yr);
+    if ((unsigned)(ef - 1) < (unsigned)cnt) left_half<W, V>(x, rec[ef - 1], xl);
   }
 }
 
-template <int W, int S, int PHI>
-__device__ __forceinline__ void prefetch(float2 *dst, int nth, const float2 *src, int ef, int cnt) {
-  using G = Geo<W, S, PHI>;
-#pragma unroll
-  for (int k = G::kLo; k <= G::kHi; k++) {
-    const int e = ef + k;
-    if ((unsigned)e < (unsigned)cnt) cp_async8(dst + (k + 1) * nth, src + e);
-  }
-}
-
-// A chase with a gap: the thread's records are found by binary search (the
-// pairs of a chase are recorded in increasing order).
+// A chase with a gap: the thread's records are found by binary search over
+// the pair positions (recorded in increasing order).
 template <int W, int V>
-__device__ __forceinline__ void apply_general(float (&x)[V][W], const float2 *__restrict__ coef,
-                                           const int32_t *__restrict__ Ca, size_t base, int cnt, int c0,
-                                           float *edge, int lane, int warp, int nwarps) {
-  float xl[V], yr[V];
-  exchange<W, V>(x, xl, yr, edge, lane, warp, nwarps);
+__device__ __forceinline__ void apply_general(float (&x)[V][W], const float2 *rec,
+                                              const int32_t *__restrict__ Ca, size_t base, int cnt, int c0,
+                                              const float (&xl)[V], const float (&yr)[V]) {
   int lo = 0, hi = cnt;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -235,7 +308,7 @@ __device__ __forceinline__ void apply_general(float (&x)[V][W], const float2 *__
   for (int e = lo; e < cnt; e++) {
     const int p = Ca[base + e] - 1 - c0;
     if (p > W - 1) break;
-    const float2 g = coef[base + e];
+    const float2 g = rec[e];
     if (p == -1) {
       left_half<W, V>(x, g, xl);
     } else if (p == W - 1) {
@@ -253,21 +326,70 @@ __device__ __forceinline__ void apply_general(float (&x)[V][W], const float2 *__
 template <int W, int V>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     k_apply_reg(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float2 *__restrict__ coef,
-                const int32_t *__restrict__ Ca, const int4 *__restrict__ desc, int T, int cap) {
-  constexpr int kSlots = W / 2 + 2;
-  extern __shared__ __align__(16) unsigned char raw[];
-  const int nth = blockDim.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-  int4 *dring = reinterpret_cast<int4 *>(raw) + tid;                                          // [kDescRing][nth]
-  float2 *cring = reinterpret_cast<float2 *>(reinterpret_cast<int4 *>(raw) + kDescRing * nth) + tid;  // [kCoefRing][kSlots][nth]
-  float *edge0 = reinterpret_cast<float *>(cring - tid + kCoefRing * kSlots * nth);          // [2][2 nwarps V]
-  const int c0 = tid * W;
-  // the warp has work in a chase whose pairs start at columns first..last iff
-  // first <= wlast and last >= wfirst (pairs across the warp's edges included)
-  const int wfirst = warp * 32 * W - 1, wlast = (warp + 1) * 32 * W - 1;
+                const int32_t *__restrict__ Ca, const int4 *__restrict__ desc, int T, int cap, Layout L,
+                int *__restrict__ status) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwc = L.nwc, R = L.R, rs = L.rshift, rmask = L.R - 1;
+  uint64_t *full = reinterpret_cast<uint64_t *>(raw + L.full);
+  uint64_t *empty = reinterpret_cast<uint64_t *>(raw + L.empty);
+  float *edge = reinterpret_cast<float *>(raw + L.edge);
+  volatile int *flag = reinterpret_cast<volatile int *>(raw + L.flag);
   const int groups = (nrow + V - 1) / V;
-  int par = 0;  // edge buffer of the next exchange; alternates so that one barrier per exchange suffices
+  const int my_groups = (int)blockIdx.x < groups ? (groups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int layers = my_groups * T;  // chases this block goes through
 
+  if (tid == 0) {
+    for (int s = 0; s < R; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nwc);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int i = tid; i < R * nwc * 2; i += blockDim.x) flag[i] = -1;
+  __syncthreads();
+
+  if (warp == nwc) {
+    // ---- producer warp: one bulk copy per chase into the ring; the
+    // descriptors come 32 at a time, one per lane
+    const int4 none = make_int4(0, kEmptyCode << 24, INT_MAX, INT_MIN);
+    int4 dcur = none;
+    for (int q = 0, u = 0; q < layers; q++, u = (u + 1 == T) ? 0 : u + 1) {
+      if ((u & 31) == 0) dcur = (u + lane < T) ? desc[u + lane] : none;
+      int4 d;
+      d.x = __shfl_sync(0xffffffffu, dcur.x, u & 31);
+      d.y = __shfl_sync(0xffffffffu, dcur.y, u & 31);
+      d.z = __shfl_sync(0xffffffffu, dcur.z, u & 31);
+      d.w = __shfl_sync(0xffffffffu, dcur.w, u & 31);
+      if (lane == 0) {
+        const int s = q & rmask;
+        if (q >= R && !mbar_wait(&empty[s], (unsigned)(((q >> rs) - 1) & 1))) atomicOr(status, ERR_APPLY);
+        unsigned char *slot = raw + (size_t)s * L.slot_bytes;
+        *reinterpret_cast<int4 *>(slot) = d;
+        const int cnt = d.y & 0xffffff;
+        const size_t first = (size_t)u * cap;  // the chase's first record
+        const size_t start = first & ~(size_t)1;
+        const unsigned bytes = cnt > 0 ? (unsigned)(((first - start + cnt + 1) / 2) * 16) : 0u;
+        mbar_arrive_tx(&full[s], bytes);
+        if (bytes) bulk_g2s(slot + 16, coef + start, bytes, &full[s]);
+      }
+      __syncwarp();
+    }
+    // the last copies have landed before the block may exit
+    if (lane == 0)
+      for (int q = layers > R ? layers - R : 0; q < layers; q++)
+        if (!mbar_wait(&full[q & rmask], (unsigned)((q >> rs) & 1))) atomicOr(status, ERR_APPLY);
+    return;
+  }
+
+  // ---- compute warps
+  const int c0 = tid * W;
+  // the warp has work in a chase whose pairs start at columns z..w iff
+  // z <= (warp + 1) * span - 1 and w >= warp * span - 1 (pairs across its
+  // edges included)
+  const int span = 32 * W;
+  const int wlo = warp * span - 1, whi = (warp + 1) * span - 1;  // this warp's reach
+  int q = 0;
   for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
     const int r0 = grp * V;
     float x[V][W];
@@ -277,52 +399,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
       for (int r = 0; r < V; r++) x[r][k] = (col < ncol && r0 + r < nrow) ? X[(size_t)col * ld + r0 + r] : 0.f;
     }
-    for (int t = -2 * kDist; t < T; t++) {
-      cp_wait<kDist - 1>();  // the group issued kDist chases ago has landed
-      if (t >= 0) {
-        const int4 d = dring[(t & (kDescRing - 1)) * nth];
-        const int cnt = d.y & 0xffffff, code = d.y >> 24;
-        if (code != 7) {
-          const bool cross = code == 1 || code == 4 || code == 5;  // one barrier in this chase
-          if (d.z <= wlast && d.w >= wfirst) {
-            float *edge = edge0 + par * 2 * nwarps * V;
-            const float2 *ring = cring + (size_t)(t & (kCoefRing - 1)) * kSlots * nth;
-            switch (code) {
-              case 0: apply_prog<W, V, 2, 0>(x, ring, nth, d.x + tid * (W / 2), cnt, edge, lane, warp, nwarps); break;
-              case 1: apply_prog<W, V, 2, 1>(x, ring, nth, d.x + tid * (W / 2), cnt, edge, lane, warp, nwarps); break;
-              case 2: apply_prog<W, V, 3, 0>(x, ring, nth, d.x + tid * (W / 3), cnt, edge, lane, warp, nwarps); break;
-              case 3: apply_prog<W, V, 3, 1>(x, ring, nth, d.x + tid * (W / 3), cnt, edge, lane, warp, nwarps); break;
-              case 4: apply_prog<W, V, 3, 2>(x, ring, nth, d.x + tid * (W / 3), cnt, edge, lane, warp, nwarps); break;
-              default: apply_general<W, V>(x, coef, Ca, (size_t)t * cap, cnt, c0, edge, lane, warp, nwarps); break;
-            }
-          } else if (cross) {
-            __syncthreads();  // the barrier of the exchange the other warps perform
-          }
-          if (cross) par ^= 1;
+    for (int t = 0; t < T; t++, q++) {
+      const int s = q & rmask;
+      if (!mbar_wait(&full[s], (unsigned)((q >> rs) & 1))) atomicOr(status, ERR_APPLY);
+      const unsigned char *slot = raw + (size_t)s * L.slot_bytes;
+      const int4 d = *reinterpret_cast<const int4 *>(slot);
+      const int cnt = d.y & 0xffffff, code = d.y >> 24;
+      if (code != kEmptyCode && d.z <= whi && d.w >= wlo) {
+        const float2 *rec = reinterpret_cast<const float2 *>(slot + 16) + (t & cap & 1);
+        float xl[V], yr[V];
+        if (code == 1 || code == 4 || code == 5) {
+          // given this warp's part, the left (right) neighbour has one iff the
+          // chase starts (ends) within its reach
+          const bool lact = warp > 0 && d.z <= wlo;
+          const bool ract = warp + 1 < nwc && d.w >= whi;
+          exchange<W, V>(x, xl, yr, edge, flag, s, q, lane, warp, nwc, lact, ract, status);
+        }
+        switch (code) {
+          case 0: apply_prog<W, V, 2, 0>(x, rec, d.x + tid * (W / 2), cnt, xl, yr); break;
+          case 1: apply_prog<W, V, 2, 1>(x, rec, d.x + tid * (W / 2), cnt, xl, yr); break;
+          case 2: apply_prog<W, V, 3, 0>(x, rec, d.x + tid * (W / 3), cnt, xl, yr); break;
+          case 3: apply_prog<W, V, 3, 1>(x, rec, d.x + tid * (W / 3), cnt, xl, yr); break;
+          case 4: apply_prog<W, V, 3, 2>(x, rec, d.x + tid * (W / 3), cnt, xl, yr); break;
+          default: apply_general<W, V>(x, rec, Ca, (size_t)t * cap, cnt, c0, xl, yr); break;
         }
       }
-      // coefficients of chase t + kDist (its descriptor landed with the group awaited above)
-      const int u = t + kDist;
-      if (u >= 0 && u < T) {
-        const int4 d = dring[(u & (kDescRing - 1)) * nth];
-        const int cnt = d.y & 0xffffff, code = d.y >> 24;
-        if (code < 5 && d.z <= wlast && d.w >= wfirst) {
-          const float2 *src = coef + (size_t)u * cap;
-          float2 *dst = cring + (size_t)(u & (kCoefRing - 1)) * kSlots * nth;
-          switch (code) {
-            case 0: prefetch<W, 2, 0>(dst, nth, src, d.x + tid * (W / 2), cnt); break;
-            case 1: prefetch<W, 2, 1>(dst, nth, src, d.x + tid * (W / 2), cnt); break;
-            case 2: prefetch<W, 3, 0>(dst, nth, src, d.x + tid * (W / 3), cnt); break;
-            case 3: prefetch<W, 3, 1>(dst, nth, src, d.x + tid * (W / 3), cnt); break;
-            default: prefetch<W, 3, 2>(dst, nth, src, d.x + tid * (W / 3), cnt); break;
-          }
-        }
-      }
-      const int v = t + 2 * kDist;
-      if (v >= 0 && v < T) cp_async16(dring + (v & (kDescRing - 1)) * nth, desc + v);
-      cp_commit();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
-    cp_wait<0>();
 #pragma unroll
     for (int k = 0; k < W; k++) {
       const int col = c0 + k;
@@ -335,21 +439,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
 template <int W, int V>
 struct RegLaunch {
-  static constexpr int kSlots = W / 2 + 2;
   int nth = 0, grid = 0;
-  size_t smem = 0;
-  // Geometry for an nrow x ncol matrix; false when it is not covered.
-  bool plan(int nrow, int ncol) {
-    nth = ((ncol + W - 1) / W + 31) / 32 * 32;
-    if (nth > kMaxThreads) return false;
-    smem = (size_t)kDescRing * nth * 16 + (size_t)kCoefRing * kSlots * nth * 8 + (size_t)2 * 2 * (nth / 32) * V * 4;
-    if (cudaFuncSetAttribute(k_apply_reg<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  Layout L{};
+  // Geometry for an nrow x ncol matrix with record slots of cap; false when
+  // it is not covered.
+  bool plan(int nrow, int ncol, int cap) {
+    const int nwc = ((ncol + W - 1) / W + 31) / 32;
+    if (nwc * 32 > kMaxCompute) return false;
+    nth = nwc * 32 + 32;
+    L.make(cap, V, nwc);
+    if (L.R == 0) return false;
+    if (cudaFuncSetAttribute(k_apply_reg<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
         cudaSuccess)
       return false;
     int dev = 0, sms = 1, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_reg<W, V>, nth, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_reg<W, V>, nth, L.total) != cudaSuccess ||
         per_sm < 1)
       return false;
     const int groups = (nrow + V - 1) / V;
@@ -357,8 +463,8 @@ struct RegLaunch {
     return true;
   }
   void launch(float *X, int64_t ld, int nrow, int ncol, const float2 *coef, const int32_t *Ca, const int4 *desc,
-              int T, int cap, cudaStream_t s) const {
-    k_apply_reg<W, V><<<grid, nth, smem, s>>>(X, ld, nrow, ncol, coef, Ca, desc, T, cap);
+              int T, int cap, int *status, cudaStream_t s) const {
+    k_apply_reg<W, V><<<grid, nth, L.total, s>>>(X, ld, nrow, ncol, coef, Ca, desc, T, cap, L, status);
   }
 };
 
@@ -366,16 +472,17 @@ struct RegLaunch {
 
 // Register-resident FP32 apply; cudaErrorNotSupported, before anything is
 // launched, when the shape or the stream is not covered (the caller then uses
-// the shared-memory slab kernel).
+// the shared-memory slab kernel).  Records are copied in 16-byte units up to
+// one entry past the last chase's slot, so Lf and Rf hold T*cap + 2 entries.
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, cudaStream_t s) {
+                             bool with_spike, int *status, cudaStream_t s) {
   const float2 *coef = side == 0 ? st.Lf : st.Rf;
   int4 *desc = side == 0 ? st.Lm : st.Rm;
-  if (!coef || !desc) return cudaErrorNotSupported;
+  if (!coef || !desc || !status) return cudaErrorNotSupported;
   RegLaunch<12, 8> narrow;
   RegLaunch<24, 4> wide;
-  const bool use_narrow = narrow.plan(nrow, ncol);
-  if (!use_narrow && !wide.plan(nrow, ncol)) {
+  const bool use_narrow = narrow.plan(nrow, ncol, st.cap);
+  if (!use_narrow && !wide.plan(nrow, ncol, st.cap)) {
     cudaGetLastError();
     return cudaErrorNotSupported;
   }
@@ -384,8 +491,8 @@ cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const Rot
   if (st.T > 0) k_chase_descriptors<<<(st.T + 255) / 256, 256, 0, s>>>(Ca, Cn, st.T, st.cap, st.p1, desc);
   if (with_spike) k_apply_spike32<<<(nrow + 127) / 128, 128, 0, s>>>(X, ld, nrow, st.Sf, st.Sa, st.Sn);
   if (st.T > 0) {
-    if (use_narrow) narrow.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, s);
-    else wide.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, s);
+    if (use_narrow) narrow.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
+    else wide.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
   }
   return cudaGetLastError();
 }
