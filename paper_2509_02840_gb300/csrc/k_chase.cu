@@ -243,14 +243,6 @@ struct Chaser {
   __device__ __forceinline__ double *rd(int i, int j) const { return inband(i, j) ? S.cell(i, j) : zero; }
   __device__ __forceinline__ double *wr(int i, int j) const { return inband(i, j) ? S.cell(i, j) : sink; }
   __device__ __forceinline__ double get(int i, int j) const { return Store::load(rd(i, j)); }
-  __device__ __forceinline__ void store(double *p, double x) {
-    if (p == sink) {
-      if (nz(x)) atomicOr(err, ERR_BAND);
-      return;
-    }
-    *p = x;
-  }
-
   __device__ __forceinline__ void rotate_extra(double *X, int ld, int a, double c, double s) {
     for (int t = 0; t < rx; t++) {
       double *U = X + (size_t)t * ld - 1;
@@ -272,14 +264,16 @@ struct Chaser {
   // a warp runs the same instruction sequence whatever its op -- on GB300 each
   // FP64 warp instruction occupies its SM sub-partition's FP64 unit for tens of
   // cycles however many lanes are active, so lanes must share them: addresses
-  // are formed first (entries outside the band read a zero cell and write to a
-  // sink), all loads are issued together, and the rotation and the pair
-  // updates are branch-free.  Returns false (nothing written) when the entry to
+  // are formed first (entries outside the band read as zero and their new
+  // values are checked, not stored), all loads are issued together, and the
+  // rotation and the pair updates are branch-free.  Returns false (nothing written) when the entry to
   // eliminate is already zero; last receives the new value of (a, lo+w-1)
   // (rows) or (lo+w-1, a) (cols), the bulge the chase looks at next.
   __device__ __forceinline__ bool exec(bool isrows, int a, int lo, int w, int src, bool withv, Rec &recL,
                                        Rec &recR, double &last) {
+    // each cell's band test and address are formed once, for its load and its store
     double *pa[5], *pb[5];
+    bool ia[5], ib[5];  // the cell is stored (inside the band)
     double x[5], y[5];
     const bool extra = (src != 0) || withv;
 #pragma unroll
@@ -287,16 +281,22 @@ struct Chaser {
       const bool in = q < w;
       const int i0 = isrows ? a : lo + q, j0 = isrows ? lo + q : a;
       const int i1 = isrows ? a + 1 : lo + q, j1 = isrows ? lo + q : a + 1;
-      pa[q] = in ? rd(i0, j0) : zero;
-      pb[q] = in ? rd(i1, j1) : zero;
+      ia[q] = in && inband(i0, j0);
+      ib[q] = in && inband(i1, j1);
+      pa[q] = ia[q] ? S.cell(i0, j0) : zero;
+      pb[q] = ib[q] ? S.cell(i1, j1) : zero;
     }
     if (extra) {
       if (src == 1) { pa[4] = S.uptr(a); pb[4] = S.uptr(a + 1); }
       else if (src == 2) { pa[4] = S.cell(1, a); pb[4] = S.cell(1, a + 1); }
       else { pa[4] = S.vptr(a); pb[4] = S.vptr(a + 1); }
+      ia[4] = ib[4] = true;
     }
 #pragma unroll
-    for (int q = 0; q < 5; q++) { x[q] = Store::load(pa[q]); y[q] = Store::load(pb[q]); }
+    for (int q = 0; q < 5; q++) {
+      x[q] = ia[q] ? Store::load(pa[q]) : 0.0;
+      y[q] = ib[q] ? Store::load(pb[q]) : 0.0;
+    }
     const double f = src == 0 ? x[0] : x[4], g = src == 0 ? y[0] : y[4];
     double c, s, r;
     if (!A::rot(f, g, c, s, r)) return false;
@@ -307,16 +307,16 @@ struct Chaser {
     }
     if (src == 0) { x[0] = r; y[0] = 0.0; }
     else { x[4] = r; y[4] = 0.0; }
+    // a value that lands outside the band must be zero (reported otherwise)
+    bool outside = false;
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-      const bool in = q < w;
-      const int i0 = isrows ? a : lo + q, j0 = isrows ? lo + q : a;
-      const int i1 = isrows ? a + 1 : lo + q, j1 = isrows ? lo + q : a + 1;
-      double *qa = in ? wr(i0, j0) : sink, *qb = in ? wr(i1, j1) : sink;
-      if (q == 4 && extra) { qa = pa[4]; qb = pb[4]; }
-      store(qa, x[q]);
-      store(qb, y[q]);
+      if (ia[q]) *pa[q] = x[q];
+      else outside |= nz(x[q]);
+      if (ib[q]) *pb[q] = y[q];
+      else outside |= nz(y[q]);
     }
+    if (outside) atomicOr(err, ERR_BAND);
     if (isrows) {
       rotate_extra(Ux, m, a, c, s);
       recL.push(c, s, a);
