@@ -71,6 +71,13 @@ typedef struct {
   int device;         /* CUDA device ordinal (default 0) */
   int engine;         /* bulge-chase engine: 0 = by size (default), 1 = one thread block,
                          2 = a 16-block cluster; all give identical results */
+  int overlap;        /* BDU_MIXED, rank-1 updates: 1 = apply each update to Q and P on a
+                         second stream while the next update's rotations are generated.
+                         The next projection is then formed from Q, P as they were
+                         before that application and rotated by its rotations (the same
+                         quantity, rounded differently; Sec. 3.2).  Doubles the memory
+                         of the rotation records.  0 = off (default); ignored in the
+                         FP64 form and when max(m, n) exceeds about 50000. */
 } bdu_options;
 
 typedef struct {
@@ -145,6 +152,12 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P);
  * rotations; at most cap are written.  Synchronizes. */
 bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
                               int64_t cap, int64_t *count);
+
+/* Enqueues on the handle's stream every part of earlier updates that the
+ * overlapped form defers (the application of the latest rank-1 column to Q
+ * and P), so that work the caller enqueues afterwards on that stream sees the
+ * updated factors.  Does not wait on the host.  A no-op without overlap. */
+bdu_status bdu_flush(bdu_handle h);
 
 /* Statistics since creation.  Synchronizes. */
 bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out);

@@ -27,7 +27,7 @@ class BduError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("overlap", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -74,6 +74,8 @@ def load(build_if_missing: bool = True):
     L.bdu_update_dev.restype = ctypes.c_int
     L.bdu_sync.argtypes = [H]
     L.bdu_sync.restype = ctypes.c_int
+    L.bdu_flush.argtypes = [H]
+    L.bdu_flush.restype = ctypes.c_int
     L.bdu_read.argtypes = [H, dp, dp, dp, dp]
     L.bdu_read.restype = ctypes.c_int
     L.bdu_read_rotations.argtypes = [H, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int32),
@@ -170,7 +172,7 @@ class Factorization:
     """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
-                 check_every=None, engine=0):
+                 check_every=None, engine=0, overlap=False):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -181,6 +183,7 @@ class Factorization:
         opt.precision = int(precision)
         opt.device = int(device)
         opt.engine = int(engine)
+        opt.overlap = 1 if overlap else 0
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:
@@ -225,6 +228,10 @@ class Factorization:
 
     def sync(self):
         _check(self._L, self._h, self._L.bdu_sync(self._h))
+
+    def flush(self):
+        """Enqueues the deferred application of the overlapped form (bdu_flush)."""
+        _check(self._L, self._h, self._L.bdu_flush(self._h))
 
     def read(self):
         m, n = self.m, self.n

@@ -88,6 +88,15 @@ struct bdu_ctx {
   cudaEvent_t probe_ev;
   bool probe_pending;
   int64_t reorth[2];
+  // overlapped mixed form: two record buffers and two more streams
+  bool ovl;
+  RotStream stb[2];      // st == stb[cur]
+  int cur;               // buffer of the most recent rank-1 column
+  bool pend;             // that column's application to Q, P is not enqueued yet
+  bool apply_ev_set[2];
+  cudaStream_t sa;       // applications (lowest priority)
+  cudaStream_t sc;       // projections' rotation and chases (highest priority)
+  cudaEvent_t ev_call, ev_proj, ev_rot, ev_chase, ev_apply[2];
   // descriptor workspace of batched updates led by this handle
   void *batch_ws;
   size_t batch_ws_bytes;
@@ -193,19 +202,20 @@ bdu_status ensure_rank_workspace(bdu_ctx *h, int64_t r) {
 struct Timer {
   bdu_ctx *h;
   int which;
+  cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
-  Timer(bdu_ctx *hh, int w) : h(hh), which(w) {
+  Timer(bdu_ctx *hh, int w, cudaStream_t st = nullptr) : h(hh), which(w), s(st ? st : hh->stream) {
     if (!h->timing) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
       cudaGetLastError();
       a = b = nullptr;
       return;
     }
-    cudaEventRecord(a, h->stream);
+    cudaEventRecord(a, s);
   }
   ~Timer() {
     if (!a) return;
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, s);
     h->pending.push_back({a, b, which});
   }
 };
@@ -229,23 +239,70 @@ bdu_status check_device_status(bdu_ctx *h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "synchronizing the handle's stream");
   if (st & ERR_STEPS) return fail(h, BDU_ETIMEOUT, "the bulge-chase engine exceeded its step budget");
   if (st & ERR_APPLY) return fail(h, BDU_ETIMEOUT, "a bounded wait of the rotation apply ran out");
+  if (st & ERR_ROTVEC) return fail(h, BDU_ETIMEOUT, "a bounded wait of the vector rotation ran out");
+  if (st & ERR_RANGE) return fail(h, BDU_EINTERNAL, "a rotation record named a pair outside the vector");
   if (st) return fail(h, BDU_EINTERNAL, "device invariant check failed (status bits 0x%x)", st);
   return BDU_OK;
 }
 
 // Enqueues the estimate of ||X^T X - I||_2 for Q (which = 0) or P (which = 1):
 // the power iteration, then a copy of the squared estimate to *dst.
-cudaError_t enqueue_probe(bdu_ctx *h, int which, double *dst) {
+cudaError_t enqueue_probe(bdu_ctx *h, int which, double *dst, cudaStream_t s) {
   const int k = (int)(which == 0 ? h->m : h->n);
-  cudaError_t e = launch_ortho_probe(h->opt.precision, which == 0 ? h->Q : h->P, k, h->ortho_ws, 20, h->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->ortho_ws + 3 * k, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = launch_ortho_probe(h->opt.precision, which == 0 ? h->Q : h->P, k, h->ortho_ws, 20, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->ortho_ws + 3 * k, sizeof(double), cudaMemcpyDeviceToHost, s);
   return e;
+}
+
+// ---- overlapped mixed form -------------------------------------------------
+// SMs an overlapped apply leaves to the concurrent chase (its cluster).
+constexpr int kChaseSMs = 16;
+
+// Enqueues on the apply stream the application of record buffer buf to Q and
+// P, after everything enqueued so far on the handle's stream (and after the
+// event `after`, if given).  The buffer's chase descriptors are current.
+bdu_status enqueue_apply(bdu_ctx *h, int buf, int sm_reserve, cudaEvent_t after = nullptr) {
+  const int m = (int)h->m, n = (int)h->n;
+  cudaError_t e = cudaEventRecord(h->ev_call, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->sa, h->ev_call, 0);
+  if (e == cudaSuccess && after) e = cudaStreamWaitEvent(h->sa, after, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering the apply stream");
+  {
+    Timer tm(h, 2, h->sa);
+    e = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, h->sa, h->status, sm_reserve, true);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
+  }
+  {
+    Timer tm(h, 3, h->sa);
+    e = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, h->sa, h->status, sm_reserve, true);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
+  }
+  e = cudaEventRecord(h->ev_apply[buf], h->sa);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering the apply stream");
+  h->apply_ev_set[buf] = true;
+  h->launches += 2;
+  if (h->timing) h->apply_launches += 2;
+  return BDU_OK;
+}
+
+// Enqueues a deferred application, if any, and orders the handle's stream
+// after it: afterwards Q and P are current for work on that stream.
+bdu_status flush_apply(bdu_ctx *h) {
+  if (!h->ovl || !h->pend) return BDU_OK;
+  h->pend = false;
+  bdu_status st = enqueue_apply(h, h->cur, 0);
+  if (st != BDU_OK) return st;
+  cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_apply[h->cur], 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering after the apply stream");
+  return BDU_OK;
 }
 
 // The same estimate, waited for.
 bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
   double acc = 0.0;
-  cudaError_t e = enqueue_probe(h, which, &acc);
+  bdu_status fs = flush_apply(h);
+  if (fs != BDU_OK) return fs;
+  cudaError_t e = enqueue_probe(h, which, &acc, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
   *est = sqrt(acc);
@@ -284,7 +341,8 @@ bdu_status resolve_probe(bdu_ctx *h) {
     const double est = sqrt(h->probe_host[which]);
     h->ortho[which] = est;
     if (h->opt.reorth_tol > 0.0 && est > h->opt.reorth_tol) {
-      bdu_status st = reorth_factor(h, which);
+      bdu_status st = flush_apply(h);
+      if (st == BDU_OK) st = reorth_factor(h, which);
       if (st != BDU_OK) return st;
     }
   }
@@ -318,16 +376,116 @@ bdu_status maybe_reorth(bdu_ctx *h, int64_t r) {
   h->since_check += r;
   if (h->since_check < h->opt.check_every || h->probe_pending) return BDU_OK;
   h->since_check = 0;
-  cudaError_t e = enqueue_probe(h, 0, &h->probe_host[0]);
-  if (e == cudaSuccess) e = enqueue_probe(h, 1, &h->probe_host[1]);
-  if (e == cudaSuccess) e = cudaEventRecord(h->probe_ev, h->stream);
+  // overlapped with an application deferred: on the apply stream, behind the
+  // latest enqueued application and everything on the handle's stream
+  const cudaStream_t ps = (h->ovl && h->pend) ? h->sa : h->stream;
+  cudaError_t e = cudaSuccess;
+  if (ps != h->stream) {
+    e = cudaEventRecord(h->ev_call, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, h->ev_call, 0);
+  }
+  if (e == cudaSuccess) e = enqueue_probe(h, 0, &h->probe_host[0], ps);
+  if (e == cudaSuccess) e = enqueue_probe(h, 1, &h->probe_host[1], ps);
+  if (e == cudaSuccess) e = cudaEventRecord(h->probe_ev, ps);
   if (e != cudaSuccess) return cuda_fail(h, e, "orthogonality probe");
   h->probe_pending = true;
   return BDU_OK;
 }
 
+// One overlapped rank-1 update (mixed form).  Streams: the handle's stream s
+// (the caller's order), the chase stream sc and the apply stream sa.  With the
+// previous column's application still deferred: on sa, project b and c with
+// Q and P as they are before it; on sc, rotate the projections by that
+// column's rotations (u = G^T Q^T b, v = H^T P^T c), then run this column's
+// chase into the other record buffer; on sa, the previous column's
+// application starts once the rotation is done, so that it runs beside the
+// chase, which has the higher priority and is placed first.  s waits for the
+// chase; this column's application is deferred in turn.
+bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
+  const int m = (int)h->m, n = (int)h->n;
+  cudaStream_t s = h->stream, sa = h->sa, sc = h->sc;
+  BandPtrs bp = band_ptrs(h->band, m, n);
+  cudaError_t e = cudaEventRecord(h->ev_call, s);  // the previous chase and this update's inputs
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, h->ev_call, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering the chase stream");
+  if (h->timing) {
+    h->timed_updates += 1;
+    if (h->pending.size() > 4096) resolve_timers(h);
+  }
+  // this column's record buffer: free once the application two columns back
+  // is done; cleared before the rotation, so that the chase follows it directly
+  const int buf = h->pend ? (h->cur ^ 1) : h->cur;
+  if (h->apply_ev_set[buf]) e = cudaStreamWaitEvent(sc, h->ev_apply[buf], 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->stb[buf].Ln, 0, sizeof(int32_t) * h->st.T, sc);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->stb[buf].Rn, 0, sizeof(int32_t) * h->st.T, sc);
+  if (e != cudaSuccess) return cuda_fail(h, e, "staging a rank-1 column");
+  if (h->pend) {
+    const int prev = h->cur;
+    e = cudaStreamWaitEvent(sa, h->ev_call, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ordering the apply stream");
+    {
+      Timer tm(h, 0, sa);
+      e = launch_project_nz(h->opt.precision, h->Q, m, m, m, dB, m, 1, h->U, m, h->nzB, sa);
+      if (e == cudaSuccess) e = launch_project_nz(h->opt.precision, h->P, n, n, n, dC, n, 1, h->V, n, h->nzC, sa);
+      if (e != cudaSuccess) return cuda_fail(h, e, "projection of b, c");
+    }
+    e = cudaEventRecord(h->ev_proj, sa);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, h->ev_proj, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ordering after the projection");
+    {
+      Timer tm(h, 0, sc);
+      e = launch_rotate_vectors(h->U, bp.u + 1, m, h->V, bp.v + 1, n, h->stb[prev], m > n, h->status, sc);
+      if (e != cudaSuccess) return cuda_fail(h, e, "rotating the projections");
+    }
+    e = cudaEventRecord(h->ev_rot, sc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ordering after the rotation");
+    h->pend = false;
+    bdu_status st = enqueue_apply(h, prev, kChaseSMs, h->ev_rot);
+    if (st != BDU_OK) return st;
+    h->launches += 5;
+  } else {
+    {
+      Timer tm(h, 0, sc);
+      e = launch_project_nz(h->opt.precision, h->Q, m, m, m, dB, m, 1, h->U, m, h->nzB, sc);
+      if (e == cudaSuccess) e = launch_project_nz(h->opt.precision, h->P, n, n, n, dC, n, 1, h->V, n, h->nzC, sc);
+      if (e != cudaSuccess) return cuda_fail(h, e, "projection of b, c");
+    }
+    e = cudaMemcpyAsync(bp.u + 1, h->U, sizeof(double) * m, cudaMemcpyDeviceToDevice, sc);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bp.v + 1, h->V, sizeof(double) * n, cudaMemcpyDeviceToDevice, sc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "staging a rank-1 column");
+    h->launches += 4;
+  }
+  h->cur = buf;
+  h->st = h->stb[buf];
+  ChaseArgs a{};
+  a.m = m; a.n = n; a.band = bp;
+  a.rx = 0; a.Ux = nullptr; a.Vx = nullptr;
+  a.st = h->st; a.status = h->status; a.counters = h->counters;
+  a.fast = 1;
+  a.engine = h->opt.engine;
+  {
+    Timer tm(h, 1, sc);
+    e = launch_chase(a, sc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+  }
+  // descriptors of this column's chases, for its application and for the
+  // next column's vector rotation
+  e = launch_chase_descriptors(h->st, 0, sc);
+  if (e == cudaSuccess) e = launch_chase_descriptors(h->st, 1, sc);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_chase, sc);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_chase, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "chase descriptors");
+  h->launches += 3;
+  h->pend = true;
+  h->updates++;
+  return maybe_reorth(h, 1);
+}
+
 // One update with B, C already in device memory.
 bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
+  if (h->ovl && r == 1) return run_overlapped(h, dB, dC);
+  bdu_status fs = flush_apply(h);
+  if (fs != BDU_OK) return fs;
   const int m = (int)h->m, n = (int)h->n;
   cudaStream_t s = h->stream;
   cudaError_t e;
@@ -384,6 +542,36 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   return maybe_reorth(h, r);
 }
 
+// Allocates one buffer of rotation records (and the mixed form's FP32 copies
+// and chase descriptors); false if an allocation failed.  Padded: the kernels
+// that stream records read whole 16-byte units.
+bool alloc_records(bdu_ctx *h, RotStream &r, int T, int cap, int64_t m, bool mixed) {
+  const size_t tc = (size_t)T * cap;
+  r.T = T; r.cap = cap; r.p1 = (int)(h->N - 1);
+  r.Lc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  r.Ls = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  r.Rc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  r.Rs = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  r.La = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tc + 4));
+  r.Ra = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tc + 4));
+  r.Ln = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
+  r.Rn = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
+  r.Sc = (double *)dev_alloc(h, sizeof(double) * (m + 1));
+  r.Ss = (double *)dev_alloc(h, sizeof(double) * (m + 1));
+  r.Sa = (int32_t *)dev_alloc(h, sizeof(int32_t) * (m + 1));
+  r.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
+  bool ok = r.Lc && r.Ls && r.Rc && r.Rs && r.La && r.Ra && r.Ln && r.Rn && r.Sc && r.Ss && r.Sa && r.Sn;
+  if (mixed) {
+    r.Lf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
+    r.Rf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
+    r.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
+    r.Lm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
+    r.Rm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
+    ok = ok && r.Lf && r.Rf && r.Sf && r.Lm && r.Rm;
+  }
+  return ok;
+}
+
 struct BatchGuard {
   std::vector<bdu_ctx *> held;
   ~BatchGuard() {
@@ -404,6 +592,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->cuda_stream = nullptr;
   opt->device = 0;
   opt->engine = 0;
+  opt->overlap = 0;
 }
 
 int bdu_version(void) { return 100; }
@@ -420,9 +609,15 @@ void bdu_destroy(bdu_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->sa) cudaStreamSynchronize(h->sa);
+  if (h->sc) cudaStreamSynchronize(h->sc);
   resolve_timers(h);
   if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
   if (h->probe_ev) cudaEventDestroy(h->probe_ev);
+  for (cudaEvent_t ev : {h->ev_call, h->ev_proj, h->ev_rot, h->ev_chase, h->ev_apply[0], h->ev_apply[1]})
+    if (ev) cudaEventDestroy(ev);
+  if (h->sa) cudaStreamDestroy(h->sa);
+  if (h->sc) cudaStreamDestroy(h->sc);
   if (h->probe_host) cudaFreeHost(h->probe_host);
   for (void *p : h->blocks) h->al.put(p);
   h->blocks.clear();
@@ -473,34 +668,40 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   }
   const size_t es = esize(h);
   const int T = num_tasks(m, n), cap = task_cap(n);
-  const size_t tc = (size_t)T * cap;
   h->Q = dev_alloc(h, es * m * m);
   h->P = dev_alloc(h, es * n * n);
   h->band = (double *)dev_alloc(h, sizeof(double) * band_doubles(m, n));
-  h->st.T = T; h->st.cap = cap; h->st.p1 = (int)(h->N - 1);
-  h->st.Lc = (double *)dev_alloc(h, sizeof(double) * tc);
-  h->st.Ls = (double *)dev_alloc(h, sizeof(double) * tc);
-  h->st.Rc = (double *)dev_alloc(h, sizeof(double) * tc);
-  h->st.Rs = (double *)dev_alloc(h, sizeof(double) * tc);
-  h->st.La = (int32_t *)dev_alloc(h, sizeof(int32_t) * tc);
-  h->st.Ra = (int32_t *)dev_alloc(h, sizeof(int32_t) * tc);
-  h->st.Ln = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
-  h->st.Rn = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
-  h->st.Sc = (double *)dev_alloc(h, sizeof(double) * (m + 1));
-  h->st.Ss = (double *)dev_alloc(h, sizeof(double) * (m + 1));
-  h->st.Sa = (int32_t *)dev_alloc(h, sizeof(int32_t) * (m + 1));
-  h->st.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
+  const bool mixed = o.precision == BDU_MIXED;
+  bool rec_ok = alloc_records(h, h->st, T, cap, m, mixed);
+  h->ovl = mixed && o.overlap != 0 && rotate_vectors_supported((int)m, (int)n);
+  if (h->ovl) {
+    h->stb[0] = h->st;
+    rec_ok = rec_ok && alloc_records(h, h->stb[1], T, cap, m, mixed);
+    // The chase's thread-block cluster needs 16 free SMs of one GPC: its
+    // stream outranks the application's, so that when both become ready the
+    // chase is placed first and the application fills the other SMs.
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (cudaStreamCreateWithPriority(&h->sa, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->sc, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_call, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_proj, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_rot, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_chase, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_apply[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_apply[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      fail(nullptr, BDU_ENOMEM, "bdu_create: stream or event creation failed");
+      bdu_destroy(h);
+      return BDU_ENOMEM;
+    }
+  }
   h->status = (int *)dev_alloc(h, sizeof(int) * 4);
   h->counters = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long) * 16);
   h->ortho[0] = h->ortho[1] = -1.0;
   h->ortho_ws = (double *)dev_alloc(h, sizeof(double) * (3 * m + 8));
   if (o.precision == BDU_MIXED) {
     h->scratch64 = (double *)dev_alloc(h, sizeof(double) * m * m);
-    h->st.Lf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
-    h->st.Rf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
-    h->st.Sf = (float2 *)dev_alloc(h, sizeof(float2) * (m + 1));
-    h->st.Lm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
-    h->st.Rm = (int4 *)dev_alloc(h, sizeof(int4) * (T + 1));
     if (cudaHostAlloc((void **)&h->probe_host, 2 * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->probe_ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
@@ -509,10 +710,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
       return BDU_ENOMEM;
     }
   }
-  bool ok = h->Q && h->P && h->band && h->st.Lc && h->st.Ls && h->st.Rc && h->st.Rs && h->st.La &&
-            h->st.Ra && h->st.Ln && h->st.Rn && h->st.Sc && h->st.Ss && h->st.Sa && h->st.Sn &&
-            h->status && h->counters && h->ortho_ws &&
-            (o.precision == BDU_FP64 || (h->scratch64 && h->st.Lf && h->st.Rf && h->st.Sf && h->st.Lm && h->st.Rm));
+  bool ok = h->Q && h->P && h->band && rec_ok && h->status && h->counters && h->ortho_ws &&
+            (o.precision == BDU_FP64 || h->scratch64);
   if (!ok) {
     fail(nullptr, BDU_ENOMEM, "bdu_create: device allocation failed (m=%lld n=%lld)", (long long)m, (long long)n);
     bdu_destroy(h);
@@ -616,6 +815,10 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
   const int precision = h0->opt.precision;
   cudaError_t ce = cudaSetDevice(h0->device);
   if (ce != cudaSuccess) return cuda_fail(h0, ce, "cudaSetDevice");
+  for (int i = 0; i < count; i++) {
+    bdu_status fs = flush_apply(hs[i]);
+    if (fs != BDU_OK) return fs;
+  }
   cudaStream_t s = stream ? (cudaStream_t)stream : h0->stream;
   int64_t max_r = 0;
   for (int i = 0; i < count; i++) {
@@ -746,8 +949,18 @@ bdu_status bdu_sync(bdu_handle h) {
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
   cudaSetDevice(h->device);
-  bdu_status st = settle_probe(h);
+  bdu_status st = flush_apply(h);
+  if (st == BDU_OK) st = settle_probe(h);
   return st != BDU_OK ? st : check_device_status(h);
+}
+
+bdu_status bdu_flush(bdu_handle h) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure");
+  cudaSetDevice(h->device);
+  return flush_apply(h);
 }
 
 bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
@@ -756,7 +969,8 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   cudaSetDevice(h->device);
   bdu_status st = BDU_OK;
-  if (!h->poisoned) st = settle_probe(h);
+  if (!h->poisoned && (Q || P)) st = flush_apply(h);  // d and e are current without it
+  if (st == BDU_OK && !h->poisoned) st = settle_probe(h);
   if (st == BDU_OK && !h->poisoned) st = check_device_status(h);
   const int64_t m = h->m, n = h->n;
   cudaError_t ce = cudaSuccess;

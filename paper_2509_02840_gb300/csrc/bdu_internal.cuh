@@ -14,6 +14,8 @@ enum : int {
   ERR_STEPS = 4,     // the chase engine exceeded its step budget (no progress)
   ERR_SCHEDULE = 8,  // an op found a zero where the schedule guarantees a nonzero
   ERR_APPLY = 16,    // a bounded wait of the register-resident apply ran out
+  ERR_ROTVEC = 32,   // a bounded wait of the vector rotation ran out
+  ERR_RANGE = 64,    // a record named a pair outside the vector (skipped)
 };
 
 // The working core M = band + u v^T of one rank-1 step, in global memory.
@@ -109,15 +111,22 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 
 // status: the device error word (needed by the register-resident FP32 path;
 // null selects the shared-memory slab kernel).
+// sm_reserve: SMs the register-resident path leaves free (for a chase that
+// runs concurrently); desc_ready: the chase descriptors of st are current.
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s,
-                         int *status = nullptr);
+                         int *status = nullptr, int sm_reserve = 0, bool desc_ready = false);
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);
 void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, int *status, cudaStream_t s);
+                             bool with_spike, int *status, int sm_reserve, bool desc_ready, cudaStream_t s);
+cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t s);
+bool rotate_vectors_supported(int m, int n);
+cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,
+                                  double *dst_right, int n, const RotStream &st, bool with_spike, int *status,
+                                  cudaStream_t s);
 cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
                                int total_slabs, size_t smem, cudaStream_t s);
 cudaError_t launch_project_batch(int precision, const ProjItem *d_items, int count, int max_nrow,

@@ -246,10 +246,12 @@ cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const in
 }
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
-                         const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status) {
+                         const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status,
+                         int sm_reserve, bool desc_ready) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
   if (precision == BDU_MIXED) {
-    const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, s);
+    const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, sm_reserve,
+                                           desc_ready, s);
     if (e != cudaErrorNotSupported) return e;
   }
   int dev = 0, optin = 0, sms = 1;

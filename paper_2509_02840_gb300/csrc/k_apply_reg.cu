@@ -443,7 +443,7 @@ struct RegLaunch {
   Layout L{};
   // Geometry for an nrow x ncol matrix with record slots of cap; false when
   // it is not covered.
-  bool plan(int nrow, int ncol, int cap) {
+  bool plan(int nrow, int ncol, int cap, int sm_reserve) {
     const int nwc = ((ncol + W - 1) / W + 31) / 32;
     if (nwc * 32 > kMaxCompute) return false;
     nth = nwc * 32 + 32;
@@ -458,8 +458,9 @@ struct RegLaunch {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_reg<W, V>, nth, L.total) != cudaSuccess ||
         per_sm < 1)
       return false;
+    const int usable = sms - sm_reserve > 0 ? sms - sm_reserve : 1;
     const int groups = (nrow + V - 1) / V;
-    grid = groups < per_sm * sms ? groups : per_sm * sms;
+    grid = groups < per_sm * usable ? groups : per_sm * usable;
     return true;
   }
   void launch(float *X, int64_t ld, int nrow, int ncol, const float2 *coef, const int32_t *Ca, const int4 *desc,
@@ -470,25 +471,35 @@ struct RegLaunch {
 
 }  // namespace
 
+// Per-chase descriptors of one side of st (see k_chase_descriptors).
+cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t s) {
+  int4 *desc = side == 0 ? st.Lm : st.Rm;
+  if (!desc || st.T <= 0) return cudaSuccess;
+  k_chase_descriptors<<<(st.T + 255) / 256, 256, 0, s>>>(side == 0 ? st.La : st.Ra, side == 0 ? st.Ln : st.Rn,
+                                                           st.T, st.cap, st.p1, desc);
+  return cudaGetLastError();
+}
+
 // Register-resident FP32 apply; cudaErrorNotSupported, before anything is
 // launched, when the shape or the stream is not covered (the caller then uses
 // the shared-memory slab kernel).  Records are copied in 16-byte units up to
 // one entry past the last chase's slot, so Lf and Rf hold T*cap + 2 entries.
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, int *status, cudaStream_t s) {
+                             bool with_spike, int *status, int sm_reserve, bool desc_ready, cudaStream_t s) {
   const float2 *coef = side == 0 ? st.Lf : st.Rf;
   int4 *desc = side == 0 ? st.Lm : st.Rm;
   if (!coef || !desc || !status) return cudaErrorNotSupported;
   RegLaunch<12, 8> narrow;
   RegLaunch<24, 4> wide;
-  const bool use_narrow = narrow.plan(nrow, ncol, st.cap);
-  if (!use_narrow && !wide.plan(nrow, ncol, st.cap)) {
+  const bool use_narrow = narrow.plan(nrow, ncol, st.cap, sm_reserve);
+  if (!use_narrow && !wide.plan(nrow, ncol, st.cap, sm_reserve)) {
     cudaGetLastError();
     return cudaErrorNotSupported;
   }
   const int32_t *Ca = side == 0 ? st.La : st.Ra;
   const int32_t *Cn = side == 0 ? st.Ln : st.Rn;
-  if (st.T > 0) k_chase_descriptors<<<(st.T + 255) / 256, 256, 0, s>>>(Ca, Cn, st.T, st.cap, st.p1, desc);
+  if (st.T > 0 && !desc_ready)
+    k_chase_descriptors<<<(st.T + 255) / 256, 256, 0, s>>>(Ca, Cn, st.T, st.cap, st.p1, desc);
   if (with_spike) k_apply_spike32<<<(nrow + 127) / 128, 128, 0, s>>>(X, ld, nrow, st.Sf, st.Sa, st.Sn);
   if (st.T > 0) {
     if (use_narrow) narrow.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);

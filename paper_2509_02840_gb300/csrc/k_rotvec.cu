@@ -1,0 +1,233 @@
+// Rotation of projected vectors by a finished rotation stream, for the
+// overlapped mixed form.
+//
+// After rank-1 column j-1 has generated its rotations G (left) and H (right),
+// Q_j = Q_{j-1} G and P_j = P_{j-1} H (Sec. 3.2, Eq. bidiagplus), so the
+// projections of the next column satisfy u_j = Q_j^T b = G^T (Q_{j-1}^T b) and
+// v_j = H^T (P_{j-1}^T c).  They can therefore be formed from the factors as
+// they were before column j-1 was applied, and then rotated here: a rotation
+// of columns (a, a+1) of Q acts on entries (a, a+1) of Q^T b exactly as on the
+// two entries of one row of Q.  This lets the application of column j-1 to Q
+// and P run concurrently with the chase of column j.
+//
+// One block per side; the vector sits in shared memory.  The spike chain
+// (left side, m > n) is sequential: its records are staged in shared memory a
+// chunk at a time and one thread runs through them.  The chases' rotations
+// then come as the FP32 coefficients the apply uses and the per-chase
+// descriptors: a producer warp cuts each chase into chunks of up to kRecs
+// records and streams them into a ring of shared-memory slots with bulk copies
+// (full/empty mbarriers, bounded waits), so that many copies are in flight at
+// once; the compute threads apply a chunk's rotations, which act on disjoint
+// pairs, all at once, and meet at a barrier only where a chase ends.  A pair's
+// first column comes from the chase's progression (first + step * index), or
+// from the recorded positions for a chase with a gap.
+//
+// Arithmetic: FP32 with fused multiply-adds, the operations the mixed form
+// applies to the rows of Q and P with the same coefficients -- so u = G^T w
+// carries the rounding that Q_j^T b carries when Q_j is rotated in FP32.  (In
+// FP64 the rotations would be bound by one SM's FP64 rate: about 4 x 12.5M
+// operations per side at n = 4096, some 12 ms.)
+#include "async_copy.cuh"
+#include "bdu_internal.cuh"
+
+namespace bdu {
+namespace {
+
+constexpr int kCompute = 512;            // compute threads
+constexpr int kThreads = kCompute + 32;  // + the producer warp
+constexpr int kRecs = 512;               // records per chunk
+constexpr int kSpike = 512;              // spike records staged at a time
+constexpr size_t kSmemBudget = 220 * 1024;
+constexpr size_t kSlot = 16 + (kRecs + 2) * 8;  // header + coefficients (from a 16-byte boundary)
+
+__device__ __forceinline__ void rot32(float c, float s, float &x, float &y) {
+  const float xo = x, yo = y;
+  x = fmaf(c, xo, s * yo);
+  y = fmaf(c, yo, -s * xo);
+}
+
+__host__ __device__ inline size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+constexpr size_t kStaging = 16 * ((kSpike * 4 + 15) / 16) + kSpike * 8;
+
+// Shared memory: the vector, full[R] and empty[R], then R chunk slots (the
+// spike's staging area before they are used).
+struct RvLayout {
+  int R, rmask, rshift;
+  size_t vec, full, empty, ring, total;
+  bool make(int len) {
+    vec = round16((size_t)len * 4);
+    R = 0;
+    for (int r = 32, sh = 5; r >= 4; r >>= 1, sh--) {
+      const size_t ring_b = (size_t)r * kSlot > kStaging ? (size_t)r * kSlot : kStaging;
+      const size_t tot = vec + 16 * r + ring_b;
+      if (tot <= kSmemBudget) {
+        R = r; rmask = r - 1; rshift = sh;
+        full = vec;
+        empty = full + 8 * r;
+        ring = empty + 8 * r;
+        total = tot;
+        return true;
+      }
+    }
+    return false;
+  }
+};
+
+// Chunk header: x = index within its chase of the chunk's first record;
+// y = count | last << 10 | gap << 11 | shift << 12 | stop << 13;
+// z = first column of the chase's first pair; w = step, or for a chase with a
+// gap the index of its first record in the record arrays.
+constexpr int kLast = 1 << 10, kGap = 1 << 11, kShift = 1 << 12, kStop = 1 << 13;
+
+// blockIdx.x = 0: w_left (m entries) by the left stream into dst_left;
+//              1: w_right (n entries) by the right stream into dst_right.
+__global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *__restrict__ w_left,
+                                                             double *__restrict__ dst_left, int m,
+                                                             const double *__restrict__ w_right,
+                                                             double *__restrict__ dst_right, int n,
+                                                             RotStream st, int with_spike, RvLayout L,
+                                                             int *__restrict__ status) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  const bool left = blockIdx.x == 0;
+  const int len = left ? m : n;
+  const int tid = threadIdx.x;
+  const double *w = left ? w_left : w_right;
+  double *dst = left ? dst_left : dst_right;
+  float *v = reinterpret_cast<float *>(raw);
+  uint64_t *full = reinterpret_cast<uint64_t *>(raw + L.full);
+  uint64_t *empty = reinterpret_cast<uint64_t *>(raw + L.empty);
+  for (int i = tid; i < len; i += blockDim.x) v[i] = (float)w[i];
+  if (tid == 0) {
+    for (int q = 0; q < L.R; q++) {
+      async::mbar_init(&full[q], 1);
+      async::mbar_init(&empty[q], kCompute / 32);
+    }
+    async::mbar_init_fence();
+  }
+  __syncthreads();
+  if (left && with_spike) {
+    // staged in the ring, before the producer starts
+    int *sa = reinterpret_cast<int *>(raw + L.ring);
+    float2 *sg = reinterpret_cast<float2 *>(raw + L.ring + round16((size_t)kSpike * 4));
+    const int ns = st.Sn[0];
+    for (int e0 = 0; e0 < ns; e0 += kSpike) {
+      const int k = min(kSpike, ns - e0);
+      for (int i = tid; i < k; i += blockDim.x) {
+        sa[i] = st.Sa[e0 + i] - 1;
+        sg[i] = st.Sf[e0 + i];
+      }
+      __syncthreads();
+      if (tid == 0)
+        for (int i = 0; i < k; i++) {
+          if (sa[i] < 0 || sa[i] + 1 >= len) { atomicOr(status, ERR_RANGE); continue; }
+          rot32(sg[i].x, sg[i].y, v[sa[i]], v[sa[i] + 1]);
+        }
+      __syncthreads();
+    }
+  }
+  const int32_t *Ca = left ? st.La : st.Ra;
+  const float2 *Cf = left ? st.Lf : st.Rf;
+  const int4 *desc = left ? st.Lm : st.Rm;
+  const int cap = st.cap, T = st.T;
+
+  if (tid >= kCompute) {
+    // ---- producer warp: descriptors 32 at a time, one bulk copy per chunk
+    const int lane = tid - kCompute;
+    int q = 0;  // chunks issued
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int4 mine = (t0 + lane < T) ? desc[t0 + lane] : make_int4(0, 7 << 24, 0, 0);
+      for (int i = 0; i < 32 && t0 + i < T; i++) {
+        const int dy = __shfl_sync(0xffffffffu, mine.y, i);
+        const int dz = __shfl_sync(0xffffffffu, mine.z, i);
+        const int cnt = dy & 0xffffff, code = dy >> 24;
+        if (cnt == 0 || code == 7) continue;  // uniform across the warp
+        const int t = t0 + i;
+        const bool gap = code == 5;
+        const int step = code < 2 ? 2 : 3;
+        if (lane == 0) {
+          for (int e0 = 0; e0 < cnt; e0 += kRecs, q++) {
+            const int k = min(kRecs, cnt - e0);
+            const int s = q & L.rmask;
+            if (q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1)))
+              atomicOr(status, ERR_ROTVEC);
+            unsigned char *slot = raw + L.ring + (size_t)s * kSlot;
+            const size_t first = (size_t)t * cap + e0;
+            const int sh = (int)(first & 1);
+            const unsigned bytes = (unsigned)(((sh + k + 1) / 2) * 16);
+            const int flags = k | (e0 + k == cnt ? kLast : 0) | (gap ? kGap : 0) | (sh ? kShift : 0);
+            *reinterpret_cast<int4 *>(slot) = make_int4(e0, flags, dz, gap ? t * cap : step);
+            async::mbar_arrive_tx(&full[s], bytes);
+            async::bulk_g2s(slot + 16, Cf + (first - sh), bytes, &full[s]);
+          }
+        }
+        q = __shfl_sync(0xffffffffu, q, 0);
+      }
+    }
+    if (lane == 0) {
+      // the end marker, then the last copies have landed before the block may exit
+      const int s = q & L.rmask;
+      if (q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1)))
+        atomicOr(status, ERR_ROTVEC);
+      *reinterpret_cast<int4 *>(raw + L.ring + (size_t)s * kSlot) = make_int4(0, kStop, 0, 0);
+      async::mbar_arrive_tx(&full[s], 0u);
+      // (chunk q - R shared its slot with the end marker: it was consumed before)
+      for (int p = q - L.R + 1 > 0 ? q - L.R + 1 : 0; p < q; p++)
+        if (!async::mbar_wait(&full[p & L.rmask], (unsigned)((p >> L.rshift) & 1))) atomicOr(status, ERR_ROTVEC);
+    }
+    return;
+  }
+
+  // ---- compute threads
+  for (int q = 0;; q++) {
+    const int s = q & L.rmask;
+    if (!async::mbar_wait(&full[s], (unsigned)((q >> L.rshift) & 1))) {
+      atomicOr(status, ERR_ROTVEC);
+      break;
+    }
+    const unsigned char *slot = raw + L.ring + (size_t)s * kSlot;
+    const int4 hd = *reinterpret_cast<const int4 *>(slot);
+    if (hd.y & kStop) break;
+    const int k = hd.y & 1023;
+    const float2 *cf = reinterpret_cast<const float2 *>(slot + 16) + ((hd.y & kShift) ? 1 : 0);
+    if (tid < k) {
+      const int ri = hd.x + tid;  // index of the record within its chase
+      const int a = (hd.y & kGap) ? Ca[(size_t)hd.w + ri] - 1 : hd.z + hd.w * ri;
+      const float2 g = cf[tid];
+      if (a >= 0 && a + 1 < len) rot32(g.x, g.y, v[a], v[a + 1]);
+      else atomicOr(status, ERR_RANGE);
+    }
+    if (hd.y & kLast) async::named_sync(1, kCompute);  // the chase done by all: its values visible
+    __syncwarp();
+    if ((tid & 31) == 0) async::mbar_arrive(&empty[s]);
+  }
+  async::named_sync(1, kCompute);
+  for (int i = tid; i < len; i += kCompute) dst[i] = (double)v[i];
+}
+
+}  // namespace
+
+// Whether the vector rotation of an m x n factorization fits one block's
+// shared memory.
+bool rotate_vectors_supported(int m, int n) {
+  RvLayout L{};
+  return L.make(m > n ? m : n);
+}
+
+// dst_left = G^T w_left (m entries), dst_right = H^T w_right (n entries) for
+// the rotation stream st, whose chase descriptors (Lm, Rm) are current;
+// with_spike when the left stream starts with a spike chain (m > n).  The
+// FP32 coefficients are read in 16-byte units, up to one entry past the last
+// chase's slot (Lf, Rf hold T*cap + 2 entries).
+cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,
+                                  double *dst_right, int n, const RotStream &st, bool with_spike, int *status,
+                                  cudaStream_t s) {
+  RvLayout L{};
+  if (!st.Lf || !st.Rf || !st.Sf || !st.Lm || !st.Rm || !L.make(m > n ? m : n)) return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(k_rotate_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  k_rotate_vectors<<<2, kThreads, L.total, s>>>(w_left, dst_left, m, w_right, dst_right, n, st, with_spike ? 1 : 0,
+                                               L, status);
+  return cudaGetLastError();
+}
+
+}  // namespace bdu
