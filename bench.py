@@ -148,9 +148,12 @@ ALU_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # (Sec. 3.4), plus the rotation itself (2 multiplications, 1 addition, 1 square
 # root, 2 divisions counted as one flop each).
 CHASE_FLOPS_PER_ROTATION = 26
+# DRAM bytes (read + write) of one mixed-form chase launch at m = n = 4096, from one
+# ncu capture (profiles/launches_recommender_4096.md): the rotation records written.
+CHASE_TRAFFIC_4096 = 13.6e6 + 652.0e6
 
 
-def roofline(st, precision, rotations_per_update, launches_per_update):
+def roofline(st, precision, rotations_per_update, launches_per_update, steps_per_update=None):
     """Roofline object of the dominant kernel group of one update."""
     ms = {"chase": st["ms_chase"], "apply": st["ms_apply_q"] + st["ms_apply_p"], "project": st["ms_project"]}
     nup = max(st["timed_updates"], 1)
@@ -159,10 +162,16 @@ def roofline(st, precision, rotations_per_update, launches_per_update):
         per_launch_ms = ms["chase"] / nup
         flops = CHASE_FLOPS_PER_ROTATION * rotations_per_update
         ach = flops / (per_launch_ms * 1e-3) / 1e12
-        return {"kernel": "k_chase (FP64 rotation generation + bulge chase)", "bound": "alu",
-                "achieved": ach, "peak": ALU_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP64_TFLOPS,
-                "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
-                "share": ms["chase"] / sum(ms.values())}
+        out = {"kernel": "k_chase (FP64 rotation generation + bulge chase)", "bound": "alu",
+               "achieved": ach, "peak": ALU_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP64_TFLOPS,
+               "traffic": CHASE_TRAFFIC_4096 if (M == N == 4096 and precision == 1) else None,
+               "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
+               "share": ms["chase"] / sum(ms.values())}
+        if steps_per_update:
+            # the kernel is bound by its chain of dependent steps, not by a throughput
+            out["critical_path"] = {"steps_per_launch": steps_per_update,
+                                    "us_per_step": per_launch_ms * 1e3 / steps_per_update}
+        return out
     # apply: algorithmic bytes = one read + one write of Q and P per rank-1 column
     es = 8 if precision == 0 else 4
     per_launch_ms = ms["apply"] / max(st["apply_launches"], 1)
@@ -326,7 +335,7 @@ def run_gpu(args):
     st = Fm.stats()
     rot_per_update = (sum(st["rot_left"]) + sum(st["rot_right"]) - sum(st0["rot_left"]) - sum(st0["rot_right"])) / K
     launches = (st["launches"] - st0["launches"])
-    roof = roofline(st, 1, rot_per_update, launches / K)
+    roof = roofline(st, 1, rot_per_update, launches / K, (st["chase_steps"] - st0["chase_steps"]) / K)
     res_mixed = residual(Fm, (Q, d, e, P), ups[:W + K])
 
     if args.quick:
