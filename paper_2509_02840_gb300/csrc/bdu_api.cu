@@ -97,7 +97,9 @@ struct bdu_ctx {
   cudaStream_t sa;       // applications (lowest priority)
   cudaStream_t sc;       // projections' rotation and chases (highest priority)
   cudaEvent_t ev_call, ev_proj, ev_rot, ev_chase, ev_apply[2];
-  // descriptor workspace of batched updates led by this handle
+  // descriptor workspace of batched updates led by this handle, and a second
+  // stream on which their small items' chases run beside the large ones'
+  cudaStream_t batch_aux;
   void *batch_ws;
   size_t batch_ws_bytes;
   // bookkeeping
@@ -611,12 +613,14 @@ void bdu_destroy(bdu_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->sa) cudaStreamSynchronize(h->sa);
   if (h->sc) cudaStreamSynchronize(h->sc);
+  if (h->batch_aux) cudaStreamSynchronize(h->batch_aux);
   resolve_timers(h);
   if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
   if (h->probe_ev) cudaEventDestroy(h->probe_ev);
   for (cudaEvent_t ev : {h->ev_call, h->ev_proj, h->ev_rot, h->ev_chase, h->ev_apply[0], h->ev_apply[1]})
     if (ev) cudaEventDestroy(ev);
   if (h->sa) cudaStreamDestroy(h->sa);
+  if (h->batch_aux) cudaStreamDestroy(h->batch_aux);
   if (h->sc) cudaStreamDestroy(h->sc);
   if (h->probe_host) cudaFreeHost(h->probe_host);
   for (void *p : h->blocks) h->al.put(p);
@@ -872,12 +876,17 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int esz = precision == BDU_FP64 ? 8 : 4;
+  if (!h0->batch_aux && cudaStreamCreateWithFlags(&h0->batch_aux, cudaStreamNonBlocking) != cudaSuccess) {
+    h0->batch_aux = nullptr;
+    return cuda_fail(h0, cudaGetLastError(), "creating the batch stream");
+  }
   for (int64_t k = 0; k < max_r; k++) {
-    std::vector<ChaseArgs> chase;
-    std::vector<const double *> cols;  // u columns then v columns
+    // small items (one thread block each) first, then large ones (a cluster each)
+    std::vector<ChaseArgs> chase_s, chase_l;
+    std::vector<const double *> ucol_s, ucol_l, vcol_s, vcol_l;
     std::vector<ApplyItem> apply;
     std::vector<int> first;
-    int max_n = 0, max_band = 0, slabs = 0;
+    int max_n = 0, max_n_l = 0, max_band = 0, slabs = 0;
     size_t smem = 0;
     for (int i = 0; i < count; i++) {
       if (r[i] <= k) continue;
@@ -890,11 +899,20 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
       a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
       a.st = h->st; a.status = h->status; a.counters = h->counters;
       a.fast = precision == BDU_MIXED ? 1 : 0;
-      a.engine = 1;
-      chase.push_back(a);
-      cols.push_back(h->U + k * m);
-      if (n > max_n) max_n = n;
-      if ((int)band_doubles(m, n) > max_band) max_band = (int)band_doubles(m, n);
+      if (n >= kClusterBatchMinN) {
+        a.engine = 2;
+        chase_l.push_back(a);
+        ucol_l.push_back(h->U + k * m);
+        vcol_l.push_back(h->V + k * n);
+        if (n > max_n_l) max_n_l = n;
+      } else {
+        a.engine = 1;
+        chase_s.push_back(a);
+        ucol_s.push_back(h->U + k * m);
+        vcol_s.push_back(h->V + k * n);
+        if (n > max_n) max_n = n;
+        if ((int)band_doubles(m, n) > max_band) max_band = (int)band_doubles(m, n);
+      }
       for (int side = 0; side < 2; side++) {
         ApplyItem it{};
         it.X = side == 0 ? h->Q : h->P;
@@ -912,16 +930,37 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
         apply.push_back(it);
       }
     }
-    const int nact = (int)chase.size();
-    for (int i = 0; i < count; i++)
-      if (r[i] > k) cols.push_back(hs[i]->V + k * hs[i]->n);
+    const int ns = (int)chase_s.size(), nl = (int)chase_l.size(), nact = ns + nl;
+    std::vector<ChaseArgs> chase(chase_s);
+    chase.insert(chase.end(), chase_l.begin(), chase_l.end());
+    std::vector<const double *> cols(ucol_s);  // u columns then v columns, in chase order
+    cols.insert(cols.end(), ucol_l.begin(), ucol_l.end());
+    cols.insert(cols.end(), vcol_s.begin(), vcol_s.end());
+    cols.insert(cols.end(), vcol_l.begin(), vcol_l.end());
     first.push_back(slabs);
     ce = cudaMemcpyAsync(d_chase, chase.data(), sizeof(ChaseArgs) * nact, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_cols, cols.data(), sizeof(double *) * cols.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_apply, apply.data(), sizeof(ApplyItem) * apply.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = launch_stage_batch(d_chase, d_cols, d_cols + nact, nact, s);
-    if (ce == cudaSuccess) ce = launch_chase_batch(d_chase, nact, max_n, max_band, precision == BDU_MIXED, s);
+    // the small items' chases on the second stream, beside the large items'
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (ce == cudaSuccess && ns > 0 && nl > 0) {
+      ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventRecord(fork, s);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h0->batch_aux, fork, 0);
+    }
+    const cudaStream_t ss = (ns > 0 && nl > 0) ? h0->batch_aux : s;
+    if (ce == cudaSuccess && ns > 0) ce = launch_chase_batch(d_chase, ns, max_n, max_band, precision == BDU_MIXED, ss);
+    if (ce == cudaSuccess && nl > 0)
+      ce = launch_chase_cluster_batch(d_chase + ns, nl, max_n_l, precision == BDU_MIXED, s);
+    if (ce == cudaSuccess && join) {
+      ce = cudaEventRecord(join, h0->batch_aux);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, join, 0);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (ce == cudaSuccess) ce = launch_apply_batch(precision, d_apply, d_first, (int)apply.size(), slabs, smem, s);
     if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched update round");
     h0->launches += 3;

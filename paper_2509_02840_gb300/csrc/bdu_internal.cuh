@@ -119,6 +119,10 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);
+// In a batch, items with n at or above this size get a thread-block cluster each.
+constexpr int kClusterBatchMinN = 512;
+cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int max_n, int fast,
+                                       cudaStream_t s);
 void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
                              bool with_spike, int *status, int sm_reserve, bool desc_ready, cudaStream_t s);

@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase_batch(const ChaseArgs *__
 // unfinished chase) into every CTA's inbox, so that the reads on a step's
 // critical path are local.  Totals are one step old, which is conservative.
 template <bool FAST>
-__global__ void __launch_bounds__(kMaxThreads) k_chase_cluster(ChaseArgs Ar) {
+__device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   __shared__ int2 st[2][kMaxThreads];    // this CTA's chase status words
   __shared__ int2 pred[2][kMaxThreads];  // mirror of the previous CTA's status words
   __shared__ int inbox[2][kMaxCluster][4];  // every CTA's counters: done, p1done, min unfinished
@@ -788,6 +788,19 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase_cluster(ChaseArgs Ar) {
 }
 
 template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase_cluster(ChaseArgs Ar) {
+  engine_cluster<FAST>(Ar);
+}
+
+// Many independent factorizations, one 16-CTA cluster each (the large items
+// of a batched update): cluster c runs the cluster engine on items[c].
+template <bool FAST>
+__global__ void __launch_bounds__(kMaxThreads) k_chase_cluster_batch(const ChaseArgs *__restrict__ items) {
+  const ChaseArgs Ar = items[blockIdx.x / kMaxCluster];
+  engine_cluster<FAST>(Ar);
+}
+
+template <bool FAST>
 cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
   const int n = a.n, m = a.m;
   const int N = (m > n) ? n + 1 : n;
@@ -835,6 +848,38 @@ cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// The items one thread-block cluster each; the block size suits the largest n.
+cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int max_n, int fast,
+                                       cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int CS = kMaxCluster;
+  int threads = ((max_n / 3 + 16) / CS + 31) / 32 * 32;
+  if (threads < 64) threads = 64;
+  if (threads > kMaxThreads) threads = kMaxThreads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS * count);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (fast) {
+    e = cudaFuncSetAttribute(k_chase_cluster_batch<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_chase_cluster_batch<true>, d_items);
+  } else {
+    e = cudaFuncSetAttribute(k_chase_cluster_batch<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_chase_cluster_batch<false>, d_items);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s) {
