@@ -699,12 +699,18 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   for (;; step++) {
     cl.sync();  // every write of the previous step is visible cluster-wide
     const int rd = step & 1, wr = rd ^ 1;
-    // cluster totals at the end of the previous step (inbox slot wr)
-    int sd = 0, sp1 = 0, fr = INT_MAX;
-    for (int c = 0; c < CS; c++) {
-      sd += inbox[wr][c][0];
-      sp1 += inbox[wr][c][1];
-      fr = min(fr, inbox[wr][c][2]);
+    // this step's lowest-unfinished slot is my_min[rd]; my_min[wr] was read by
+    // the previous step's pushes, all done before the barrier above
+    if (me == 0) my_min[wr] = INT_MAX;
+    // cluster totals at the end of the previous step (inbox slot wr): lane c
+    // reads CTA c's counters, then warp reductions
+    int sd, sp1, fr;
+    {
+      const int lane = me & 31;
+      const bool has = lane < CS;
+      sd = __reduce_add_sync(0xffffffffu, has ? inbox[wr][lane][0] : 0);
+      sp1 = __reduce_add_sync(0xffffffffu, has ? inbox[wr][lane][1] : 0);
+      fr = __reduce_min_sync(0xffffffffu, has ? inbox[wr][lane][2] : INT_MAX);
     }
     if (fr == INT_MAX) fr = T;
     if (!fold_done && sp1 == p1) {
@@ -776,8 +782,6 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
       ib[1] = my_p1;
       ib[2] = my_min[rd];
     }
-    __syncthreads();
-    if (me == 0) my_min[wr] = INT_MAX;
   }
   if (me == 0) {
     if (cta == 0) cnt[8] = step;
