@@ -148,8 +148,11 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P);
  * the order in which they are applied: side 0 = left rotations (on Q),
  * side 1 = right rotations (on P).  Each rotation is (c[k], s[k], a[k]) with
  * a 1-based pair (a, a+1) and pair update x_a <- c x_a + s x_b,
- * x_b <- -s x_a + c x_b (Eqs. giv, giv1).  *count receives the number of
- * rotations; at most cap are written.  Synchronizes. */
+ * x_b <- -s x_a + c x_b (Eqs. giv, giv1).  The FP64 form returns the FP64
+ * coefficients; the mixed form, which keeps only the FP32 coefficients its
+ * FP32 factors are rotated with, returns those (exactly, as doubles).
+ * *count receives the number of rotations; at most cap are written.
+ * Synchronizes. */
 bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
                               int64_t cap, int64_t *count);
 

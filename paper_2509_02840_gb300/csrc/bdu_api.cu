@@ -544,16 +544,19 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   return maybe_reorth(h, r);
 }
 
-// Allocates one buffer of rotation records (and the mixed form's FP32 copies
-// and chase descriptors); false if an allocation failed.  Padded: the kernels
-// that stream records read whole 16-byte units.
+// Allocates one buffer of rotation records; false if an allocation failed.
+// The FP64 form keeps (c, s) in FP64; the mixed form keeps only their FP32
+// copies (what its FP32 factors are rotated with) and the chase descriptors.
+// Padded: the kernels that stream records read whole 16-byte units.
 bool alloc_records(bdu_ctx *h, RotStream &r, int T, int cap, int64_t m, bool mixed) {
   const size_t tc = (size_t)T * cap;
   r.T = T; r.cap = cap; r.p1 = (int)(h->N - 1);
-  r.Lc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
-  r.Ls = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
-  r.Rc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
-  r.Rs = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  if (!mixed) {
+    r.Lc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+    r.Ls = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+    r.Rc = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+    r.Rs = (double *)dev_alloc(h, sizeof(double) * (tc + 2));
+  }
   r.La = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tc + 4));
   r.Ra = (int32_t *)dev_alloc(h, sizeof(int32_t) * (tc + 4));
   r.Ln = (int32_t *)dev_alloc(h, sizeof(int32_t) * (T + 1));
@@ -562,7 +565,7 @@ bool alloc_records(bdu_ctx *h, RotStream &r, int T, int cap, int64_t m, bool mix
   r.Ss = (double *)dev_alloc(h, sizeof(double) * (m + 1));
   r.Sa = (int32_t *)dev_alloc(h, sizeof(int32_t) * (m + 1));
   r.Sn = (int32_t *)dev_alloc(h, sizeof(int32_t) * 4);
-  bool ok = r.Lc && r.Ls && r.Rc && r.Rs && r.La && r.Ra && r.Ln && r.Rn && r.Sc && r.Ss && r.Sa && r.Sn;
+  bool ok = (mixed || (r.Lc && r.Ls && r.Rc && r.Rs)) && r.La && r.Ra && r.Ln && r.Rn && r.Sc && r.Ss && r.Sa && r.Sn;
   if (mixed) {
     r.Lf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
     r.Rf = (float2 *)dev_alloc(h, sizeof(float2) * (tc + 2));
@@ -1062,8 +1065,16 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
   std::vector<double> hc(tc), hs(tc);
   std::vector<int32_t> ha(tc);
   ce = cudaMemcpy(cnt.data(), side == 0 ? st.Ln : st.Rn, sizeof(int32_t) * st.T, cudaMemcpyDeviceToHost);
-  if (ce == cudaSuccess) ce = cudaMemcpy(hc.data(), side == 0 ? st.Lc : st.Rc, sizeof(double) * tc, cudaMemcpyDeviceToHost);
-  if (ce == cudaSuccess) ce = cudaMemcpy(hs.data(), side == 0 ? st.Ls : st.Rs, sizeof(double) * tc, cudaMemcpyDeviceToHost);
+  const double *dc = side == 0 ? st.Lc : st.Rc;
+  if (dc) {
+    if (ce == cudaSuccess) ce = cudaMemcpy(hc.data(), dc, sizeof(double) * tc, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(hs.data(), side == 0 ? st.Ls : st.Rs, sizeof(double) * tc, cudaMemcpyDeviceToHost);
+  } else {
+    // mixed form: the FP32 coefficients the factors are rotated with
+    std::vector<float2> hf(tc);
+    if (ce == cudaSuccess) ce = cudaMemcpy(hf.data(), side == 0 ? st.Lf : st.Rf, sizeof(float2) * tc, cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < tc; i++) { hc[i] = hf[i].x; hs[i] = hf[i].y; }
+  }
   if (ce == cudaSuccess) ce = cudaMemcpy(ha.data(), side == 0 ? st.La : st.Ra, sizeof(int32_t) * tc, cudaMemcpyDeviceToHost);
   int32_t ns = 0;
   std::vector<double> sc, ss;
@@ -1071,8 +1082,14 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
   if (ce == cudaSuccess && side == 0 && h->m > h->n) {
     ce = cudaMemcpy(&ns, st.Sn, sizeof(int32_t), cudaMemcpyDeviceToHost);
     sc.resize(ns + 1); ss.resize(ns + 1); sa.resize(ns + 1);
-    if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sc.data(), st.Sc, sizeof(double) * ns, cudaMemcpyDeviceToHost);
-    if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(ss.data(), st.Ss, sizeof(double) * ns, cudaMemcpyDeviceToHost);
+    if (dc) {
+      if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sc.data(), st.Sc, sizeof(double) * ns, cudaMemcpyDeviceToHost);
+      if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(ss.data(), st.Ss, sizeof(double) * ns, cudaMemcpyDeviceToHost);
+    } else {
+      std::vector<float2> sf(ns + 1);
+      if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sf.data(), st.Sf, sizeof(float2) * ns, cudaMemcpyDeviceToHost);
+      for (int32_t q = 0; q < ns; q++) { sc[q] = sf[q].x; ss[q] = sf[q].y; }
+    }
     if (ce == cudaSuccess && ns > 0) ce = cudaMemcpy(sa.data(), st.Sa, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost);
   }
   if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_rotations");

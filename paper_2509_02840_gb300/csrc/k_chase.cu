@@ -202,7 +202,8 @@ struct Rec {
   int *err;
   __device__ __forceinline__ void push(double cc, double ss, int aa) {
     if (cnt < cap) {
-      c[cnt] = cc; s[cnt] = ss; a[cnt] = aa;
+      a[cnt] = aa;
+      if (c) { c[cnt] = cc; s[cnt] = ss; }
       if (f) f[cnt] = make_float2(f32_of(cc), f32_of(ss));
     } else {
       atomicOr(err, ERR_CAP);
@@ -600,8 +601,10 @@ __device__ __forceinline__ void bind_rec(const ChaseArgs &Ar, const Task &k, Rec
   const int cap = Ar.st.cap;
   if (k.t < Ar.st.T) {
     const size_t o = (size_t)k.t * cap;
-    recL.c = Ar.st.Lc + o; recL.s = Ar.st.Ls + o; recL.a = Ar.st.La + o;
-    recR.c = Ar.st.Rc + o; recR.s = Ar.st.Rs + o; recR.a = Ar.st.Ra + o;
+    recL.a = Ar.st.La + o;
+    recR.a = Ar.st.Ra + o;
+    recL.c = Ar.st.Lc ? Ar.st.Lc + o : nullptr; recL.s = Ar.st.Ls ? Ar.st.Ls + o : nullptr;
+    recR.c = Ar.st.Rc ? Ar.st.Rc + o : nullptr; recR.s = Ar.st.Rs ? Ar.st.Rs + o : nullptr;
     recL.f = Ar.st.Lf ? Ar.st.Lf + o : nullptr;
     recR.f = Ar.st.Rf ? Ar.st.Rf + o : nullptr;
     recL.cnt = recR.cnt = 0;

@@ -51,10 +51,14 @@ def reserve_bytes(m, n, precision, max_rank=4):
     tc = T * (n // 2 + 4)
     b = es * (m * m + n * n)                              # Q, P
     b += 8 * (6 * (N + 2) + 2 * (n + 2) + (m + 2))       # band, row 1, u, v
-    b += tc * (4 * 8 + 2 * 4) + 8 * (T + 1) + 20 * (m + 1) + 8 * (3 * m + 8) + 256
+    if precision == bdu.MIXED:
+        b += tc * (2 * 8 + 2 * 4)                         # FP32 (c, s) and int32 pair records
+    else:
+        b += tc * (4 * 8 + 2 * 4)                         # FP64 (c, s) and int32 pair records
+    b += 8 * (T + 1) + 20 * (m + 1) + 8 * (3 * m + 8) + 256
     b += max_rank * (16 * (m + n) + 4 * (m + n)) + 8      # B, C, U, V and their nonzero lists
     if precision == bdu.MIXED:
-        b += 8 * m * m + 16 * tc + 8 * (m + 1)            # FP64 scratch, FP32 record copies
+        b += 8 * m * m + 8 * (m + 1) + 32 * (T + 1)       # FP64 scratch, spike copies, chase descriptors
         b += 16 * m * m                                   # re-orthogonalization workspace
     return b
 

@@ -46,6 +46,25 @@ def test_fp64_bitwise(m, n, r):
             assert np.array_equal(c, ref.c) and np.array_equal(s, ref.s) and np.array_equal(a, ref.a)
 
 
+
+@pytest.mark.parametrize("m,n", [(64, 48), (130, 97), (256, 128)])
+def test_mixed_rotations_are_the_fp32_coefficients(m, n):
+    """The mixed form keeps only the FP32 coefficients its factors are rotated
+    with: read_rotations returns FP32 values, as many rotations on the same
+    pairs as the oracle generates, each close to the oracle's (its inputs
+    differ from the oracle's by the FP32 rounding of Q and P)."""
+    Q, d, e, P = I.factorization(m, n, config=0, which=m + n)
+    B, C = I.dense_update(m, n, h=1, config=0, r=1)
+    _, rots, _ = _gpu_update(Q, d, e, P, B, C, precision=bdu.MIXED)
+    U, V = O.project(Q, P, B, C)
+    _, _, L, R, _ = O.generate(m, n, d, e, U, V)
+    for (c, s, a), ref in ((rots[0], L), (rots[1], R)):
+        assert len(c) == len(ref) and np.array_equal(a, ref.a)
+        assert np.array_equal(c, c.astype(np.float32).astype(np.float64))
+        assert np.array_equal(s, s.astype(np.float32).astype(np.float64))
+        assert np.max(np.abs(c * c + s * s - 1.0)) <= 1e-6
+        assert np.median(np.abs(c - ref.c)) <= 1e-5 and np.median(np.abs(s - ref.s)) <= 1e-5
+
 def test_fp64_stream_config0():
     """20 sequential rank-1 updates at m=256, n=128, compared after every update."""
     m, n = 256, 128
