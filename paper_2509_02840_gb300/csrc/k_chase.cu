@@ -119,15 +119,22 @@ __device__ __forceinline__ float f32_of(double x) {
 // in [0.25, 2); y0 = rsqrtf(q) (q truncated to FP32 and y0 widened back
 // through the bit patterns, about 22 correct bits) is refined by
 // y = y0 (1 + e/2 + 3e^2/8) with e = 1 - q y0^2 (third-order Newton step,
-// error about e^3).  Inputs outside [2^-1021, 2^1022) take the exact path.
+// error about e^3).  Inputs outside [2^-1021, 2^1022), subnormal, or with a
+// ratio below 2^-1021 take the exact path.  Results are those of the same
+// formulas with the scalings done as FP64 multiplies (which are exact).
 __device__ __forceinline__ bool rotg_fast(double f, double g, double &c, double &s, double &r) {
   const unsigned long long bf = absbits(f), bg = absbits(g);
-  const int ex = (int)((bf > bg ? bf : bg) >> 52);
-  if ((ex < 2 || ex > 2044) && bg != 0) return rotg_exact(f, g, c, s, r);
-  const int exs = ex < 2 ? 2 : ex;  // keeps sigma finite when f = g = 0
-  const double sigma = __longlong_as_double((long long)(2045 - exs) << 52);  // 2^(1022-ex)
-  const double inv = __longlong_as_double((long long)(exs + 1) << 52);       // 1/sigma
-  const double fs = f * sigma, gs = g * sigma;
+  const unsigned long long bm = bf > bg ? bf : bg, bn = bf > bg ? bg : bf;
+  const int ex = (int)(bm >> 52), en = (int)(bn >> 52);
+  // the exact path when the scalings below would leave the normal range: the
+  // larger input's exponent outside [2, 2044], or the smaller input subnormal
+  // or more than 2^1021 below the larger
+  if (bg != 0 && (ex < 2 || ex > 2044 || (bn != 0 && (en == 0 || en + 1021 < ex)))) return rotg_exact(f, g, c, s, r);
+  // fs = f 2^(1022-ex), gs = g 2^(1022-ex) and r = |r_s| 2^(ex-1022): exact
+  // power-of-two scalings, done on the exponent field (integer pipes)
+  const long long dk = (long long)(1022 - ex) << 52;
+  const double fs = bf == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(f) + dk);
+  const double gs = bg == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(g) + dk);
   const double q = fma(fs, fs, gs * gs);
   const unsigned qf = (unsigned)(((unsigned long long)__double_as_longlong(q) >> 29) - (896ULL << 23));
   double y = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(rsqrtf(__uint_as_float(qf))) << 29) +
@@ -135,14 +142,13 @@ __device__ __forceinline__ bool rotg_fast(double f, double g, double &c, double 
   const double e = fma(-(q * y), y, 1.0);
   y = fma(y * e, fma(0.375, e, 0.5), y);
   const bool fz = bf == 0;
-  const double fa = __longlong_as_double((long long)absbits(fs));                 // |fs|
-  const double gsg = __longlong_as_double(__double_as_longlong(gs) ^
-                                          (__double_as_longlong(f) & (long long)0x8000000000000000ULL));  // sign(f) gs
-  const double qy = q * y;
+  const long long sf = __double_as_longlong(f) & (long long)0x8000000000000000ULL;  // sign(f)
+  const double fa = __longlong_as_double((long long)absbits(fs));                  // |fs|
+  const double gsg = __longlong_as_double(__double_as_longlong(gs) ^ sf);          // sign(f) gs
+  const double qy = q * y;                                                         // |r| scaled, in [0.5, 1.5)
   c = fz ? 0.0 : fa * y;
   s = fz ? 1.0 : gsg * y;
-  r = fz ? g : __longlong_as_double(__double_as_longlong(qy * inv) ^
-                                    (__double_as_longlong(f) & (long long)0x8000000000000000ULL));
+  r = fz ? g : __longlong_as_double((__double_as_longlong(qy) - dk) ^ sf);
   return bg != 0;
 }
 
