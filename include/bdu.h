@@ -78,6 +78,14 @@ typedef struct {
                          quantity, rounded differently; Sec. 3.2).  Doubles the memory
                          of the rotation records.  0 = off (default); ignored in the
                          FP64 form and when max(m, n) exceeds about 50000. */
+  int graphs;         /* 1 = capture the launch sequence of an update (projection, the
+                         chase and the applications of each rank-1 column) in a CUDA
+                         graph the first time a rank and pair of input buffers are seen,
+                         and replay it for later updates with the same ones (default);
+                         0 = launch every kernel separately.  Results are identical.
+                         Not used for overlapped rank-1 updates or while timing is on.
+                         The capture runs on the handle's stream: work that other threads
+                         enqueue on that stream during an update would be captured too. */
 } bdu_options;
 
 typedef struct {
@@ -95,6 +103,7 @@ typedef struct {
   double ms_apply_p;        /* device time of the rotation apply to P (K3) */
   int64_t apply_launches;   /* apply-kernel launches covered by ms_apply_q + ms_apply_p */
   int64_t device_bytes;     /* device memory currently held by the handle */
+  int64_t graph_replays;    /* updates issued by replaying a captured CUDA graph */
 } bdu_stats_t;
 
 /* Fills *opt with the defaults listed above. */

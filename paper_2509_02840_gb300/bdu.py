@@ -27,7 +27,7 @@ class BduError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int), ("overlap", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("overlap", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("timed_updates", ctypes.c_int64),
                 ("ms_project", ctypes.c_double), ("ms_chase", ctypes.c_double),
                 ("ms_apply_q", ctypes.c_double), ("ms_apply_p", ctypes.c_double),
-                ("apply_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("apply_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
@@ -172,7 +173,7 @@ class Factorization:
     """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
-                 check_every=None, engine=0, overlap=False):
+                 check_every=None, engine=0, overlap=False, graphs=True):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -184,6 +185,7 @@ class Factorization:
         opt.device = int(device)
         opt.engine = int(engine)
         opt.overlap = 1 if overlap else 0
+        opt.graphs = 1 if graphs else 0
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:
@@ -264,7 +266,7 @@ class Factorization:
                 "timed_updates": st.timed_updates, "ms_project": st.ms_project,
                 "ms_chase": st.ms_chase, "ms_apply_q": st.ms_apply_q,
                 "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches,
-                "device_bytes": st.device_bytes}
+                "device_bytes": st.device_bytes, "graph_replays": st.graph_replays}
 
     def check_orthogonality(self):
         q = ctypes.c_double(); p = ctypes.c_double()

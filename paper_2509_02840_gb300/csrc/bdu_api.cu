@@ -102,6 +102,16 @@ struct bdu_ctx {
   cudaStream_t batch_aux;
   void *batch_ws;
   size_t batch_ws_bytes;
+  // the captured launch sequence of a plain update, replayed while the rank
+  // and the buffers it reads are the same (null = none; g_off after a failed capture)
+  cudaGraphExec_t gexec;
+  int64_t g_r;
+  const double *g_B, *g_C;
+  double *g_U;
+  int32_t *g_rec;      // the record buffer the graph writes (h->st.La)
+  int64_t g_launches;  // kernels one replay launches
+  bool g_off;
+  int64_t graph_replays;
   // bookkeeping
   int64_t updates;
   int64_t launches;
@@ -484,10 +494,8 @@ bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
 }
 
 // One update with B, C already in device memory.
-bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
-  if (h->ovl && r == 1) return run_overlapped(h, dB, dC);
-  bdu_status fs = flush_apply(h);
-  if (fs != BDU_OK) return fs;
+// Enqueues the launches of a plain update (every rank-1 column in turn).
+bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
   const int m = (int)h->m, n = (int)h->n;
   cudaStream_t s = h->stream;
   cudaError_t e;
@@ -541,6 +549,63 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     if (h->timing) h->apply_launches += 2;
     h->updates++;
   }
+  return BDU_OK;
+}
+
+void drop_graph(bdu_ctx *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
+  if (h->ovl && r == 1) return run_overlapped(h, dB, dC);
+  bdu_status fs = flush_apply(h);
+  if (fs != BDU_OK) return fs;
+  if (!h->opt.graphs || h->g_off || h->timing) {
+    fs = enqueue_update(h, dB, dC, r);
+    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+  }
+  cudaStream_t s = h->stream;
+  if (h->gexec && h->g_r == r && h->g_B == dB && h->g_C == dC && h->g_U == h->U && h->g_rec == h->st.La) {
+    const cudaError_t e = cudaGraphLaunch(h->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "replaying the update graph");
+    h->launches += h->g_launches;
+    h->updates += r;
+    h->graph_replays++;
+    return maybe_reorth(h, r);
+  }
+  // capture this rank's launch sequence, then run it
+  drop_graph(h);
+  const int64_t l0 = h->launches, u0 = h->updates;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->g_off = true;
+    fs = enqueue_update(h, dB, dC, r);
+    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+  }
+  fs = enqueue_update(h, dB, dC, r);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  cudaGraphExec_t ex = nullptr;
+  if (fs == BDU_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (fs != BDU_OK || e != cudaSuccess) {
+    // not capturable here: launch separately from now on
+    cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+    h->g_off = true;
+    h->poisoned = false;
+    h->launches = l0;
+    h->updates = u0;
+    fs = enqueue_update(h, dB, dC, r);
+    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+  }
+  h->gexec = ex;
+  h->g_r = r; h->g_B = dB; h->g_C = dC; h->g_U = h->U; h->g_rec = h->st.La;
+  h->g_launches = h->launches - l0;
+  e = cudaGraphLaunch(ex, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "launching the update graph");
   return maybe_reorth(h, r);
 }
 
@@ -598,6 +663,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->device = 0;
   opt->engine = 0;
   opt->overlap = 0;
+  opt->graphs = 1;
 }
 
 int bdu_version(void) { return 100; }
@@ -618,6 +684,7 @@ void bdu_destroy(bdu_handle h) {
   if (h->sc) cudaStreamSynchronize(h->sc);
   if (h->batch_aux) cudaStreamSynchronize(h->batch_aux);
   resolve_timers(h);
+  drop_graph(h);
   if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
   if (h->probe_ev) cudaEventDestroy(h->probe_ev);
   for (cudaEvent_t ev : {h->ev_call, h->ev_proj, h->ev_rot, h->ev_chase, h->ev_apply[0], h->ev_apply[1]})
@@ -1147,6 +1214,7 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   int64_t bytes = 0;
   for (size_t b : h->block_bytes) bytes += (int64_t)b;
   out->device_bytes = bytes;
+  out->graph_replays = h->graph_replays;
   return BDU_OK;
 }
 
