@@ -63,7 +63,17 @@ enum {
 
 typedef struct {
   int precision;      /* BDU_FP64 (default) or BDU_MIXED */
-  int nb;             /* panel width of the blocked apply; 0 = library choice */
+  int nb;             /* tile shape of the rotation apply (all give identical results):
+                         0 = picked by the autotuner (default): after the first update
+                         of a shape not seen before, each candidate is timed on a
+                         scratch copy of Q and P with that update's rotations, which
+                         makes that first call wait for the device; choices are kept
+                         per (GPU, form, order, SMs) for the process and, if the
+                         environment variable BDU_TUNE_FILE names a file, in it (JSON).
+                         FP64 form: an even number <= 64 = rows of Q/P per thread
+                         block of the shared-memory apply.  Mixed form: 1..4 = a
+                         register-resident layout of (columns x rows) per thread
+                         12x8, 24x4, 6x16, 18x4; 5 = the shared-memory apply. */
   double reorth_tol;  /* BDU_MIXED: re-orthogonalize Q (P) when the estimated
                          ||Q^T Q - I||_2 exceeds this; 0 = never (default 1e-6) */
   int check_every;    /* BDU_MIXED: updates between orthogonality estimates (default 10) */
@@ -104,6 +114,8 @@ typedef struct {
   int64_t apply_launches;   /* apply-kernel launches covered by ms_apply_q + ms_apply_p */
   int64_t device_bytes;     /* device memory currently held by the handle */
   int64_t graph_replays;    /* updates issued by replaying a captured CUDA graph */
+  int64_t apply_variant[2]; /* apply tile shape in use for Q, P (the nb values; 0 = default) */
+  int64_t tunings;          /* apply variants this handle picked by timing */
 } bdu_stats_t;
 
 /* Fills *opt with the defaults listed above. */

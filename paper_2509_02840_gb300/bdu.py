@@ -39,7 +39,8 @@ class Stats(ctypes.Structure):
                 ("ms_project", ctypes.c_double), ("ms_chase", ctypes.c_double),
                 ("ms_apply_q", ctypes.c_double), ("ms_apply_p", ctypes.c_double),
                 ("apply_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("graph_replays", ctypes.c_int64)]
+                ("graph_replays", ctypes.c_int64), ("apply_variant", ctypes.c_int64 * 2),
+                ("tunings", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
@@ -173,7 +174,7 @@ class Factorization:
     """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
-                 check_every=None, engine=0, overlap=False, graphs=True):
+                 check_every=None, engine=0, overlap=False, graphs=True, nb=0):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -186,6 +187,7 @@ class Factorization:
         opt.engine = int(engine)
         opt.overlap = 1 if overlap else 0
         opt.graphs = 1 if graphs else 0
+        opt.nb = int(nb)
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:
@@ -266,7 +268,8 @@ class Factorization:
                 "timed_updates": st.timed_updates, "ms_project": st.ms_project,
                 "ms_chase": st.ms_chase, "ms_apply_q": st.ms_apply_q,
                 "ms_apply_p": st.ms_apply_p, "apply_launches": st.apply_launches,
-                "device_bytes": st.device_bytes, "graph_replays": st.graph_replays}
+                "device_bytes": st.device_bytes, "graph_replays": st.graph_replays,
+                "apply_variant": list(st.apply_variant), "tunings": st.tunings}
 
     def check_orthogonality(self):
         q = ctypes.c_double(); p = ctypes.c_double()

@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include <cublas_v2.h>
@@ -112,6 +115,11 @@ struct bdu_ctx {
   int64_t g_launches;  // kernels one replay launches
   bool g_off;
   int64_t graph_replays;
+  // apply variant per side (launch_apply), and whether the autotuner is still
+  // to run after the next update
+  int apply_var[2];
+  bool tune_pending;
+  int64_t tunings;
   // bookkeeping
   int64_t updates;
   int64_t launches;
@@ -281,12 +289,14 @@ bdu_status enqueue_apply(bdu_ctx *h, int buf, int sm_reserve, cudaEvent_t after 
   if (e != cudaSuccess) return cuda_fail(h, e, "ordering the apply stream");
   {
     Timer tm(h, 2, h->sa);
-    e = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, h->sa, h->status, sm_reserve, true);
+    e = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, h->sa, h->status, sm_reserve, true,
+                     h->apply_var[0]);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
   }
   {
     Timer tm(h, 3, h->sa);
-    e = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, h->sa, h->status, sm_reserve, true);
+    e = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, h->sa, h->status, sm_reserve, true,
+                     h->apply_var[1]);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
   }
   e = cudaEventRecord(h->ev_apply[buf], h->sa);
@@ -413,6 +423,165 @@ bdu_status maybe_reorth(bdu_ctx *h, int64_t r) {
 // application starts once the rotation is done, so that it runs beside the
 // chase, which has the higher priority and is placed first.  s waits for the
 // chase; this column's application is deferred in turn.
+void drop_graph(bdu_ctx *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+// ------------------------------------------------------------------ autotuner
+// The apply variant of each side (launch_apply: the slab kernel's rows per
+// block in the FP64 form, the register layout or the slab kernel in the mixed
+// form) is picked by timing.  After the first update of a handle created with
+// nb = 0 whose shape is not yet known, every candidate runs twice on a scratch
+// copy of the factor with that update's rotation records, and the faster
+// candidate is kept (all candidates give identical results).  Choices are
+// cached for the process per (GPU, form, order of the factor, SMs left to the
+// apply) and, when the environment variable BDU_TUNE_FILE names a file, kept
+// there as a JSON object {"key": variant, ...}: read on first use, rewritten
+// after every new choice.
+namespace tune {
+std::mutex mu;
+std::map<std::string, int> table;
+bool loaded = false;
+
+std::string key(const bdu_ctx *h, int dim, int sm_reserve) {
+  cudaDeviceProp p{};
+  cudaGetDeviceProperties(&p, h->device);
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|%s|%d|%d", p.name, h->opt.precision == BDU_FP64 ? "fp64" : "mixed", dim,
+           sm_reserve);
+  for (char *c = buf; *c; c++)
+    if (*c == '"' || *c == '\\') *c = '_';
+  return buf;
+}
+
+// caller holds mu
+void load() {
+  if (loaded) return;
+  loaded = true;
+  const char *path = getenv("BDU_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  std::string text;
+  char chunk[4096];
+  size_t got;
+  while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) text.append(chunk, got);
+  fclose(f);
+  size_t i = 0;
+  while ((i = text.find('"', i)) != std::string::npos) {
+    const size_t j = text.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string k = text.substr(i + 1, j - i - 1);
+    const size_t c = text.find(':', j);
+    if (c == std::string::npos) break;
+    char *end = nullptr;
+    const long v = strtol(text.c_str() + c + 1, &end, 10);
+    if (end != text.c_str() + c + 1) table[k] = (int)v;
+    i = end ? (size_t)(end - text.c_str()) : c + 1;
+  }
+}
+
+// caller holds mu
+void save() {
+  const char *path = getenv("BDU_TUNE_FILE");
+  if (!path || !*path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  size_t k = 0;
+  for (const auto &kv : table) fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < table.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+}  // namespace tune
+
+// Picks the apply variant of one side; the rotation records of the latest
+// rank-1 column must be complete (the handle's stream synchronized) and not
+// yet applied, or applied: only a scratch copy of the factor is touched.
+bdu_status tune_side(bdu_ctx *h, int side, int sm_reserve) {
+  const int m = (int)h->m, n = (int)h->n, dim = side == 0 ? m : n;
+  const std::string k = tune::key(h, dim, sm_reserve);
+  {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    tune::load();
+    auto it = tune::table.find(k);
+    if (it != tune::table.end()) {
+      h->apply_var[side] = it->second;
+      return BDU_OK;
+    }
+  }
+  std::vector<int> cand;
+  if (h->opt.precision == BDU_FP64) {
+    for (int R : {2, 4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64}) cand.push_back(R);
+  } else {
+    for (int v = 1; v <= 4; v++) cand.push_back(v);
+    cand.push_back(kSlabVariant);
+  }
+  const size_t bytes = esize(h) * (size_t)dim * dim;
+  void *scratch = dev_alloc(h, bytes);
+  if (!scratch) return BDU_OK;  // no room: keep the library's choice
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 3.0e38f;
+  void *X = side == 0 ? h->Q : h->P;
+  for (size_t c = 0; c < cand.size() && ce == cudaSuccess; c++) {
+    float ms = 3.0e38f;
+    for (int rep = 0; rep < 2 && ce == cudaSuccess; rep++) {
+      ce = cudaMemcpyAsync(scratch, X, bytes, cudaMemcpyDeviceToDevice, s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+      if (ce != cudaSuccess) break;
+      const cudaError_t le = launch_apply(h->opt.precision, scratch, dim, dim, dim, h->st, side, side == 0 && m > n, s,
+                                          h->status, sm_reserve, false, cand[c]);
+      if (le == cudaErrorNotSupported) {
+        cudaGetLastError();
+        break;
+      }
+      ce = le;
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+      if (ce == cudaSuccess && t < ms) ms = t;
+    }
+    if (ce == cudaSuccess && ms < best_ms) { best_ms = ms; best = cand[c]; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  dev_free(h, scratch);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "autotuning the apply");
+  h->apply_var[side] = best;
+  h->tunings++;
+  std::lock_guard<std::mutex> lk(tune::mu);
+  tune::table[k] = best;
+  tune::save();
+  return BDU_OK;
+}
+
+// After an update: runs the autotuner once the first update's records exist.
+bdu_status maybe_tune(bdu_ctx *h) {
+  if (!h->tune_pending || h->st.T <= 0) return BDU_OK;
+  h->tune_pending = false;
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotuning the apply");
+  const int reserve = h->ovl ? kChaseSMs : 0;
+  bdu_status st = tune_side(h, 0, reserve);
+  if (st == BDU_OK) st = tune_side(h, 1, reserve);
+  drop_graph(h);  // captured with the previous variants
+  return st;
+}
+
+bdu_status finish_update(bdu_ctx *h, int64_t r) {
+  const bdu_status st = maybe_tune(h);
+  return st != BDU_OK ? st : maybe_reorth(h, r);
+}
+
 bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
   const int m = (int)h->m, n = (int)h->n;
   cudaStream_t s = h->stream, sa = h->sa, sc = h->sc;
@@ -490,7 +659,7 @@ bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
   h->launches += 3;
   h->pend = true;
   h->updates++;
-  return maybe_reorth(h, 1);
+  return finish_update(h, 1);
 }
 
 // One update with B, C already in device memory.
@@ -537,12 +706,12 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
     // K3: Q <- Q prod G^T, P <- P prod H
     {
       Timer tm(h, 2);
-      e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s, h->status);
+      e = launch_apply(h->opt.precision, h->Q, m, m, m, h->st, 0, m > n, s, h->status, 0, false, h->apply_var[0]);
       if (e != cudaSuccess) return cuda_fail(h, e, "apply to Q");
     }
     {
       Timer tm(h, 3);
-      e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s, h->status);
+      e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s, h->status, 0, false, h->apply_var[1]);
       if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
     }
     h->launches += 3;
@@ -552,18 +721,13 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
   return BDU_OK;
 }
 
-void drop_graph(bdu_ctx *h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-}
-
 bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
   if (h->ovl && r == 1) return run_overlapped(h, dB, dC);
   bdu_status fs = flush_apply(h);
   if (fs != BDU_OK) return fs;
   if (!h->opt.graphs || h->g_off || h->timing) {
     fs = enqueue_update(h, dB, dC, r);
-    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+    return fs != BDU_OK ? fs : finish_update(h, r);
   }
   cudaStream_t s = h->stream;
   if (h->gexec && h->g_r == r && h->g_B == dB && h->g_C == dC && h->g_U == h->U && h->g_rec == h->st.La) {
@@ -572,7 +736,7 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     h->launches += h->g_launches;
     h->updates += r;
     h->graph_replays++;
-    return maybe_reorth(h, r);
+    return finish_update(h, r);
   }
   // capture this rank's launch sequence, then run it
   drop_graph(h);
@@ -582,7 +746,7 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     cudaGetLastError();
     h->g_off = true;
     fs = enqueue_update(h, dB, dC, r);
-    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+    return fs != BDU_OK ? fs : finish_update(h, r);
   }
   fs = enqueue_update(h, dB, dC, r);
   cudaGraph_t g = nullptr;
@@ -599,14 +763,14 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     h->launches = l0;
     h->updates = u0;
     fs = enqueue_update(h, dB, dC, r);
-    return fs != BDU_OK ? fs : maybe_reorth(h, r);
+    return fs != BDU_OK ? fs : finish_update(h, r);
   }
   h->gexec = ex;
   h->g_r = r; h->g_B = dB; h->g_C = dC; h->g_U = h->U; h->g_rec = h->st.La;
   h->g_launches = h->launches - l0;
   e = cudaGraphLaunch(ex, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "launching the update graph");
-  return maybe_reorth(h, r);
+  return finish_update(h, r);
 }
 
 // Allocates one buffer of rotation records; false if an allocation failed.
@@ -713,6 +877,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown precision %d", o.precision);
   if (o.engine < 0 || o.engine > 2)
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
+  if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1)) : (o.nb < 0 || o.nb > kSlabVariant))
+    return fail(nullptr, BDU_EINVAL, "bdu_create: unknown apply variant nb=%d", o.nb);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
     return fail(nullptr, BDU_EINVAL, "bdu_create: non-finite value in Q, d, e or P");
 
@@ -720,6 +886,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   if (!h) return fail(nullptr, BDU_ENOMEM, "bdu_create: host allocation failed");
   h->m = m; h->n = n; h->N = (m > n) ? n + 1 : n;
   h->opt = o; h->device = o.device;
+  h->apply_var[0] = h->apply_var[1] = o.nb;
+  h->tune_pending = o.nb == 0;
   h->busy.store(0);
   h->al = Alloc{g_alloc.load(), g_free.load(), g_alloc_ctx.load(), o.device};
   cudaError_t ce = cudaSetDevice(o.device);
@@ -1215,6 +1383,9 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   for (size_t b : h->block_bytes) bytes += (int64_t)b;
   out->device_bytes = bytes;
   out->graph_replays = h->graph_replays;
+  out->apply_variant[0] = h->apply_var[0];
+  out->apply_variant[1] = h->apply_var[1];
+  out->tunings = h->tunings;
   return BDU_OK;
 }
 

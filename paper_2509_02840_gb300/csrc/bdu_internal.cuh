@@ -113,9 +113,15 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 // null selects the shared-memory slab kernel).
 // sm_reserve: SMs the register-resident path leaves free (for a chase that
 // runs concurrently); desc_ready: the chase descriptors of st are current.
+// variant (all give identical results): 0 = the library's choice; FP64 form:
+// R > 0 = rows per thread block of the slab kernel (even, <= 64); mixed form:
+// 1..4 = a register layout of launch_apply_reg, kSlabVariant = the slab
+// kernel.  cudaErrorNotSupported when the variant does not cover the shape.
+constexpr int kSlabVariant = 5;
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s,
-                         int *status = nullptr, int sm_reserve = 0, bool desc_ready = false);
+                         int *status = nullptr, int sm_reserve = 0, bool desc_ready = false,
+                         int variant = 0);
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);
@@ -125,7 +131,8 @@ cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int 
                                        cudaStream_t s);
 void apply_geometry(int precision, int ncol, size_t smem_cap, int *R, int *csw);
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, int *status, int sm_reserve, bool desc_ready, cudaStream_t s);
+                             bool with_spike, int *status, int sm_reserve, bool desc_ready, int layout,
+                             cudaStream_t s);
 cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t s);
 bool rotate_vectors_supported(int m, int n);
 cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,

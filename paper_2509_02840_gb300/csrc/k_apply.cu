@@ -247,12 +247,12 @@ cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const in
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status,
-                         int sm_reserve, bool desc_ready) {
+                         int sm_reserve, bool desc_ready, int variant) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
-  if (precision == BDU_MIXED) {
+  if (precision == BDU_MIXED && variant != kSlabVariant) {
     const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, sm_reserve,
-                                           desc_ready, s);
-    if (e != cudaErrorNotSupported) return e;
+                                           desc_ready, variant, s);
+    if (e != cudaErrorNotSupported || variant != 0) return e;
   }
   int dev = 0, optin = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -262,8 +262,11 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
   const int V = 16 / esz;
   // rows per CTA: a multiple of V; the column stride is an odd number of
   // 16-byte vectors.  Pick the R that minimizes waves x (R + overhead).
+  // (FP64 form: a positive variant fixes R instead)
   int best_R = 0, best_csw = 0;
   double best_cost = 1e300;
+  const bool fixed = precision == BDU_FP64 && variant > 0;
+  if (fixed && (variant % V != 0 || variant > 64)) return cudaErrorNotSupported;
   for (int R = V; R <= 64; R += V) {
     int w = R / V;
     if ((w & 1) == 0) w++;
@@ -272,9 +275,10 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
     if (smem > (size_t)optin) break;
     const int ctas = (nrow + R - 1) / R;
     const int waves = (ctas + sms - 1) / sms;
-    const double cost = (double)waves * (R + 4);
+    const double cost = fixed ? (R == variant ? 0.0 : 1e299) : (double)waves * (R + 4);
     if (cost <= best_cost) { best_cost = cost; best_R = R; best_csw = csw; }
   }
+  if (fixed && best_R != variant) return cudaErrorNotSupported;
   if (best_R == 0) return cudaErrorInvalidValue;  // a single vector column does not fit
   const size_t smem = (size_t)esz * best_csw * ncol;
   const int blocks = (nrow + best_R - 1) / best_R;

@@ -482,17 +482,32 @@ cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t
 
 // Register-resident FP32 apply; cudaErrorNotSupported, before anything is
 // launched, when the shape or the stream is not covered (the caller then uses
-// the shared-memory slab kernel).  Records are copied in 16-byte units up to
-// one entry past the last chase's slot, so Lf and Rf hold T*cap + 2 entries.
+// the shared-memory slab kernel).  layout: 0 = the first of (W, V) = (12, 8),
+// (24, 4) that covers the columns; 1 = (12, 8), 2 = (24, 4), 3 = (6, 16),
+// 4 = (18, 4) (columns per thread W, rows per thread V; all give identical
+// results).  Records are copied in 16-byte units up to one entry past the last
+// chase's slot, so Lf and Rf hold T*cap + 2 entries.
 cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
-                             bool with_spike, int *status, int sm_reserve, bool desc_ready, cudaStream_t s) {
+                             bool with_spike, int *status, int sm_reserve, bool desc_ready, int layout,
+                             cudaStream_t s) {
   const float2 *coef = side == 0 ? st.Lf : st.Rf;
   int4 *desc = side == 0 ? st.Lm : st.Rm;
-  if (!coef || !desc || !status) return cudaErrorNotSupported;
-  RegLaunch<12, 8> narrow;
-  RegLaunch<24, 4> wide;
-  const bool use_narrow = narrow.plan(nrow, ncol, st.cap, sm_reserve);
-  if (!use_narrow && !wide.plan(nrow, ncol, st.cap, sm_reserve)) {
+  if (!coef || !desc || !status || layout < 0 || layout > 4) return cudaErrorNotSupported;
+  RegLaunch<12, 8> l1;
+  RegLaunch<24, 4> l2;
+  RegLaunch<6, 16> l3;
+  RegLaunch<18, 4> l4;
+  int use = 0;
+  if (layout == 0) {
+    use = l1.plan(nrow, ncol, st.cap, sm_reserve) ? 1 : (l2.plan(nrow, ncol, st.cap, sm_reserve) ? 2 : 0);
+  } else {
+    const bool ok = layout == 1   ? l1.plan(nrow, ncol, st.cap, sm_reserve)
+                    : layout == 2 ? l2.plan(nrow, ncol, st.cap, sm_reserve)
+                    : layout == 3 ? l3.plan(nrow, ncol, st.cap, sm_reserve)
+                                  : l4.plan(nrow, ncol, st.cap, sm_reserve);
+    use = ok ? layout : 0;
+  }
+  if (use == 0) {
     cudaGetLastError();
     return cudaErrorNotSupported;
   }
@@ -502,8 +517,10 @@ cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const Rot
     k_chase_descriptors<<<(st.T + 255) / 256, 256, 0, s>>>(Ca, Cn, st.T, st.cap, st.p1, desc);
   if (with_spike) k_apply_spike32<<<(nrow + 127) / 128, 128, 0, s>>>(X, ld, nrow, st.Sf, st.Sa, st.Sn);
   if (st.T > 0) {
-    if (use_narrow) narrow.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
-    else wide.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
+    if (use == 1) l1.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
+    else if (use == 2) l2.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
+    else if (use == 3) l3.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
+    else l4.launch(X, ld, nrow, ncol, coef, Ca, desc, st.T, st.cap, status, s);
   }
   return cudaGetLastError();
 }

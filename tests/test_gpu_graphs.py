@@ -16,7 +16,10 @@ RANKS = [1, 1, 1, 2, 2, 1, 3, 1, 1]
 
 def _run(precision, graphs, m, n, dev_inputs=False, timing_at=None):
     Q, d, e, P = I.factorization(m, n, config=0, which=41)
-    with bdu.Factorization(Q, d, e, P, precision=precision, graphs=graphs, check_every=0 if precision == bdu.MIXED else None) as F:
+    # a fixed apply variant: the autotuner would drop the first update's graph
+    nb = 8 if precision == bdu.FP64 else 1
+    with bdu.Factorization(Q, d, e, P, precision=precision, graphs=graphs, nb=nb,
+                           check_every=0 if precision == bdu.MIXED else None) as F:
         keep = []
         for h, r in enumerate(RANKS):
             if timing_at is not None:
