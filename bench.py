@@ -149,8 +149,10 @@ ALU_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # root, 2 divisions counted as one flop each).
 CHASE_FLOPS_PER_ROTATION = 26
 # DRAM bytes (read + write) of one mixed-form chase launch at m = n = 4096, from one
-# ncu capture (profiles/launches_recommender_4096.md): the rotation records written.
-CHASE_TRAFFIC_4096 = 13.6e6 + 652.0e6
+# ncu capture (profiles/launches_recommender_4096.md): the rotation records written
+# (FP32 (c, s) and an int32 pair index per rotation, 12 B x 25.2M = 302 MB, part of
+# which is still in L2 when the launch ends).
+CHASE_TRAFFIC_4096 = 9.14e6 + 250.55e6
 
 
 def roofline(st, precision, rotations_per_update, launches_per_update, steps_per_update=None):

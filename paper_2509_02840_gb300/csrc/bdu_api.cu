@@ -432,9 +432,10 @@ void drop_graph(bdu_ctx *h) {
 // The apply variant of each side (launch_apply: the slab kernel's rows per
 // block in the FP64 form, the register layout or the slab kernel in the mixed
 // form) is picked by timing.  After the first update of a handle created with
-// nb = 0 whose shape is not yet known, every candidate runs twice on a scratch
-// copy of the factor with that update's rotation records, and the faster
-// candidate is kept (all candidates give identical results).  Choices are
+// nb = 0 whose shape is not yet known, every candidate runs on a scratch copy
+// of the factor with that update's rotation records (twice when a run takes
+// under 2 ms, the faster counting), and the fastest candidate is kept (all
+// candidates give identical results).  Choices are
 // cached for the process per (GPU, form, order of the factor, SMs left to the
 // apply) and, when the environment variable BDU_TUNE_FILE names a file, kept
 // there as a JSON object {"key": variant, ...}: read on first use, rewritten
@@ -548,6 +549,7 @@ bdu_status tune_side(bdu_ctx *h, int side, int sm_reserve) {
       float t = 0.f;
       if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
       if (ce == cudaSuccess && t < ms) ms = t;
+      if (t > 2.0f) break;  // long enough to time once
     }
     if (ce == cudaSuccess && ms < best_ms) { best_ms = ms; best = cand[c]; }
   }
