@@ -57,10 +57,10 @@ namespace bdu {
 namespace {
 
 constexpr int kMaxThreads = 256;
-// Stand-ins for band entries outside the stored diagonals: g_zero_sink[0]
-// always reads 0; g_zero_sink[1] is the address writes to such entries go to
-// (they are dropped, and a nonzero one is reported).  Never written.
-__device__ double g_zero_sink[2];  // the fully inlined chase code holds ~250 registers per thread
+// A placeholder address for band entries outside the stored diagonals: such
+// entries read as zero and their new values are checked (a nonzero one is
+// reported) instead of stored, so it is never read or written.
+__device__ double g_zero_sink[1];
 constexpr int kMaxCluster = 16;
 // Ops a chase may run in one step, each while it stays within the lag of the
 // chase ahead as that chase stood at the start of the step (which only moves
@@ -286,8 +286,7 @@ struct Chaser {
   int *err;
   double *Ux, *Vx;
   int rx;
-  double *zero;  // a cell that always reads 0: stands for entries outside the band
-  double *sink;  // a cell that absorbs writes to entries outside the band
+  double *zero;  // placeholder address of entries outside the band (never dereferenced)
 
   __device__ __forceinline__ bool inband(int i, int j) const {
     if (i < 1 || i > N || j < 1 || j > n) return false;
@@ -295,9 +294,9 @@ struct Chaser {
     const int o = j - i;
     return o >= -2 && o <= 3;
   }
-  __device__ __forceinline__ double *rd(int i, int j) const { return inband(i, j) ? S.cell(i, j) : zero; }
-  __device__ __forceinline__ double *wr(int i, int j) const { return inband(i, j) ? S.cell(i, j) : sink; }
-  __device__ __forceinline__ double get(int i, int j) const { return Store::load(rd(i, j)); }
+  // an entry outside the band reads as zero without a memory access (a chase's
+  // end test at the bottom of the band would otherwise wait on an L2 round trip)
+  __device__ __forceinline__ double get(int i, int j) const { return inband(i, j) ? Store::load(S.cell(i, j)) : 0.0; }
   __device__ __forceinline__ void rotate_extra(double *X, int ld, int a, double c, double s) {
     for (int t = 0; t < rx; t++) {
       double *U = X + (size_t)t * ld - 1;
@@ -645,10 +644,10 @@ __device__ __forceinline__ void engine_cta(const ChaseArgs &Ar, int use_smem) {
   if (me == 0) run_spike<FAST>(Ar, &cnt[0]);
   __syncthreads();
 
-  __shared__ double zero_cell, sink_cell;
-  if (me == 0) { zero_cell = 0.0; sink_cell = 0.0; }
+  __shared__ double zero_cell;
+  if (me == 0) zero_cell = 0.0;
   Chaser<LocalStore, FAST> K;
-  K.zero = &zero_cell; K.sink = &sink_cell;
+  K.zero = &zero_cell;
   K.N = N; K.n = n; K.m = m; K.err = Ar.status;
   K.Ux = Ar.Ux; K.Vx = Ar.Vx; K.rx = Ar.rx;
   const int64_t nband = 6 * (int64_t)(N + 2) + 2 * (int64_t)(n + 2) + (N + 2);
@@ -811,7 +810,7 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   cl.sync();  // spike done (global u)
 
   Chaser<GlobalStore, FAST> K;
-  K.zero = &g_zero_sink[0]; K.sink = &g_zero_sink[1];
+  K.zero = &g_zero_sink[0];
   K.S.dg0 = Ar.band.dg[0]; K.S.ld = N + 2;
   K.S.r1 = Ar.band.r1; K.S.u = Ar.band.u; K.S.v = Ar.band.v;
   K.N = N; K.n = n; K.m = m; K.err = Ar.status;

@@ -63,3 +63,27 @@ def test_reorthogonalization_reduces_the_error():
     assert st["reorth_q"] == 1
     after = np.linalg.norm(Qg.T @ Qg - np.eye(m), 2)
     assert after < 0.2 * before and after < 5e-6
+
+
+def test_block_stream_full_size_invariants():
+    """The rank-8 configuration at its full size (m = 8192, n = 2048, mixed
+    form, re-orthogonalization above 1e-6): after two updates the factors are
+    orthogonal to 1e-5 and a randomized residual ||A+ x - Q Bd P^T x|| / ||A+ x||
+    (probe vectors x, FP64 on the host) is at the level of FP32 rounding."""
+    m, n, r = 8192, 2048, 8
+    Q, d, e, P = I.factorization(m, n, config=2)
+    ups = [I.block_update(m, n, h, config=2, r=r) for h in range(2)]
+    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, reorth_tol=1e-6, check_every=1) as F:
+        for B, C in ups:
+            F.update(B, C)
+        q_est, p_est = F.check_orthogonality()
+        Qg, dg, eg, Pg = F.read()
+    assert q_est <= 1e-5 and p_est <= 1e-5
+    g = np.random.default_rng(7)
+    X = g.standard_normal((n, 3))
+    # A+ X = Q (Bd (P^T X)) + sum_h B_h (C_h^T X), all in FP64
+    want = Q @ (O.bidiag_dense(d, e, m) @ (P.T @ X))
+    for B, C in ups:
+        want += B @ (C.T @ X)
+    got = Qg @ (O.bidiag_dense(dg, eg, m) @ (Pg.T @ X))
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
