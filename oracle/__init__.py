@@ -12,6 +12,7 @@ update(Q, d, e, P, B, C)        full update, Eqs. rk1 / bidiagsubproblem / bidia
 generate(m, n, d, e, U, V)      the reduction only: rotation lists + new (d, e)
 apply_rows(X, rows, rotlist)    X(rows, :) <- X(rows, :) * prod(rotations)
 jacobi_sv(X)                    one-sided Jacobi singular values (tiny inputs)
+truncated_bd(Q, d, e, P, r)     truncated bidiagonal approximation, Eqs. trBD / errtrBD
 """
 import ctypes
 import os
@@ -225,3 +226,40 @@ def bidiag_dense(d, e, rows=None):
     if n > 1:
         M[np.arange(n - 1), np.arange(1, n)] = e
     return M
+
+
+def truncated_bd(Q, d, e, P, r):
+    """Truncated bidiagonal approximation (Sec. 2, Eq. trBD) and its error
+    (Eq. errtrBD), written out from their definitions.
+
+    With alpha_i = d_i, beta_i = e_i (beta_0 = 0), the rank-r approximation keeps
+    the r indices i with the largest alpha_i^2 + beta_{i-1}^2 (ties: the lower i
+    first) and is A_r = L R^T with L(:, k) = alpha_i q_i + beta_{i-1} q_{i-1},
+    R(:, k) = p_i, the kept indices in increasing order.  The error
+    ||A - A_r||_F^2 is the sum of alpha_i^2 + beta_{i-1}^2 over the others,
+    added in increasing i.  Weights, products and sums are separately rounded
+    FP64 operations.  Returns (L, R, idx (1-based i), err2).
+    """
+    Q = _f64(Q); P = _f64(P)
+    d = np.asarray(d, dtype=np.float64); e = np.asarray(e, dtype=np.float64)
+    n = len(d)
+    if not 0 <= r <= n:
+        raise ValueError("0 <= r <= n required")
+    w = np.empty(n)
+    for i in range(n):
+        a2 = d[i] * d[i]
+        w[i] = a2 if i == 0 else a2 + e[i - 1] * e[i - 1]
+    order = sorted(range(n), key=lambda i: (-w[i], i))
+    keep = sorted(order[:r])
+    kept = set(keep)
+    err2 = 0.0
+    for i in range(n):
+        if i not in kept:
+            err2 = err2 + w[i]
+    m = Q.shape[0]
+    L = np.zeros((m, r), order="F")
+    R = np.zeros((P.shape[0], r), order="F")
+    for k, i in enumerate(keep):
+        L[:, k] = d[i] * Q[:, i] if i == 0 else d[i] * Q[:, i] + e[i - 1] * Q[:, i - 1]
+        R[:, k] = P[:, i]
+    return L, R, np.array([i + 1 for i in keep], dtype=np.int64), err2

@@ -322,3 +322,61 @@ def test_pins_detect_a_wrong_rotation_sign():
     P2 = O.apply_rows(P, np.arange(n), R)
     Q2 = O.apply_rows(Q, np.arange(m), L)
     assert rel_resid(Aplus, Q2, d2, e2, P2) > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# truncated bidiagonal approximation (Sec. 2, Eqs. trBD, errtrBD)
+# ---------------------------------------------------------------------------
+def _random_bd(m, n, seed):
+    g = np.random.default_rng(seed)
+    Q = I.householder_orthogonal(m, g)
+    P = I.householder_orthogonal(n, g)
+    d = g.uniform(-3, 3, n)
+    e = g.standard_normal(max(n - 1, 0))
+    return Q, d, e, P
+
+
+@pytest.mark.parametrize("m,n,r", [(12, 9, 0), (12, 9, 1), (12, 9, 4), (12, 9, 9), (30, 30, 11), (7, 1, 1)])
+def test_truncated_bd_error_identity(m, n, r):
+    """||A - L R^T||_F^2, formed densely, equals the sum of the dropped
+    alpha_i^2 + beta_{i-1}^2 (Eq. errtrBD)."""
+    Q, d, e, P = _random_bd(m, n, 100 + m + n + r)
+    A = Q @ O.bidiag_dense(d, e, m) @ P.T
+    L, R, idx, err2 = O.truncated_bd(Q, d, e, P, r)
+    assert L.shape == (m, r) and R.shape == (n, r) and len(idx) == r
+    assert np.all(np.diff(idx) > 0) and (r == 0 or (idx[0] >= 1 and idx[-1] <= n))
+    direct = np.linalg.norm(A - L @ R.T, "fro") ** 2
+    assert abs(direct - err2) <= 1e-12 * max(1.0, np.linalg.norm(A, "fro") ** 2)
+    if r == n:
+        assert err2 == 0.0 and np.allclose(L @ R.T, A, rtol=0, atol=1e-13 * np.abs(A).max())
+
+
+def test_truncated_bd_keeps_the_largest_pairs():
+    """The kept set maximizes the captured energy: no swap of a kept and a
+    dropped index lowers the error (brute force over all r-subsets)."""
+    import itertools
+    Q, d, e, P = _random_bd(8, 6, 7)
+    w = d ** 2 + np.concatenate([[0.0], e ** 2])
+    _, _, idx, err2 = O.truncated_bd(Q, d, e, P, 3)
+    best = min(sum(w) - sum(w[list(c)]) for c in itertools.combinations(range(6), 3))
+    assert abs(err2 - best) <= 1e-14 * sum(w)
+
+
+def test_truncated_bd_of_a_diagonal_is_the_truncated_svd():
+    """beta = 0: the bidiagonal decomposition is an SVD (up to signs), so the
+    truncation keeps the r largest |alpha| and its error is the sum of the
+    other sigma^2 (the Eckart-Young error of the truncated SVD)."""
+    g = np.random.default_rng(3)
+    m, n, r = 10, 7, 3
+    Q = I.householder_orthogonal(m, g)
+    P = I.householder_orthogonal(n, g)
+    d = g.uniform(-5, 5, n)
+    e = np.zeros(n - 1)
+    A = Q @ O.bidiag_dense(d, e, m) @ P.T
+    L, R, idx, err2 = O.truncated_bd(Q, d, e, P, r)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert abs(err2 - np.sum(sv[r:] ** 2)) <= 1e-12 * np.sum(sv ** 2)
+    U, S, Vt = np.linalg.svd(A)
+    Ar = (U[:, :r] * S[:r]) @ Vt[:r]
+    assert np.linalg.norm(L @ R.T - Ar) <= 1e-12 * np.linalg.norm(A)
+    assert set(idx - 1) == set(np.argsort(-np.abs(d))[:r])
