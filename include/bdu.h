@@ -177,6 +177,18 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P);
 bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
                               int64_t cap, int64_t *count);
 
+/* Truncated bidiagonal approximation of the current factorization (Sec. 2,
+ * Eq. trBD): with alpha_i = d_i, beta_i = e_i and beta_0 = 0, keeps the r
+ * indices i with the largest alpha_i^2 + beta_{i-1}^2 (on ties the lower i),
+ * listed in increasing order in idx (1-based), and returns A_r = L R^T with
+ * L(:, k) = alpha_i q_i + beta_{i-1} q_{i-1} (m x r) and R(:, k) = p_i (n x r),
+ * column-major FP64 (in the mixed form from the FP32 factors), and in *err2
+ * the exact error ||A - A_r||_F^2 = the sum of alpha_i^2 + beta_{i-1}^2 over
+ * the other indices (Eq. errtrBD; exact for orthogonal Q and P).  0 <= r <= n
+ * (BDU_EINVAL otherwise).  Host buffers, any may be NULL; completes deferred
+ * work first and synchronizes. */
+bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int64_t *idx, double *err2);
+
 /* Enqueues on the handle's stream every part of earlier updates that the
  * overlapped form defers (the application of the latest rank-1 column to Q
  * and P), so that work the caller enqueues afterwards on that stream sees the

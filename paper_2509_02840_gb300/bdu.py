@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
     L.bdu_read_rotations.argtypes = [H, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.bdu_read_rotations.restype = ctypes.c_int
+    L.bdu_read_truncated.argtypes = [H, ctypes.c_int64, dp, dp, ctypes.POINTER(ctypes.c_int64), dp]
+    L.bdu_read_truncated.restype = ctypes.c_int
     L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
     L.bdu_stats.restype = ctypes.c_int
     L.bdu_update_batch.argtypes = [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
@@ -258,6 +260,17 @@ class Factorization:
         _check(self._L, self._h, self._L.bdu_read_rotations(
             self._h, side, _dp(c), _dp(s), a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), k, ctypes.byref(cnt)))
         return c[:k], s[:k], a[:k]
+
+    def read_truncated(self, r):
+        """Truncated bidiagonal approximation A_r = L R^T (bdu_read_truncated):
+        returns (L m x r, R n x r, idx (1-based kept indices), err2)."""
+        r = int(r)
+        L = np.zeros((self.m, max(r, 1)), order="F"); R = np.zeros((self.n, max(r, 1)), order="F")
+        idx = np.zeros(max(r, 1), dtype=np.int64)
+        err2 = ctypes.c_double()
+        _check(self._L, self._h, self._L.bdu_read_truncated(
+            self._h, r, _dp(L), _dp(R), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(err2)))
+        return L[:, :r], R[:, :r], idx[:r], err2.value
 
     def stats(self):
         st = Stats()

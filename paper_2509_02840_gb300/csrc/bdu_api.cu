@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -582,6 +583,26 @@ bdu_status maybe_tune(bdu_ctx *h) {
 bdu_status finish_update(bdu_ctx *h, int64_t r) {
   const bdu_status st = maybe_tune(h);
   return st != BDU_OK ? st : maybe_reorth(h, r);
+}
+
+// Copies d (n) and e (n-1) of the current bidiagonal from the band to the
+// host (either may be null); synchronizes the handle's stream.
+cudaError_t read_bidiagonal(bdu_ctx *h, double *d, double *e) {
+  const int64_t m = h->m, n = h->n;
+  std::vector<double> hb(band_doubles(m, n));
+  cudaError_t ce = cudaMemcpyAsync(hb.data(), h->band, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return ce;
+  BandPtrs hp = band_ptrs(hb.data(), m, n);
+  if (d) {
+    d[0] = hp.r1[1];
+    for (int64_t i = 2; i <= n; i++) d[i - 1] = hp.dg[2][i];
+  }
+  if (e && n > 1) {
+    e[0] = hp.r1[2];
+    for (int64_t i = 2; i <= n - 1; i++) e[i - 1] = hp.dg[3][i];
+  }
+  return cudaSuccess;
 }
 
 bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
@@ -1266,23 +1287,7 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
   };
   fetch(h->Q, Q, m * m);
   fetch(h->P, P, n * n);
-  if (d || e) {
-    std::vector<double> hb(band_doubles(m, n));
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(hb.data(), h->band, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, h->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    if (ce == cudaSuccess) {
-      BandPtrs hp = band_ptrs(hb.data(), m, n);
-      if (d) {
-        d[0] = hp.r1[1];
-        for (int64_t i = 2; i <= n; i++) d[i - 1] = hp.dg[2][i];
-      }
-      if (e && n > 1) {
-        e[0] = hp.r1[2];
-        for (int64_t i = 2; i <= n - 1; i++) e[i - 1] = hp.dg[3][i];
-      }
-    }
-  }
+  if ((d || e) && ce == cudaSuccess) ce = read_bidiagonal(h, d, e);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read");
   return st;
@@ -1346,6 +1351,79 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
       put(hc[i], hs[i], ha[i]);
     }
   *count = k;
+  return BDU_OK;
+}
+
+bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int64_t *idx, double *err2) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (r < 0 || r > h->n) return fail(h, BDU_EINVAL, "bdu_read_truncated: need 0 <= r <= n (r=%lld)", (long long)r);
+  cudaSetDevice(h->device);
+  bdu_status st = BDU_OK;
+  if (!h->poisoned) st = flush_apply(h);
+  if (st == BDU_OK && !h->poisoned) st = settle_probe(h);
+  if (st == BDU_OK && !h->poisoned) st = check_device_status(h);
+  if (st != BDU_OK) return st;
+  const int64_t m = h->m, n = h->n;
+  std::vector<double> d(n), e(n > 1 ? n - 1 : 1);
+  cudaError_t ce = read_bidiagonal(h, d.data(), e.data());
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_truncated");
+  // weights alpha_i^2 + beta_{i-1}^2 (Eq. errtrBD), each product rounded on its
+  // own (volatile keeps the host compiler from fusing them into an FMA); the r
+  // largest, lower i first on ties
+  std::vector<double> w(n);
+  for (int64_t i = 0; i < n; i++) {
+    volatile double a2 = d[i] * d[i];
+    if (i == 0) {
+      w[i] = a2;
+    } else {
+      volatile double b2 = e[i - 1] * e[i - 1];
+      w[i] = a2 + b2;
+    }
+  }
+  std::vector<int64_t> order(n);
+  for (int64_t i = 0; i < n; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return w[a] > w[b]; });
+  std::vector<int64_t> keep(order.begin(), order.begin() + r);
+  std::sort(keep.begin(), keep.end());
+  std::vector<char> kept(n, 0);
+  for (int64_t i : keep) kept[i] = 1;
+  double err = 0.0;
+  for (int64_t i = 0; i < n; i++)
+    if (!kept[i]) err = err + w[i];
+  if (err2) *err2 = err;
+  if (idx)
+    for (int64_t k = 0; k < r; k++) idx[k] = keep[k] + 1;
+  if (r == 0 || (!L && !R)) return BDU_OK;
+  // the columns of L and R, formed on the device
+  std::vector<int32_t> hi(r);
+  std::vector<double> ha(r), hbt(r);
+  for (int64_t k = 0; k < r; k++) {
+    const int64_t i = keep[k];
+    hi[k] = (int32_t)(i + 1);
+    ha[k] = d[i];
+    hbt[k] = i > 0 ? e[i - 1] : 0.0;
+  }
+  const size_t bytes = sizeof(double) * (size_t)(m + n) * r + sizeof(double) * 2 * r + sizeof(int32_t) * r + 64;
+  char *ws = (char *)dev_alloc(h, bytes);
+  if (!ws) return fail(h, BDU_ENOMEM, "bdu_read_truncated: workspace allocation failed");
+  double *dL = (double *)ws;
+  double *dR = dL + (size_t)m * r;
+  double *da = dR + (size_t)n * r;
+  double *db = da + r;
+  int32_t *di = (int32_t *)(db + r);
+  cudaStream_t s = h->stream;
+  ce = cudaMemcpyAsync(da, ha.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(db, hbt.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(di, hi.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = launch_truncate(h->opt.precision, h->Q, m, h->P, n, di, da, db, (int)r, dL, dR, s);
+  if (ce == cudaSuccess && L) ce = cudaMemcpyAsync(L, dL, sizeof(double) * (size_t)m * r, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && R) ce = cudaMemcpyAsync(R, dR, sizeof(double) * (size_t)n * r, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  dev_free(h, ws);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_truncated");
+  h->launches += 1;
   return BDU_OK;
 }
 
