@@ -13,6 +13,7 @@ generate(m, n, d, e, U, V)      the reduction only: rotation lists + new (d, e)
 apply_rows(X, rows, rotlist)    X(rows, :) <- X(rows, :) * prod(rotations)
 jacobi_sv(X)                    one-sided Jacobi singular values (tiny inputs)
 truncated_bd(Q, d, e, P, r)     truncated bidiagonal approximation, Eqs. trBD / errtrBD
+singular_values(d, e)           singular values of the bidiagonal (library SVD)
 """
 import ctypes
 import os
@@ -263,3 +264,9 @@ def truncated_bd(Q, d, e, P, r):
         L[:, k] = d[i] * Q[:, i] if i == 0 else d[i] * Q[:, i] + e[i - 1] * Q[:, i - 1]
         R[:, k] = P[:, i]
     return L, R, np.array([i + 1 for i in keep], dtype=np.int64), err2
+
+
+def singular_values(d, e):
+    """Singular values of the upper bidiagonal (d, e), descending: the plain
+    definition, evaluated by a library SVD of the dense n x n matrix."""
+    return np.linalg.svd(bidiag_dense(d, e), compute_uv=False)

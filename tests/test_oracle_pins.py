@@ -380,3 +380,30 @@ def test_truncated_bd_of_a_diagonal_is_the_truncated_svd():
     Ar = (U[:, :r] * S[:r]) @ Vt[:r]
     assert np.linalg.norm(L @ R.T - Ar) <= 1e-12 * np.linalg.norm(A)
     assert set(idx - 1) == set(np.argsort(-np.abs(d))[:r])
+
+
+# ---------------------------------------------------------------------------
+# singular values of the bidiagonal
+# ---------------------------------------------------------------------------
+def test_bidiagonal_singular_values_2x2_closed_form():
+    """[[a, b], [0, c]]: sigma_1 sigma_2 = |a c| and
+    sigma_1^2 + sigma_2^2 = a^2 + b^2 + c^2."""
+    for a, b, c in ((3.0, 4.0, 5.0), (-1.0, 0.5, 2.0), (1e-3, 7.0, -2.0), (2.0, 0.0, 3.0)):
+        s1, s2 = O.singular_values([a, c], [b])
+        assert abs(s1 * s2 - abs(a * c)) <= 1e-14 * s1 * s1
+        assert abs(s1 * s1 + s2 * s2 - (a * a + b * b + c * c)) <= 1e-14 * (a * a + b * b + c * c)
+
+
+def test_bidiagonal_singular_values_match_jacobi_and_the_full_matrix():
+    """Against the oracle's own one-sided Jacobi (independent code) on small
+    random bidiagonals, and against the singular values of A = Q Bd P^T."""
+    g = np.random.default_rng(11)
+    for n in (1, 3, 8, 15):
+        d = g.standard_normal(n) * 3
+        e = g.standard_normal(n - 1)
+        sv = O.singular_values(d, e)
+        assert np.allclose(sv, O.jacobi_sv(O.bidiag_dense(d, e)), rtol=0, atol=1e-13 * sv[0])
+        Q = I.householder_orthogonal(n + 4, g)
+        P = I.householder_orthogonal(n, g)
+        A = Q @ O.bidiag_dense(d, e, n + 4) @ P.T
+        assert np.allclose(sv, np.linalg.svd(A, compute_uv=False), rtol=0, atol=1e-12 * sv[0])
