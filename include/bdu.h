@@ -189,6 +189,14 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
  * work first and synchronizes. */
 bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int64_t *idx, double *err2);
 
+/* The k largest singular values of the current bidiagonal Bd (those of A when
+ * Q and P are orthogonal; Sec. 2), in descending order, computed on the device
+ * by multisection with Sturm counts on the Golub-Kahan tridiagonal matrix of
+ * Bd (absolute accuracy about 1e-15 of the largest).  0 <= k <= n (BDU_EINVAL
+ * otherwise); sv is a host buffer of k doubles.  Needs no deferred work to
+ * complete (Bd is current after every update); synchronizes. */
+bdu_status bdu_singular_values(bdu_handle h, int64_t k, double *sv);
+
 /* Enqueues on the handle's stream every part of earlier updates that the
  * overlapped form defers (the application of the latest rank-1 column to Q
  * and P), so that work the caller enqueues afterwards on that stream sees the

@@ -85,6 +85,8 @@ def load(build_if_missing: bool = True):
     L.bdu_read_rotations.restype = ctypes.c_int
     L.bdu_read_truncated.argtypes = [H, ctypes.c_int64, dp, dp, ctypes.POINTER(ctypes.c_int64), dp]
     L.bdu_read_truncated.restype = ctypes.c_int
+    L.bdu_singular_values.argtypes = [H, ctypes.c_int64, dp]
+    L.bdu_singular_values.restype = ctypes.c_int
     L.bdu_stats.argtypes = [H, ctypes.POINTER(Stats)]
     L.bdu_stats.restype = ctypes.c_int
     L.bdu_update_batch.argtypes = [ctypes.POINTER(H), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
@@ -271,6 +273,13 @@ class Factorization:
         _check(self._L, self._h, self._L.bdu_read_truncated(
             self._h, r, _dp(L), _dp(R), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(err2)))
         return L[:, :r], R[:, :r], idx[:r], err2.value
+
+    def singular_values(self, k=None):
+        """The k largest singular values of Bd, descending (bdu_singular_values)."""
+        k = self.n if k is None else int(k)
+        sv = np.zeros(max(k, 1))
+        _check(self._L, self._h, self._L.bdu_singular_values(self._h, k, _dp(sv)))
+        return sv[:k]
 
     def stats(self):
         st = Stats()

@@ -2,6 +2,7 @@
 // argument validation, device memory, and the order of the kernels of one
 // update (Sec. 3.2: project, reduce, compose).
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1423,6 +1424,51 @@ bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   dev_free(h, ws);
   if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_read_truncated");
+  h->launches += 1;
+  return BDU_OK;
+}
+
+bdu_status bdu_singular_values(bdu_handle h, int64_t k, double *sv) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (k < 0 || k > h->n) return fail(h, BDU_EINVAL, "bdu_singular_values: need 0 <= k <= n (k=%lld)", (long long)k);
+  if (k > 0 && !sv) return fail(h, BDU_EINVAL, "bdu_singular_values: NULL output");
+  cudaSetDevice(h->device);
+  bdu_status st = BDU_OK;
+  if (!h->poisoned) st = settle_probe(h);
+  if (st == BDU_OK && !h->poisoned) st = check_device_status(h);
+  if (st != BDU_OK) return st;
+  if (k == 0) return BDU_OK;
+  const int64_t n = h->n;
+  std::vector<double> d(n), e(n > 1 ? n - 1 : 1);
+  cudaError_t ce = read_bidiagonal(h, d.data(), e.data());
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_singular_values");
+  // Golub-Kahan off-diagonal d_1, e_1, ..., d_n: squares, a Gershgorin bound
+  // of sigma_max and the smallest pivot magnitude
+  std::vector<double> b2(2 * n - 1);
+  double bmax2 = 0.0, hi = 0.0, prev = 0.0;
+  for (int64_t i = 0; i < 2 * n - 1; i++) {
+    const double b = fabs((i & 1) ? e[i / 2] : d[i / 2]);
+    b2[i] = b * b;
+    bmax2 = b2[i] > bmax2 ? b2[i] : bmax2;
+    hi = prev + b > hi ? prev + b : hi;
+    prev = b;
+  }
+  hi = prev > hi ? prev : hi;
+  hi = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
+  const double pivmin = DBL_MIN * (bmax2 > 1.0 ? bmax2 : 1.0);
+  const size_t bytes = sizeof(double) * (size_t)(2 * n - 1 + k) + 64;
+  double *ws = (double *)dev_alloc(h, bytes);
+  if (!ws) return fail(h, BDU_ENOMEM, "bdu_singular_values: workspace allocation failed");
+  double *db2 = ws, *dsv = ws + (2 * n - 1);
+  cudaStream_t s = h->stream;
+  ce = cudaMemcpyAsync(db2, b2.data(), sizeof(double) * b2.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = launch_bidiag_svals(db2, (int)n, hi, pivmin, (int)k, dsv, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(sv, dsv, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  dev_free(h, ws);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_singular_values");
   h->launches += 1;
   return BDU_OK;
 }

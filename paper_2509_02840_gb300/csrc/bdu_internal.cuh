@@ -142,6 +142,10 @@ cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m,
 // R(:, k) = p_i, i = idx[k] (1-based), in FP64 (L m x r, R n x r, column-major).
 cudaError_t launch_truncate(int precision, const void *Q, int64_t m, const void *P, int64_t n, const int32_t *idx,
                             const double *alpha, const double *beta, int r, double *L, double *R, cudaStream_t s);
+// The k largest singular values (descending) of the bidiagonal whose
+// Golub-Kahan off-diagonal entries squared are b2[0 .. 2n-2] (all on the device).
+cudaError_t launch_bidiag_svals(const double *b2, int n, double hi, double pivmin, int k, double *sv,
+                                cudaStream_t s);
 cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const int *d_first, int count,
                                int total_slabs, size_t smem, cudaStream_t s);
 cudaError_t launch_project_batch(int precision, const ProjItem *d_items, int count, int max_nrow,
