@@ -96,6 +96,10 @@ typedef struct {
                          Not used for overlapped rank-1 updates or while timing is on.
                          The capture runs on the handle's stream: work that other threads
                          enqueue on that stream during an update would be captured too. */
+  int64_t step_budget; /* watchdog of the chase: synchronous steps allowed per rank-1
+                         column before the kernel stops and the update fails with
+                         BDU_ETIMEOUT (poisoning the handle); 0 = 64 (n + 16) + 4096
+                         (default; a column needs about 11 n) */
 } bdu_options;
 
 typedef struct {

@@ -27,7 +27,8 @@ class BduError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int), ("overlap", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("overlap", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("step_budget", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -178,7 +179,8 @@ class Factorization:
     """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
-                 check_every=None, engine=0, overlap=False, graphs=True, nb=0):
+                 check_every=None, engine=0, overlap=False, graphs=True, nb=0,
+                 step_budget=0):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -192,6 +194,7 @@ class Factorization:
         opt.overlap = 1 if overlap else 0
         opt.graphs = 1 if graphs else 0
         opt.nb = int(nb)
+        opt.step_budget = int(step_budget)
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:

@@ -668,6 +668,7 @@ bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
   a.st = h->st; a.status = h->status; a.counters = h->counters;
   a.fast = 1;
   a.engine = h->opt.engine;
+  a.step_budget = h->opt.step_budget;
   {
     Timer tm(h, 1, sc);
     e = launch_chase(a, sc);
@@ -714,7 +715,7 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Ln, 0, sizeof(int32_t) * h->st.T, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Rn, 0, sizeof(int32_t) * h->st.T, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "staging a rank-1 column");
-    ChaseArgs a;
+    ChaseArgs a{};
     a.m = m; a.n = n; a.band = bp;
     a.rx = (int)(r - k - 1);
     a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
@@ -722,6 +723,7 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
     a.st = h->st; a.status = h->status; a.counters = h->counters;
     a.fast = (h->opt.precision == BDU_MIXED) ? 1 : 0;
     a.engine = h->opt.engine;
+    a.step_budget = h->opt.step_budget;
     {
       Timer tm(h, 1);
       e = launch_chase(a, s);
@@ -852,6 +854,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->engine = 0;
   opt->overlap = 0;
   opt->graphs = 1;
+  opt->step_budget = 0;
 }
 
 int bdu_version(void) { return 100; }
@@ -901,6 +904,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown precision %d", o.precision);
   if (o.engine < 0 || o.engine > 2)
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
+  if (o.step_budget < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative step budget");
   if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1)) : (o.nb < 0 || o.nb > kSlabVariant))
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown apply variant nb=%d", o.nb);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
@@ -1161,6 +1165,7 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
       a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
       a.st = h->st; a.status = h->status; a.counters = h->counters;
       a.fast = precision == BDU_MIXED ? 1 : 0;
+      a.step_budget = h->opt.step_budget;
       if (n >= kClusterBatchMinN) {
         a.engine = 2;
         chase_l.push_back(a);

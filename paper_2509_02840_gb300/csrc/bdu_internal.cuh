@@ -83,6 +83,7 @@ struct ChaseArgs {
   unsigned long long *counters;  // [0..3] left by phase, [4..7] right by phase, [8] steps
   int fast;           // 1: fused multiply-add / Newton rotation arithmetic (mixed form)
   int engine;         // 0: by size, 1: one CTA, 2: thread-block cluster
+  long long step_budget;  // bound on synchronous steps per column; 0: 64 (n + 16) + 4096
 };
 
 // One matrix (Q or P of one factorization) for the batched apply.

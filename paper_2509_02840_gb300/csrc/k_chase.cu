@@ -681,7 +681,7 @@ __device__ __forceinline__ void engine_cta(const ChaseArgs &Ar, int use_smem) {
     p1done = 0; ndone = 0;
   }
   bool fold_done = false;
-  const long long max_steps = 64LL * (n + 16) + 4096;
+  const long long max_steps = Ar.step_budget > 0 ? Ar.step_budget : 64LL * (n + 16) + 4096;
   long long step = 0;
   for (;; step++) {
     // Snapshot the shared counters between two barriers: during the step they
@@ -841,7 +841,7 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
     }
   }
   bool fold_done = false;
-  const long long max_steps = 64LL * (n + 16) + 4096;
+  const long long max_steps = Ar.step_budget > 0 ? Ar.step_budget : 64LL * (n + 16) + 4096;
   long long step = 0;
   for (;; step++) {
     cl.sync();  // every write of the previous step is visible cluster-wide
