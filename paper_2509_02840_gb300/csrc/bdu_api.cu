@@ -99,6 +99,7 @@ struct bdu_ctx {
   int cur;               // buffer of the most recent rank-1 column
   bool pend;             // that column's application to Q, P is not enqueued yet
   bool apply_ev_set[2];
+  bool pipe_ok, pipe_failed;  // rank-r pipeline resources present / could not be made
   cudaStream_t sa;       // applications (lowest priority)
   cudaStream_t sc;       // projections' rotation and chases (highest priority)
   cudaEvent_t ev_call, ev_proj, ev_rot, ev_chase, ev_apply[2];
@@ -688,6 +689,134 @@ bdu_status run_overlapped(bdu_ctx *h, const double *dB, const double *dC) {
 }
 
 // One update with B, C already in device memory.
+bool alloc_records(bdu_ctx *h, RotStream &r, int T, int cap, int64_t m, bool mixed);
+
+// Resources of the rank-r pipeline: a second record buffer, a chase stream of
+// the greatest priority and an apply stream of the least (so that, when a
+// column's application and the next column's chase become ready together, the
+// chase's cluster is placed first), and events.  Made on the first rank-r
+// update; false when they cannot be (the update then runs column by column).
+bool ensure_pipeline(bdu_ctx *h) {
+  if (h->pipe_ok) return true;
+  if (h->pipe_failed) return false;
+  h->pipe_failed = true;
+  if (!h->stb[1].La) {
+    h->stb[0] = h->st;
+    h->cur = 0;
+    if (!alloc_records(h, h->stb[1], h->st.T, h->st.cap, h->m, h->opt.precision == BDU_MIXED)) {
+      for (void *p : {(void *)h->stb[1].Lc, (void *)h->stb[1].Ls, (void *)h->stb[1].Rc, (void *)h->stb[1].Rs,
+                      (void *)h->stb[1].La, (void *)h->stb[1].Ra, (void *)h->stb[1].Ln, (void *)h->stb[1].Rn,
+                      (void *)h->stb[1].Sc, (void *)h->stb[1].Ss, (void *)h->stb[1].Sa, (void *)h->stb[1].Sn,
+                      (void *)h->stb[1].Lf, (void *)h->stb[1].Rf, (void *)h->stb[1].Sf, (void *)h->stb[1].Lm,
+                      (void *)h->stb[1].Rm})
+        dev_free(h, p);
+      h->stb[1] = RotStream{};
+      return false;
+    }
+  }
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (!h->sa && cudaStreamCreateWithPriority(&h->sa, cudaStreamNonBlocking, least) != cudaSuccess) h->sa = nullptr;
+  if (!h->sc && cudaStreamCreateWithPriority(&h->sc, cudaStreamNonBlocking, greatest) != cudaSuccess) h->sc = nullptr;
+  for (cudaEvent_t *ev : {&h->ev_call, &h->ev_chase, &h->ev_apply[0], &h->ev_apply[1]})
+    if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) *ev = nullptr;
+  if (!h->sa || !h->sc || !h->ev_call || !h->ev_chase || !h->ev_apply[0] || !h->ev_apply[1]) {
+    cudaGetLastError();
+    return false;
+  }
+  h->pipe_failed = false;
+  h->pipe_ok = true;
+  return true;
+}
+
+// The columns of a rank-r update, pipelined: column k's chase runs on the
+// chase stream while column k-1 is applied to Q and P on the apply stream.
+// The later columns' projections are rotated inside the chases (U(:, k+1:r),
+// V(:, k+1:r)), so no column waits for an earlier column's application, and
+// the results are those of the column-by-column order.  Record buffers
+// alternate; a buffer is reused only after its column's application.
+bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
+  const int m = (int)h->m, n = (int)h->n;
+  cudaStream_t s = h->stream, sc = h->sc, sa = h->sa;
+  BandPtrs bp = band_ptrs(h->band, m, n);
+  cudaError_t e = cudaEventRecord(h->ev_call, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, h->ev_call, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sa, h->ev_call, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering the rank-r pipeline");
+  // Column k-1's application is enqueued once column k is staged, so that it
+  // and column k's chase become ready together and the chase (on the stream
+  // of greater priority) is placed first; the application leaves it SMs.
+  auto enqueue_apply_of = [&](int buf, int reserve) -> bdu_status {
+    cudaError_t ee = cudaEventRecord(h->ev_chase, sc);
+    if (ee == cudaSuccess) ee = cudaStreamWaitEvent(sa, h->ev_chase, 0);
+    if (ee != cudaSuccess) return cuda_fail(h, ee, "ordering the rank-r pipeline");
+    {
+      Timer tm(h, 2, sa);
+      ee = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, sa, h->status, reserve, false,
+                        h->apply_var[0]);
+      if (ee != cudaSuccess) return cuda_fail(h, ee, "apply to Q");
+    }
+    {
+      Timer tm(h, 3, sa);
+      ee = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, sa, h->status, reserve, false,
+                        h->apply_var[1]);
+      if (ee != cudaSuccess) return cuda_fail(h, ee, "apply to P");
+    }
+    ee = cudaEventRecord(h->ev_apply[buf], sa);
+    if (ee != cudaSuccess) return cuda_fail(h, ee, "ordering the rank-r pipeline");
+    h->launches += 2;
+    if (h->timing) h->apply_launches += 2;
+    return BDU_OK;
+  };
+  int b = h->cur;
+  for (int64_t k = 0; k < r; k++) {
+    b ^= 1;
+    RotStream &sb = h->stb[b];
+    // this buffer's previous column (k-2) is applied before it is reused
+    // (earlier calls' applications are behind the caller's stream already)
+    if (k >= 2) e = cudaStreamWaitEvent(sc, h->ev_apply[b], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pipelined column: waiting for its record buffer");
+    e = cudaMemcpyAsync(bp.u + 1, h->U + k * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, sc);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bp.v + 1, h->V + k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, sc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pipelined column: staging u, v");
+    e = cudaMemsetAsync(sb.Ln, 0, sizeof(int32_t) * sb.T, sc);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sb.Rn, 0, sizeof(int32_t) * sb.T, sc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pipelined column: clearing the record counts");
+    if (k > 0) {
+      const bdu_status st = enqueue_apply_of(b ^ 1, kChaseSMs);
+      if (st != BDU_OK) return st;
+    }
+    ChaseArgs a{};
+    a.m = m; a.n = n; a.band = bp;
+    a.rx = (int)(r - k - 1);
+    a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
+    a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
+    a.st = sb; a.status = h->status; a.counters = h->counters;
+    a.fast = (h->opt.precision == BDU_MIXED) ? 1 : 0;
+    a.engine = h->opt.engine;
+    a.step_budget = h->opt.step_budget;
+    {
+      Timer tm(h, 1, sc);
+      e = launch_chase(a, sc);
+      if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+    }
+    h->launches += 1;
+    h->updates++;
+  }
+  const bdu_status st = enqueue_apply_of(b, 0);
+  if (st != BDU_OK) return st;
+  // the caller's stream continues after the last application (which follows
+  // the last chase on the apply stream); later work ordered after that stream
+  // needs no wait on the buffers' events, which may have been recorded inside
+  // a graph capture and cannot be waited on outside it
+  e = cudaStreamWaitEvent(s, h->ev_apply[b], 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ordering the rank-r pipeline");
+  h->apply_ev_set[0] = h->apply_ev_set[1] = false;
+  h->cur = b;
+  h->st = h->stb[b];
+  return BDU_OK;
+}
+
 // Enqueues the launches of a plain update (every rank-1 column in turn).
 bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
   const int m = (int)h->m, n = (int)h->n;
@@ -706,6 +835,7 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
     if (e != cudaSuccess) return cuda_fail(h, e, "projection of C");
     h->launches += 4;
   }
+  if (r > 1 && ensure_pipeline(h)) return enqueue_columns_pipelined(h, r);
   BandPtrs bp = band_ptrs(h->band, m, n);
   for (int64_t k = 0; k < r; k++) {
     // u = U(:,k), v = V(:,k) (1-based in the band buffer)

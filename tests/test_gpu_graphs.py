@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2509_02840_gb300 import bdu, inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -63,3 +64,41 @@ def test_device_inputs_and_timing():
     for x, y in zip(got, ref):
         assert np.array_equal(x, y)
     assert st["graph_replays"] == 3 and st["timed_updates"] == 1
+
+
+@pytest.mark.parametrize("precision", [bdu.FP64, bdu.MIXED])
+def test_rank_r_pipeline_equals_column_by_column(precision):
+    """A rank-r call runs column k's chase beside column k-1's application
+    (with and without graph replay); the batched path applies the columns one
+    after another.  All three must agree bit for bit, and the FP64 form with
+    the oracle."""
+    m, n = 300, 260
+    Q, d, e, P = I.factorization(m, n, config=0, which=77)
+    ranks = [3, 2, 2, 4, 4, 1, 2]
+    ups = [I.dense_update(m, n, h, config=0, r=r) for h, r in enumerate(ranks)]
+    kw = dict(precision=precision, nb=8 if precision == bdu.FP64 else 1,
+              check_every=0 if precision == bdu.MIXED else None)
+    outs = []
+    for graphs in (True, False):
+        with bdu.Factorization(Q, d, e, P, graphs=graphs, **kw) as F:
+            for B, C in ups:
+                F.update(B, C)
+            st = F.stats()
+            outs.append(F.read())
+        if graphs:
+            assert st["graph_replays"] == 2  # the second rank-2 and the second rank-4 call
+    with bdu.Factorization(Q, d, e, P, **kw) as F:
+        for B, C in ups:
+            tb = torch.from_numpy(B.reshape(-1, order="F").copy()).cuda()
+            tc = torch.from_numpy(C.reshape(-1, order="F").copy()).cuda()
+            torch.cuda.synchronize()
+            bdu.update_batch([F], [tb.data_ptr()], [tc.data_ptr()], [B.shape[1]])
+        outs.append(F.read())
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
+    if precision == bdu.FP64:
+        for B, C in ups:
+            Q, d, e, P, _ = O.update(Q, d, e, P, B, C)
+        for a, b in zip(outs[0], (Q, d, e, P)):
+            assert np.array_equal(a, b)
