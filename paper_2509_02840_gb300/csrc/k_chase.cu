@@ -297,12 +297,26 @@ struct Chaser {
   // an entry outside the band reads as zero without a memory access (a chase's
   // end test at the bottom of the band would otherwise wait on an L2 round trip)
   __device__ __forceinline__ double get(int i, int j) const { return inband(i, j) ? Store::load(S.cell(i, j)) : 0.0; }
+  // The later columns of U (V) of a rank-r update: entries (a, a+1) of each
+  // rotated like the band's pair.  Loads of four columns are issued together,
+  // so that they share one L2 round trip.
   __device__ __forceinline__ void rotate_extra(double *X, int ld, int a, double c, double s) {
-    for (int t = 0; t < rx; t++) {
-      double *U = X + (size_t)t * ld - 1;
-      const double xu = Store::load(U + a), yu = Store::load(U + a + 1);
-      U[a] = A::px(c, s, xu, yu);
-      U[a + 1] = A::py(c, s, xu, yu);
+    for (int t0 = 0; t0 < rx; t0 += 4) {
+      double xu[4], yu[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const double *U = X + (size_t)(t0 + q) * ld - 1;
+        xu[q] = t0 + q < rx ? Store::load(U + a) : 0.0;
+        yu[q] = t0 + q < rx ? Store::load(U + a + 1) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (t0 + q < rx) {
+          double *U = X + (size_t)(t0 + q) * ld - 1;
+          U[a] = A::px(c, s, xu[q], yu[q]);
+          U[a + 1] = A::py(c, s, xu[q], yu[q]);
+        }
+      }
     }
   }
 
