@@ -339,6 +339,10 @@ def run_gpu(args):
     launches = (st["launches"] - st0["launches"])
     roof = roofline(st, 1, rot_per_update, launches / K, (st["chase_steps"] - st0["chase_steps"]) / K)
     res_mixed = residual(Fm, (Q, d, e, P), ups[:W + K])
+    ortho_q, ortho_p = Fm.check_orthogonality()
+    ortho = {"q": ortho_q, "p": ortho_p, "tolerance": 1e-5, "reorth_q": st["reorth_q"] - st0["reorth_q"],
+             "reorth_p": st["reorth_p"] - st0["reorth_p"],
+             "policy": "one Newton-Schulz step (FP32 products, FP64 diagonal) after every rank-1 column"}
 
     if args.quick:
         Fm.close()
@@ -398,6 +402,7 @@ def run_gpu(args):
         "fp64_form": {"value": 1e3 / statistics.mean(ms64), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
                       "steps": len(ms64), "relative_residual": res64},
         "mixed_relative_residual": res_mixed,
+        "mixed_orthogonality": ortho,
         "mixed_vs_fp64_speedup": (K / (total_ms / 1e3)) / (1e3 / statistics.mean(ms64)),
         "kernel_ms_per_update": {"project": st["ms_project"] / max(st["timed_updates"], 1),
                                  "chase": st["ms_chase"] / max(st["timed_updates"], 1),

@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nb", ctypes.c_int), ("reorth_tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("engine", ctypes.c_int), ("overlap", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("step_budget", ctypes.c_int64)]
+                ("step_budget", ctypes.c_int64), ("reorth_every", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -180,7 +180,7 @@ class Factorization:
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
                  check_every=None, engine=0, overlap=False, graphs=True, nb=0,
-                 step_budget=0):
+                 step_budget=0, reorth_every=None):
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
@@ -195,6 +195,8 @@ class Factorization:
         opt.graphs = 1 if graphs else 0
         opt.nb = int(nb)
         opt.step_budget = int(step_budget)
+        if reorth_every is not None:
+            opt.reorth_every = int(reorth_every)
         if reorth_tol is not None:
             opt.reorth_tol = float(reorth_tol)
         if check_every is not None:

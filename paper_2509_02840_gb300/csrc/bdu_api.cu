@@ -86,6 +86,7 @@ struct bdu_ctx {
   double *ortho_ws;       // 3*m+1 doubles
   double *rx_E, *rx_W;    // m*m doubles each, allocated on the first re-orthogonalization
   int64_t since_check;
+  int64_t cols_since_reorth;  // rank-1 columns since the last unconditional step
   double ortho[2];        // last estimates for Q, P (-1 = none)
   // automatic check in flight: the two squared estimates land in probe_host
   // (pinned) and probe_ev marks their arrival; acted on once it has fired
@@ -116,6 +117,7 @@ struct bdu_ctx {
   double *g_U;
   int32_t *g_rec;      // the record buffer the graph writes (h->st.La)
   int64_t g_launches;  // kernels one replay launches
+  int64_t g_reorth[2];  // re-orthogonalizations one replay performs
   bool g_off;
   int64_t graph_replays;
   // apply variant per side (launch_apply), and whether the autotuner is still
@@ -284,6 +286,20 @@ constexpr int kChaseSMs = 16;
 // Enqueues on the apply stream the application of record buffer buf to Q and
 // P, after everything enqueued so far on the handle's stream (and after the
 // event `after`, if given).  The buffer's chase descriptors are current.
+bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s);
+
+// The mixed form's unconditional re-orthogonalization: after every
+// reorth_every rank-1 columns, one Newton-Schulz step on Q and on P, enqueued
+// on s behind that column's application.
+bdu_status reorth_after_column(bdu_ctx *h, cudaStream_t s) {
+  if (h->opt.precision != BDU_MIXED || h->opt.reorth_every <= 0) return BDU_OK;
+  if (++h->cols_since_reorth < h->opt.reorth_every) return BDU_OK;
+  h->cols_since_reorth = 0;
+  bdu_status st = reorth_factor(h, 0, s);
+  if (st == BDU_OK) st = reorth_factor(h, 1, s);
+  return st;
+}
+
 bdu_status enqueue_apply(bdu_ctx *h, int buf, int sm_reserve, cudaEvent_t after = nullptr) {
   const int m = (int)h->m, n = (int)h->n;
   cudaError_t e = cudaEventRecord(h->ev_call, h->stream);
@@ -302,6 +318,8 @@ bdu_status enqueue_apply(bdu_ctx *h, int buf, int sm_reserve, cudaEvent_t after 
                      h->apply_var[1]);
     if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
   }
+  const bdu_status rs = reorth_after_column(h, h->sa);
+  if (rs != BDU_OK) return rs;
   e = cudaEventRecord(h->ev_apply[buf], h->sa);
   if (e != cudaSuccess) return cuda_fail(h, e, "ordering the apply stream");
   h->apply_ev_set[buf] = true;
@@ -335,7 +353,8 @@ bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
   return BDU_OK;
 }
 
-bdu_status reorth_factor(bdu_ctx *h, int which) {
+// One Newton-Schulz step on Q (which = 0) or P, enqueued on stream s.
+bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s) {
   const int64_t k = which == 0 ? h->m : h->n;
   if (!h->cublas) {
     cublasHandle_t hb;
@@ -343,16 +362,16 @@ bdu_status reorth_factor(bdu_ctx *h, int which) {
     h->cublas = hb;
   }
   if (!h->rx_E) {
-    h->rx_E = (double *)dev_alloc(h, sizeof(double) * h->m * h->m);
-    h->rx_W = (double *)dev_alloc(h, sizeof(double) * h->m * h->m);
+    h->rx_E = (double *)dev_alloc(h, sizeof(float) * h->m * h->m);
+    h->rx_W = (double *)dev_alloc(h, sizeof(float) * h->m * h->m);
     if (!h->rx_E || !h->rx_W) {
       dev_free(h, h->rx_E); dev_free(h, h->rx_W);
       h->rx_E = h->rx_W = nullptr;
       return fail(h, BDU_ENOMEM, "re-orthogonalization workspace allocation failed");
     }
   }
-  cudaError_t e = launch_reorth((float *)(which == 0 ? h->Q : h->P), (int)k, h->scratch64, h->rx_E, h->rx_W,
-                                h->cublas, h->stream);
+  cudaError_t e = launch_reorth32((float *)(which == 0 ? h->Q : h->P), (int)k, (float *)h->rx_E, (float *)h->rx_W,
+                                  h->cublas, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "re-orthogonalization");
   h->reorth[which]++;
   return BDU_OK;
@@ -366,8 +385,20 @@ bdu_status resolve_probe(bdu_ctx *h) {
     const double est = sqrt(h->probe_host[which]);
     h->ortho[which] = est;
     if (h->opt.reorth_tol > 0.0 && est > h->opt.reorth_tol) {
-      bdu_status st = flush_apply(h);
-      if (st == BDU_OK) st = reorth_factor(h, which);
+      // overlapped with an application deferred: on the apply stream, between
+      // the applications already enqueued and the next (the factor is then
+      // re-orthogonalized at that point of its update sequence); otherwise
+      // after all work on the handle's stream
+      bdu_status st = BDU_OK;
+      if (h->ovl && h->pend) {
+        cudaError_t e = cudaEventRecord(h->ev_call, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->sa, h->ev_call, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "ordering the re-orthogonalization");
+        st = reorth_factor(h, which, h->sa);
+      } else {
+        st = flush_apply(h);
+        if (st == BDU_OK) st = reorth_factor(h, which, h->stream);
+      }
       if (st != BDU_OK) return st;
     }
   }
@@ -762,6 +793,8 @@ bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
                         h->apply_var[1]);
       if (ee != cudaSuccess) return cuda_fail(h, ee, "apply to P");
     }
+    const bdu_status rs = reorth_after_column(h, sa);
+    if (rs != BDU_OK) return rs;
     ee = cudaEventRecord(h->ev_apply[buf], sa);
     if (ee != cudaSuccess) return cuda_fail(h, ee, "ordering the rank-r pipeline");
     h->launches += 2;
@@ -870,6 +903,8 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
       e = launch_apply(h->opt.precision, h->P, n, n, n, h->st, 1, false, s, h->status, 0, false, h->apply_var[1]);
       if (e != cudaSuccess) return cuda_fail(h, e, "apply to P");
     }
+    const bdu_status rs = reorth_after_column(h, s);
+    if (rs != BDU_OK) return rs;
     h->launches += 3;
     if (h->timing) h->apply_launches += 2;
     h->updates++;
@@ -890,13 +925,16 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     const cudaError_t e = cudaGraphLaunch(h->gexec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "replaying the update graph");
     h->launches += h->g_launches;
+    h->reorth[0] += h->g_reorth[0];
+    h->reorth[1] += h->g_reorth[1];
     h->updates += r;
     h->graph_replays++;
     return finish_update(h, r);
   }
   // capture this rank's launch sequence, then run it
   drop_graph(h);
-  const int64_t l0 = h->launches, u0 = h->updates;
+  const int64_t l0 = h->launches, u0 = h->updates, q0 = h->reorth[0], p0 = h->reorth[1];
+  const int64_t c0 = h->cols_since_reorth;
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -918,12 +956,17 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     h->poisoned = false;
     h->launches = l0;
     h->updates = u0;
+    h->reorth[0] = q0;
+    h->reorth[1] = p0;
+    h->cols_since_reorth = c0;
     fs = enqueue_update(h, dB, dC, r);
     return fs != BDU_OK ? fs : finish_update(h, r);
   }
   h->gexec = ex;
   h->g_r = r; h->g_B = dB; h->g_C = dC; h->g_U = h->U; h->g_rec = h->st.La;
   h->g_launches = h->launches - l0;
+  h->g_reorth[0] = h->reorth[0] - q0;
+  h->g_reorth[1] = h->reorth[1] - p0;
   e = cudaGraphLaunch(ex, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "launching the update graph");
   return finish_update(h, r);
@@ -977,7 +1020,7 @@ void bdu_default_options(bdu_options *opt) {
   if (!opt) return;
   opt->precision = BDU_FP64;
   opt->nb = 0;
-  opt->reorth_tol = 1e-6;
+  opt->reorth_tol = 5e-6;
   opt->check_every = 10;
   opt->cuda_stream = nullptr;
   opt->device = 0;
@@ -985,6 +1028,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->overlap = 0;
   opt->graphs = 1;
   opt->step_budget = 0;
+  opt->reorth_every = 1;
 }
 
 int bdu_version(void) { return 100; }
@@ -1035,6 +1079,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   if (o.engine < 0 || o.engine > 2)
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
   if (o.step_budget < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative step budget");
+  if (o.reorth_every < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative reorth_every");
   if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1)) : (o.nb < 0 || o.nb > kSlabVariant))
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown apply variant nb=%d", o.nb);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
@@ -1361,6 +1406,11 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
     if (ce == cudaSuccess) ce = launch_apply_batch(precision, d_apply, d_first, (int)apply.size(), slabs, smem, s);
     if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched update round");
     h0->launches += 3;
+    for (int i = 0; i < count; i++)
+      if (r[i] > k) {
+        const bdu_status rs = reorth_after_column(hs[i], s);
+        if (rs != BDU_OK) return rs;
+      }
   }
   h0->launches += 2;
   // each handle's later work waits for the batch

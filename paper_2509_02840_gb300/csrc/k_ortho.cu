@@ -8,9 +8,15 @@
 // Each product reads X once, coalesced, with FP64 accumulation.
 //
 // Re-orthogonalization: one Newton-Schulz step towards the polar factor,
-// X <- X (3I - X^T X) / 2 = X - X E / 2, with E formed in FP64 from the FP32
-// entries (exact in FP64) -- two plain GEMMs (cuBLAS DGEMM).  It changes the
-// represented A by O(||E||) relative, and shrinks ||E|| to O(||E||^2).
+// X <- X (3I - X^T X) / 2 = X - X E / 2 with E = X^T X - I.  It changes the
+// represented A by O(||E||) relative, and shrinks ||E|| to O(||E||^2).  E is
+// small (~1e-5), so it only needs to be right in absolute terms: its
+// off-diagonal entries are sums of products of nearly orthogonal columns whose
+// partial sums stay ~1/sqrt(k), and an FP32 GEMM (two plain cuBLAS SGEMMs, no
+// tensor-core rounding) gets them to ~1e-7; the diagonal, where the partial
+// sums grow to 1, is formed in FP64.  X E / 2 is a correction of relative size
+// ||E||, so its FP32 rounding is negligible.  (FP64 GEMMs would cost ~0.25 s at
+// k = 4096 on GB300's FP64 rate; these take a few ms.)
 #include <cublas_v2.h>
 
 #include "bdu_internal.cuh"
@@ -74,6 +80,27 @@ __global__ void k_minus_identity(double *__restrict__ E, int64_t ld, int k) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) E[(size_t)i * ld + i] -= 1.0;
 }
 
+// E(i, i) = sum_r X(r, i)^2 - 1 in FP64 (one warp per column)
+__global__ void k_diag_gram(const float *__restrict__ X, int k, float *__restrict__ E) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= k) return;
+  const float *col = X + (size_t)warp * k;
+  double s = 0.0;
+  for (int i = lane; i < k; i += 32) {
+    const double v = (double)col[i];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) E[(size_t)warp * k + warp] = (float)(s - 1.0);
+}
+
+// X = X - W / 2 (FP32 entries, the difference formed in FP64 and rounded once)
+__global__ void k_finish_reorth32(const float *__restrict__ W, float *__restrict__ X, int64_t count) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    X[q] = (float)((double)X[q] - 0.5 * (double)W[q]);
+}
+
 // X = (float)(Xd - W / 2)
 __global__ void k_finish_reorth(const double *__restrict__ Xd, const double *__restrict__ W,
                                 float *__restrict__ X, int64_t count) {
@@ -126,6 +153,22 @@ cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, voi
   if (cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, Xd, k, E, k, &zero, W, k) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
   k_finish_reorth<<<1216, 256, 0, s>>>(Xd, W, X, cnt);
+  return cudaGetLastError();
+}
+
+// One Newton-Schulz step on X (k x k, FP32), E and W: k*k floats of workspace.
+cudaError_t launch_reorth32(float *X, int k, float *E, float *W, void *cublas_handle, cudaStream_t s) {
+  cublasHandle_t hb = (cublasHandle_t)cublas_handle;
+  if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  if (cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  const float one = 1.0f, zero = 0.0f;
+  // E = X^T X (FP32; its diagonal is replaced by the FP64 one minus 1)
+  if (cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, k, k, &one, X, k, X, k, &zero, E, k) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  k_diag_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(X, k, E);
+  if (cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, X, k, E, k, &zero, W, k) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  k_finish_reorth32<<<1216, 256, 0, s>>>(W, X, (int64_t)k * k);
   return cudaGetLastError();
 }
 

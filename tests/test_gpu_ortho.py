@@ -32,7 +32,7 @@ def test_block_stream_with_reorthogonalization():
     m, n, r = 2048, 512, 8
     Q, d, e, P = I.factorization(m, n, config=2)
     A = Q @ O.bidiag_dense(d, e, m) @ P.T
-    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, reorth_tol=1e-6, check_every=8) as F:
+    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, reorth_tol=1e-6, check_every=8, reorth_every=0) as F:
         for h in range(6):
             B, C = I.block_update(m, n, h, config=2, r=r)
             A += B @ C.T
@@ -55,7 +55,7 @@ def test_reorthogonalization_reduces_the_error():
     g = np.random.default_rng(1)
     Qp = Q + 2e-5 * g.standard_normal((m, m)) / np.sqrt(m)
     before = np.linalg.norm(Qp.T @ Qp - np.eye(m), 2)
-    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-7, check_every=1) as F:
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-7, check_every=1, reorth_every=0) as F:
         B, C = I.dense_update(m, n, 0, config=0)
         F.update(B, C)
         Qg, _, _, _ = F.read()
@@ -87,3 +87,23 @@ def test_block_stream_full_size_invariants():
         want += B @ (C.T @ X)
     got = Qg @ (O.bidiag_dense(dg, eg, m) @ (Pg.T @ X))
     assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_default_policy_keeps_the_tolerance_after_every_update(overlap):
+    """With the default policy (one Newton-Schulz step after every column) the
+    mixed form keeps ||Q^T Q - I||_2 and ||P^T P - I||_2 under 1e-5 after every
+    update of the rank-1 recommender stream at m = n = 4096, where FP32
+    rounding alone exceeds it after the first update."""
+    m = n = 4096
+    Q, d, e, P = I.factorization(m, n, config=1)
+    worst = 0.0
+    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, overlap=overlap) as F:
+        for h in range(4):
+            F.update(*I.recommender_update(m, n, h, config=1))
+            q_est, p_est = F.check_orthogonality()
+            worst = max(worst, q_est, p_est)
+        st = F.stats()
+    assert worst <= 1e-5
+    assert st["reorth_q"] >= 3 and st["reorth_p"] >= 3

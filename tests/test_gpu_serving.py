@@ -84,7 +84,7 @@ def test_automatic_check_acts_after_a_batch():
     tb = torch.from_numpy(B.reshape(-1, order="F").copy()).cuda()
     tc = torch.from_numpy(C.reshape(-1, order="F").copy()).cuda()
     torch.cuda.synchronize()
-    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-7, check_every=1) as F:
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-7, check_every=1, reorth_every=0) as F:
         bdu.update_batch([F], [tb.data_ptr()], [tc.data_ptr()], [1])
         Qg, _, _, _ = F.read()
         st = F.stats()
