@@ -100,15 +100,17 @@ typedef struct {
                          column before the kernel stops and the update fails with
                          BDU_ETIMEOUT (poisoning the handle); 0 = 64 (n + 16) + 4096
                          (default; a column needs about 11 n) */
-  int reorth_every;   /* BDU_MIXED: one Newton-Schulz re-orthogonalization step of Q and P
-                         after every reorth_every rank-1 columns, enqueued behind that
-                         column's application (in the overlapped form beside the next
-                         chase); 0 = only when the check below finds the estimate above
-                         reorth_tol.  Default 1: FP32 rounding in the application moves
-                         ||Q^T Q - I||_2 by about 2e-6 per column at n = 4096 (by up to
-                         2e-5 in some), and one step brings it back to ~1.3e-6, so the
-                         1e-5 tolerance holds after every update.  With graph replay
-                         the cadence counts within a call. */
+  int reorth_every;   /* BDU_MIXED: one Newton-Schulz re-orthogonalization step of Q (P)
+                         behind the application of a factor's first rank-1 column and
+                         then of every reorth_every-th (in the overlapped and rank-r
+                         paths on the apply stream, beside the next chase); 0 = only
+                         when the check below finds the estimate above reorth_tol;
+                         -1 (default) = every max(1, 100 / sqrt(k)) columns for a factor
+                         of order k: FP32 rounding in the application moves
+                         ||X^T X - I||_2 by about 3e-8 sqrt(k) per column (more in the
+                         first), a step leaves ~1e-6, so the 1e-5 tolerance holds after
+                         every update.  Graph replay is used only when the cadence is
+                         in the state the graph was captured in. */
 } bdu_options;
 
 typedef struct {

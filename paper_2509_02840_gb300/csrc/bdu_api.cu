@@ -86,7 +86,7 @@ struct bdu_ctx {
   double *ortho_ws;       // 3*m+1 doubles
   double *rx_E, *rx_W;    // m*m doubles each, allocated on the first re-orthogonalization
   int64_t since_check;
-  int64_t cols_since_reorth;  // rank-1 columns since the last unconditional step
+  int64_t cols_since_reorth[2];  // rank-1 columns since the last unconditional step (Q, P)
   double ortho[2];        // last estimates for Q, P (-1 = none)
   // automatic check in flight: the two squared estimates land in probe_host
   // (pinned) and probe_ev marks their arrival; acted on once it has fired
@@ -118,6 +118,7 @@ struct bdu_ctx {
   int32_t *g_rec;      // the record buffer the graph writes (h->st.La)
   int64_t g_launches;  // kernels one replay launches
   int64_t g_reorth[2];  // re-orthogonalizations one replay performs
+  int64_t g_cols[2], g_cols_after[2];  // re-orthogonalization cadence counters before / after
   bool g_off;
   int64_t graph_replays;
   // apply variant per side (launch_apply), and whether the autotuner is still
@@ -288,16 +289,28 @@ constexpr int kChaseSMs = 16;
 // event `after`, if given).  The buffer's chase descriptors are current.
 bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s);
 
-// The mixed form's unconditional re-orthogonalization: after every
-// reorth_every rank-1 columns, one Newton-Schulz step on Q and on P, enqueued
-// on s behind that column's application.
+// Columns between unconditional steps for a factor of order k: FP32 rounding
+// in the application moves ||X^T X - I||_2 by about 3e-8 sqrt(k) per rank-1
+// column (measured for k = 64 .. 4096), and a step leaves ~1e-6, so every
+// 100 / sqrt(k) columns keeps it near half the 1e-5 tolerance.
+int auto_cadence(int64_t k) {
+  const int c = (int)(100.0 / sqrt((double)(k > 1 ? k : 1)));
+  return c > 1 ? c : 1;
+}
+
+// The mixed form's unconditional re-orthogonalization: one Newton-Schulz step
+// on Q (P) behind the application of the first column and then of every
+// reorth_every-th (automatic: auto_cadence of its order), enqueued on s.
 bdu_status reorth_after_column(bdu_ctx *h, cudaStream_t s) {
-  if (h->opt.precision != BDU_MIXED || h->opt.reorth_every <= 0) return BDU_OK;
-  if (++h->cols_since_reorth < h->opt.reorth_every) return BDU_OK;
-  h->cols_since_reorth = 0;
-  bdu_status st = reorth_factor(h, 0, s);
-  if (st == BDU_OK) st = reorth_factor(h, 1, s);
-  return st;
+  if (h->opt.precision != BDU_MIXED || h->opt.reorth_every == 0) return BDU_OK;
+  for (int which = 0; which < 2; which++) {
+    const int every = h->opt.reorth_every > 0 ? h->opt.reorth_every : auto_cadence(which == 0 ? h->m : h->n);
+    if (++h->cols_since_reorth[which] < every && h->reorth[which] > 0) continue;
+    h->cols_since_reorth[which] = 0;
+    const bdu_status st = reorth_factor(h, which, s);
+    if (st != BDU_OK) return st;
+  }
+  return BDU_OK;
 }
 
 bdu_status enqueue_apply(bdu_ctx *h, int buf, int sm_reserve, cudaEvent_t after = nullptr) {
@@ -921,12 +934,16 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     return fs != BDU_OK ? fs : finish_update(h, r);
   }
   cudaStream_t s = h->stream;
-  if (h->gexec && h->g_r == r && h->g_B == dB && h->g_C == dC && h->g_U == h->U && h->g_rec == h->st.La) {
+  if (h->gexec && h->g_r == r && h->g_B == dB && h->g_C == dC && h->g_U == h->U && h->g_rec == h->st.La &&
+      h->g_cols[0] == h->cols_since_reorth[0] && h->g_cols[1] == h->cols_since_reorth[1] &&
+      (h->reorth[0] > 0) == (h->g_cols_after[0] >= 0) && (h->reorth[1] > 0) == (h->g_cols_after[1] >= 0)) {
     const cudaError_t e = cudaGraphLaunch(h->gexec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "replaying the update graph");
     h->launches += h->g_launches;
     h->reorth[0] += h->g_reorth[0];
     h->reorth[1] += h->g_reorth[1];
+    h->cols_since_reorth[0] = h->g_cols_after[0] >= 0 ? h->g_cols_after[0] : -1 - h->g_cols_after[0];
+    h->cols_since_reorth[1] = h->g_cols_after[1] >= 0 ? h->g_cols_after[1] : -1 - h->g_cols_after[1];
     h->updates += r;
     h->graph_replays++;
     return finish_update(h, r);
@@ -934,7 +951,7 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   // capture this rank's launch sequence, then run it
   drop_graph(h);
   const int64_t l0 = h->launches, u0 = h->updates, q0 = h->reorth[0], p0 = h->reorth[1];
-  const int64_t c0 = h->cols_since_reorth;
+  const int64_t c0 = h->cols_since_reorth[0], c1 = h->cols_since_reorth[1];
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -958,7 +975,8 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
     h->updates = u0;
     h->reorth[0] = q0;
     h->reorth[1] = p0;
-    h->cols_since_reorth = c0;
+    h->cols_since_reorth[0] = c0;
+    h->cols_since_reorth[1] = c1;
     fs = enqueue_update(h, dB, dC, r);
     return fs != BDU_OK ? fs : finish_update(h, r);
   }
@@ -967,6 +985,12 @@ bdu_status run_update(bdu_ctx *h, const double *dB, const double *dC, int64_t r)
   h->g_launches = h->launches - l0;
   h->g_reorth[0] = h->reorth[0] - q0;
   h->g_reorth[1] = h->reorth[1] - p0;
+  // counters as the call found and left them; the sign of the latter records
+  // whether the factor had been re-orthogonalized before the call (which
+  // changes the first-column rule), so a replay needs the same
+  h->g_cols[0] = c0; h->g_cols[1] = c1;
+  h->g_cols_after[0] = q0 > 0 ? h->cols_since_reorth[0] : -1 - h->cols_since_reorth[0];
+  h->g_cols_after[1] = p0 > 0 ? h->cols_since_reorth[1] : -1 - h->cols_since_reorth[1];
   e = cudaGraphLaunch(ex, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "launching the update graph");
   return finish_update(h, r);
@@ -1028,7 +1052,7 @@ void bdu_default_options(bdu_options *opt) {
   opt->overlap = 0;
   opt->graphs = 1;
   opt->step_budget = 0;
-  opt->reorth_every = 1;
+  opt->reorth_every = -1;
 }
 
 int bdu_version(void) { return 100; }
@@ -1079,7 +1103,7 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   if (o.engine < 0 || o.engine > 2)
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
   if (o.step_budget < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative step budget");
-  if (o.reorth_every < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative reorth_every");
+  if (o.reorth_every < -1) return fail(nullptr, BDU_EINVAL, "bdu_create: reorth_every below -1");
   if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1)) : (o.nb < 0 || o.nb > kSlabVariant))
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown apply variant nb=%d", o.nb);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))

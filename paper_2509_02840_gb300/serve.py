@@ -13,7 +13,10 @@ update A <- A + B C^T of one session (Sec. 3.4 applied r times).  The loop
     flight on two CUDA streams (continuous batching: a request arriving while
     batches run joins the next one as soon as its session is free);
   * applies each session's requests in arrival order, so that every session
-    ends where the same updates applied one by one leave it.
+    ends where the same updates applied one by one leave it (in the mixed form
+    exactly so when re-orthogonalization runs after every column,
+    reorth_every=1: the default cadence counts columns per resident handle,
+    and a re-admitted session starts counting afresh).
 
 It reports rank-1 updates per second and the p50/p99 request latency (arrival
 to the completion of its batch, seen by polling an event): first saturated
@@ -64,10 +67,11 @@ def reserve_bytes(m, n, precision, max_rank=4):
 
 
 class Session:
-    def __init__(self, sid, m, n, precision, check_every=None, config=4):
+    def __init__(self, sid, m, n, precision, check_every=None, config=4, reorth_every=None):
         self.sid, self.m, self.n = sid, m, n
         self.precision = precision
         self.check_every = check_every
+        self.reorth_every = reorth_every
         self.state = inputs.factorization(m, n, config=config, which=sid)  # host copy while evicted
         self.handle = None
         self.pending = collections.deque()
@@ -80,7 +84,8 @@ class Session:
     def admit(self):
         Q, d, e, P = self.state
         # each session gets its own CUDA stream; batches order themselves after it
-        self.handle = bdu.Factorization(Q, d, e, P, precision=self.precision, check_every=self.check_every)
+        self.handle = bdu.Factorization(Q, d, e, P, precision=self.precision, check_every=self.check_every,
+                                        reorth_every=self.reorth_every)
         self.state = None
         self.bytes = max(self.bytes, self.handle.stats()["device_bytes"])
 
@@ -95,10 +100,12 @@ class Session:
 
 
 class Server:
-    def __init__(self, specs, precision=bdu.MIXED, budget_bytes=None, max_batch=64, check_every=None):
+    def __init__(self, specs, precision=bdu.MIXED, budget_bytes=None, max_batch=64, check_every=None,
+                 reorth_every=None):
         import torch
         self.torch = torch
-        self.sessions = [Session(i, m, n, precision, check_every) for i, (m, n) in enumerate(specs)]
+        self.sessions = [Session(i, m, n, precision, check_every, reorth_every=reorth_every)
+                         for i, (m, n) in enumerate(specs)]
         self.cuda = [torch.cuda.Stream(), torch.cuda.Stream()]
         self.budget = budget_bytes if budget_bytes is not None else sum(s.bytes for s in self.sessions)
         if max(s.bytes for s in self.sessions) > self.budget:

@@ -25,7 +25,7 @@ def test_version_and_defaults(lib):
     o = bdu.Options()
     lib.bdu_default_options(ctypes.byref(o))
     assert o.precision == bdu.FP64 and o.nb == 0 and o.device == 0
-    assert o.reorth_tol == pytest.approx(5e-6) and o.check_every == 10 and o.reorth_every == 1
+    assert o.reorth_tol == pytest.approx(5e-6) and o.check_every == 10 and o.reorth_every == -1
     assert o.graphs == 1 and o.step_budget == 0 and o.overlap == 0
 
 

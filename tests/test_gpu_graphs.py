@@ -19,7 +19,8 @@ def _run(precision, graphs, m, n, dev_inputs=False, timing_at=None):
     Q, d, e, P = I.factorization(m, n, config=0, which=41)
     # a fixed apply variant: the autotuner would drop the first update's graph
     nb = 8 if precision == bdu.FP64 else 1
-    with bdu.Factorization(Q, d, e, P, precision=precision, graphs=graphs, nb=nb,
+    # (no re-orthogonalization cadence: its counters take part in the replay key)
+    with bdu.Factorization(Q, d, e, P, precision=precision, graphs=graphs, nb=nb, reorth_every=0,
                            check_every=0 if precision == bdu.MIXED else None) as F:
         keep = []
         for h, r in enumerate(RANKS):
@@ -76,7 +77,7 @@ def test_rank_r_pipeline_equals_column_by_column(precision):
     Q, d, e, P = I.factorization(m, n, config=0, which=77)
     ranks = [3, 2, 2, 4, 4, 1, 2]
     ups = [I.dense_update(m, n, h, config=0, r=r) for h, r in enumerate(ranks)]
-    kw = dict(precision=precision, nb=8 if precision == bdu.FP64 else 1,
+    kw = dict(precision=precision, nb=8 if precision == bdu.FP64 else 1, reorth_every=0,
               check_every=0 if precision == bdu.MIXED else None)
     outs = []
     for graphs in (True, False):
@@ -102,3 +103,26 @@ def test_rank_r_pipeline_equals_column_by_column(precision):
             Q, d, e, P, _ = O.update(Q, d, e, P, B, C)
         for a, b in zip(outs[0], (Q, d, e, P)):
             assert np.array_equal(a, b)
+
+
+
+@pytest.mark.parametrize("every", [-1, 1, 3])
+def test_replay_with_reorthogonalization_cadence(every):
+    """The mixed form's re-orthogonalization cadence is host state that a
+    replay must follow: graphs are replayed only when the cadence is where it
+    was at capture, and the results equal separate launches bit for bit."""
+    m, n = 300, 256
+    Q, d, e, P = I.factorization(m, n, config=0, which=43)
+    outs, stats = [], []
+    for graphs in (True, False):
+        with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, graphs=graphs, nb=1, reorth_every=every,
+                               check_every=0) as F:
+            for h, r in enumerate([1, 1, 1, 2, 2, 2, 1, 3, 1, 1]):
+                F.update(*I.dense_update(m, n, h, config=0, r=r))
+            outs.append(F.read())
+            stats.append(F.stats())
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert stats[0]["reorth_q"] == stats[1]["reorth_q"] and stats[0]["reorth_p"] == stats[1]["reorth_p"]
+    if every == 1:
+        assert stats[0]["graph_replays"] >= 3

@@ -21,7 +21,7 @@ def _replay(specs, reqs, precision, check_every):
     out = {}
     for sid, (m, n) in enumerate(specs):
         Q, d, e, P = I.factorization(m, n, config=4, which=sid)
-        with bdu.Factorization(Q, d, e, P, precision=precision, check_every=check_every) as F:
+        with bdu.Factorization(Q, d, e, P, precision=precision, check_every=check_every, reorth_every=1) as F:
             for q in by_sid[sid]:
                 F.update(q.B, q.C)
             out[sid] = F.read()
@@ -34,7 +34,9 @@ def test_serving_equals_sequential_replay(precision):
     check_every = 0 if precision == bdu.MIXED else None
     per = [S.reserve_bytes(m, n, precision) for m, n in specs]
     budget = max(per) + sorted(per)[len(per) // 2]  # room for about two sessions: forces evictions
-    srv = S.Server(specs, precision, budget, max_batch=5, check_every=check_every)
+    # one re-orthogonalization step after every column: a cadence that does not
+    # depend on how long a session has been resident
+    srv = S.Server(specs, precision, budget, max_batch=5, check_every=check_every, reorth_every=1)
     counter = collections.Counter()
     burst = S.poisson_arrivals(specs, 0.0, 24, seed=3, first_update=counter)
     res1 = srv.run(burst)
