@@ -790,19 +790,20 @@ bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
   // Column k-1's application is enqueued once column k is staged, so that it
   // and column k's chase become ready together and the chase (on the stream
   // of greater priority) is placed first; the application leaves it SMs.
+  bool desc_ready = false;  // set below, before the first application
   auto enqueue_apply_of = [&](int buf, int reserve) -> bdu_status {
     cudaError_t ee = cudaEventRecord(h->ev_chase, sc);
     if (ee == cudaSuccess) ee = cudaStreamWaitEvent(sa, h->ev_chase, 0);
     if (ee != cudaSuccess) return cuda_fail(h, ee, "ordering the rank-r pipeline");
     {
       Timer tm(h, 2, sa);
-      ee = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, sa, h->status, reserve, false,
+      ee = launch_apply(h->opt.precision, h->Q, m, m, m, h->stb[buf], 0, m > n, sa, h->status, reserve, desc_ready,
                         h->apply_var[0]);
       if (ee != cudaSuccess) return cuda_fail(h, ee, "apply to Q");
     }
     {
       Timer tm(h, 3, sa);
-      ee = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, sa, h->status, reserve, false,
+      ee = launch_apply(h->opt.precision, h->P, n, n, n, h->stb[buf], 1, false, sa, h->status, reserve, desc_ready,
                         h->apply_var[1]);
       if (ee != cudaSuccess) return cuda_fail(h, ee, "apply to P");
     }
@@ -814,6 +815,13 @@ bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
     if (h->timing) h->apply_launches += 2;
     return BDU_OK;
   };
+  // Mixed form: the later columns' projections are rotated by each column's
+  // rotations after its chase, all at once (one block per vector, FP32 like
+  // the application to Q and P), instead of inside the chase, where they
+  // lengthened every step; the chase descriptors this needs also serve the
+  // applications.  The FP64 form rotates them inside the chase (exact order).
+  const bool after = h->opt.precision == BDU_MIXED && rotate_vectors_supported(m, n);
+  desc_ready = after;
   int b = h->cur;
   for (int64_t k = 0; k < r; k++) {
     b ^= 1;
@@ -834,7 +842,7 @@ bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
     }
     ChaseArgs a{};
     a.m = m; a.n = n; a.band = bp;
-    a.rx = (int)(r - k - 1);
+    a.rx = after ? 0 : (int)(r - k - 1);
     a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
     a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
     a.st = sb; a.status = h->status; a.counters = h->counters;
@@ -847,6 +855,16 @@ bdu_status enqueue_columns_pipelined(bdu_ctx *h, int64_t r) {
       if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
     }
     h->launches += 1;
+    if (after) {
+      e = launch_chase_descriptors(sb, 0, sc);
+      if (e == cudaSuccess) e = launch_chase_descriptors(sb, 1, sc);
+      const int later = (int)(r - k - 1);
+      if (e == cudaSuccess && later > 0)
+        e = launch_rotate_vector_sets(h->U + (k + 1) * m, h->U + (k + 1) * m, m, later, m, h->V + (k + 1) * n,
+                                      h->V + (k + 1) * n, n, later, n, sb, m > n, h->status, sc);
+      if (e != cudaSuccess) return cuda_fail(h, e, "rotating the later projections");
+      h->launches += later > 0 ? 3 : 2;
+    }
     h->updates++;
   }
   const bdu_status st = enqueue_apply_of(b, 0);
@@ -891,9 +909,12 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Ln, 0, sizeof(int32_t) * h->st.T, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st.Rn, 0, sizeof(int32_t) * h->st.T, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "staging a rank-1 column");
+    // (mixed form: the later projections are rotated after the chase, as in
+    // the pipelined path)
+    const bool after = h->opt.precision == BDU_MIXED && r > 1 && rotate_vectors_supported(m, n);
     ChaseArgs a{};
     a.m = m; a.n = n; a.band = bp;
-    a.rx = (int)(r - k - 1);
+    a.rx = after ? 0 : (int)(r - k - 1);
     a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
     a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
     a.st = h->st; a.status = h->status; a.counters = h->counters;
@@ -904,6 +925,16 @@ bdu_status enqueue_update(bdu_ctx *h, const double *dB, const double *dC, int64_
       Timer tm(h, 1);
       e = launch_chase(a, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "bulge-chase kernel");
+    }
+    if (after && k + 1 < r) {
+      const int later = (int)(r - k - 1);
+      e = launch_chase_descriptors(h->st, 0, s);
+      if (e == cudaSuccess) e = launch_chase_descriptors(h->st, 1, s);
+      if (e == cudaSuccess)
+        e = launch_rotate_vector_sets(h->U + (k + 1) * m, h->U + (k + 1) * m, m, later, m, h->V + (k + 1) * n,
+                                      h->V + (k + 1) * n, n, later, n, h->st, m > n, h->status, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "rotating the later projections");
+      h->launches += 3;
     }
     // K3: Q <- Q prod G^T, P <- P prod H
     {
@@ -1359,7 +1390,8 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
       const int m = (int)h->m, n = (int)h->n;
       ChaseArgs a{};
       a.m = m; a.n = n; a.band = band_ptrs(h->band, m, n);
-      a.rx = (int)(r[i] - k - 1);
+      const bool after = precision == BDU_MIXED && rotate_vectors_supported(m, n);
+      a.rx = after ? 0 : (int)(r[i] - k - 1);
       a.Ux = a.rx > 0 ? h->U + (k + 1) * m : nullptr;
       a.Vx = a.rx > 0 ? h->V + (k + 1) * n : nullptr;
       a.st = h->st; a.status = h->status; a.counters = h->counters;
@@ -1427,6 +1459,18 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
     }
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    // mixed form: each item's later projections, rotated by this round's rotations
+    for (int i = 0; i < count && ce == cudaSuccess; i++) {
+      bdu_ctx *h = hs[i];
+      const int m = (int)h->m, n = (int)h->n, later = (int)(r[i] - k - 1);
+      if (later <= 0 || precision != BDU_MIXED || !rotate_vectors_supported(m, n)) continue;
+      ce = launch_chase_descriptors(h->st, 0, s);
+      if (ce == cudaSuccess) ce = launch_chase_descriptors(h->st, 1, s);
+      if (ce == cudaSuccess)
+        ce = launch_rotate_vector_sets(h->U + (k + 1) * m, h->U + (k + 1) * m, m, later, m, h->V + (k + 1) * n,
+                                       h->V + (k + 1) * n, n, later, n, h->st, m > n, h->status, s);
+      h0->launches += 3;
+    }
     if (ce == cudaSuccess) ce = launch_apply_batch(precision, d_apply, d_first, (int)apply.size(), slabs, smem, s);
     if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched update round");
     h0->launches += 3;

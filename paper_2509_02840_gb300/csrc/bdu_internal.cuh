@@ -139,6 +139,9 @@ bool rotate_vectors_supported(int m, int n);
 cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,
                                   double *dst_right, int n, const RotStream &st, bool with_spike, int *status,
                                   cudaStream_t s);
+cudaError_t launch_rotate_vector_sets(const double *w_left, double *dst_left, int64_t ldl, int nl, int m,
+                                      const double *w_right, double *dst_right, int64_t ldr, int nr, int n,
+                                      const RotStream &st, bool with_spike, int *status, cudaStream_t s);
 // L(:, k) = alpha[k] q_i + beta[k] q_{i-1} (just alpha[k] q_1 for i = 1) and
 // R(:, k) = p_i, i = idx[k] (1-based), in FP64 (L m x r, R n x r, column-major).
 cudaError_t launch_truncate(int precision, const void *Q, int64_t m, const void *P, int64_t n, const int32_t *idx,

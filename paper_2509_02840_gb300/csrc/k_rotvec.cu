@@ -79,20 +79,23 @@ struct RvLayout {
 // gap the index of its first record in the record arrays.
 constexpr int kLast = 1 << 10, kGap = 1 << 11, kShift = 1 << 12, kStop = 1 << 13;
 
-// blockIdx.x = 0: w_left (m entries) by the left stream into dst_left;
-//              1: w_right (n entries) by the right stream into dst_right.
-__global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *__restrict__ w_left,
-                                                             double *__restrict__ dst_left, int m,
-                                                             const double *__restrict__ w_right,
-                                                             double *__restrict__ dst_right, int n,
+// Blocks 0 .. nl-1: vector b of w_left (m entries, stride ldl) by the left
+// stream into the same place of dst_left; blocks nl .. nl+nr-1: vector b-nl of
+// w_right (n entries, stride ldr) by the right stream into dst_right.  A
+// vector is read whole into shared memory before it is written, so w and dst
+// may coincide.
+__global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_left, double *dst_left, int64_t ldl,
+                                                             int nl, int m, const double *w_right, double *dst_right,
+                                                             int64_t ldr, int n,
                                                              RotStream st, int with_spike, RvLayout L,
                                                              int *__restrict__ status) {
   extern __shared__ __align__(128) unsigned char raw[];
-  const bool left = blockIdx.x == 0;
+  const bool left = (int)blockIdx.x < nl;
+  const int vec = left ? (int)blockIdx.x : (int)blockIdx.x - nl;
   const int len = left ? m : n;
   const int tid = threadIdx.x;
-  const double *w = left ? w_left : w_right;
-  double *dst = left ? dst_left : dst_right;
+  const double *w = left ? w_left + (size_t)vec * ldl : w_right + (size_t)vec * ldr;
+  double *dst = left ? dst_left + (size_t)vec * ldl : dst_right + (size_t)vec * ldr;
   float *v = reinterpret_cast<float *>(raw);
   uint64_t *full = reinterpret_cast<uint64_t *>(raw + L.full);
   uint64_t *empty = reinterpret_cast<uint64_t *>(raw + L.empty);
@@ -221,12 +224,23 @@ bool rotate_vectors_supported(int m, int n) {
 cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,
                                   double *dst_right, int n, const RotStream &st, bool with_spike, int *status,
                                   cudaStream_t s) {
+  return launch_rotate_vector_sets(w_left, dst_left, m, 1, m, w_right, dst_right, n, 1, n, st, with_spike, status, s);
+}
+
+// The same for count vectors on each side: column j of w_left (leading
+// dimension ldl) into column j of dst_left, likewise on the right; one block
+// per vector, all at once.
+cudaError_t launch_rotate_vector_sets(const double *w_left, double *dst_left, int64_t ldl, int nl, int m,
+                                      const double *w_right, double *dst_right, int64_t ldr, int nr, int n,
+                                      const RotStream &st, bool with_spike, int *status, cudaStream_t s) {
   RvLayout L{};
-  if (!st.Lf || !st.Rf || !st.Sf || !st.Lm || !st.Rm || !L.make(m > n ? m : n)) return cudaErrorNotSupported;
+  if (!st.Lf || !st.Rf || !st.Sf || !st.Lm || !st.Rm || !L.make(m > n ? m : n) || nl < 0 || nr < 0)
+    return cudaErrorNotSupported;
+  if (nl + nr == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_rotate_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
-  k_rotate_vectors<<<2, kThreads, L.total, s>>>(w_left, dst_left, m, w_right, dst_right, n, st, with_spike ? 1 : 0,
-                                               L, status);
+  k_rotate_vectors<<<nl + nr, kThreads, L.total, s>>>(w_left, dst_left, ldl, nl, m, w_right, dst_right, ldr, n, st,
+                                                     with_spike ? 1 : 0, L, status);
   return cudaGetLastError();
 }
 
