@@ -155,7 +155,7 @@ CHASE_FLOPS_PER_ROTATION = 26
 # ncu capture (profiles/launches_recommender_4096.md): the rotation records written
 # (FP32 (c, s) and an int32 pair index per rotation, 12 B x 25.2M = 302 MB, part of
 # which is still in L2 when the launch ends).
-CHASE_TRAFFIC_4096 = 9.14e6 + 250.55e6
+CHASE_TRAFFIC_4096 = 6.08e6 + 248.72e6
 
 
 def roofline(st, precision, rotations_per_update, launches_per_update, steps_per_update=None):
