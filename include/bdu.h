@@ -21,7 +21,14 @@
  *
  * Conventions for every entry point:
  *   - matrices are column-major, double precision on the host side;
- *   - requirement m >= n >= 1;
+ *   - m, n >= 1.  For m < n the factorization is A = Q L P^T with L lower
+ *     bidiagonal (diagonal d[i] = L(i,i), subdiagonal e[i] = L(i+1,i)), the
+ *     form whose transpose A^T = P L^T Q^T is the upper form above: the
+ *     library holds that transpose and updates it with A^T + C B^T.  Every
+ *     entry point still speaks of the caller's A, Q, P, B and C (left
+ *     rotations act on Q, right ones on P); in this form Q(:,1), not P(:,1),
+ *     is the vector that no rotation touches.  d has min(m, n) entries and e
+ *     min(m, n) - 1;
  *   - host pointers are copied in or out and stay owned by the caller; all
  *     device memory is owned by the handle (see bdu_set_allocator);
  *   - functions return a bdu_status and never abort; the message of the most
@@ -44,7 +51,7 @@ typedef struct bdu_ctx *bdu_handle;
 
 typedef enum {
   BDU_OK = 0,
-  BDU_EINVAL = 1,    /* bad argument (null pointer, m < n, r < 0, NaN/Inf input, ...) */
+  BDU_EINVAL = 1,    /* bad argument (null pointer, m or n < 1, r < 0, NaN/Inf input, ...) */
   BDU_ENOMEM = 2,    /* device allocation failed; the handle stays usable */
   BDU_ECUDA = 3,     /* CUDA runtime error; handle poisoned */
   BDU_ETIMEOUT = 4,  /* a bounded device-side wait expired; handle poisoned */
@@ -136,11 +143,12 @@ typedef struct {
 /* Fills *opt with the defaults listed above. */
 void bdu_default_options(bdu_options *opt);
 
-/* Creates a handle holding A = Q diag-band(d, e) P^T on the GPU.
- *   Q: m*m host doubles (column-major), P: n*n, d: n, e: n-1 (may be NULL
- *   when n == 1).  Q and P are assumed orthogonal (not checked: O(m^3)).
- *   opt may be NULL (defaults).
- * Errors: BDU_EINVAL (null pointers, m < n, n < 1, non-finite input),
+/* Creates a handle holding A = Q diag-band(d, e) P^T on the GPU (upper
+ * bidiagonal for m >= n, lower for m < n).
+ *   Q: m*m host doubles (column-major), P: n*n, d: k = min(m, n), e: k-1
+ *   (may be NULL when k == 1).  Q and P are assumed orthogonal (not checked:
+ *   O(m^3)).  opt may be NULL (defaults).
+ * Errors: BDU_EINVAL (null pointers, m < 1, n < 1, non-finite input),
  *         BDU_ENOMEM, BDU_ECUDA.  On error *h is set to NULL. */
 bdu_status bdu_create(bdu_handle *h, int64_t m, int64_t n, const double *Q, const double *d,
                       const double *e, const double *P, const bdu_options *opt);
@@ -177,7 +185,8 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
 bdu_status bdu_sync(bdu_handle h);
 
 /* Copies the current factorization to host buffers (any may be NULL):
- * Q m*m, d n, e n-1, P n*n.  Synchronizes the handle's stream. */
+ * Q m*m, d min(m, n), e min(m, n)-1, P n*n.  Synchronizes the handle's
+ * stream. */
 bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P);
 
 /* Copies the rotations of the most recent rank-1 column to host buffers, in
@@ -199,7 +208,10 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
  * L(:, k) = alpha_i q_i + beta_{i-1} q_{i-1} (m x r) and R(:, k) = p_i (n x r),
  * column-major FP64 (in the mixed form from the FP32 factors), and in *err2
  * the exact error ||A - A_r||_F^2 = the sum of alpha_i^2 + beta_{i-1}^2 over
- * the other indices (Eq. errtrBD; exact for orthogonal Q and P).  0 <= r <= n
+ * the other indices (Eq. errtrBD; exact for orthogonal Q and P).  For m < n
+ * (L lower bidiagonal) the same applies to A^T: the kept indices are those of
+ * the largest alpha_i^2 + beta_{i-1}^2 (rows of L), with L(:, k) = q_i and
+ * R(:, k) = alpha_i p_i + beta_{i-1} p_{i-1}.  0 <= r <= min(m, n)
  * (BDU_EINVAL otherwise).  Host buffers, any may be NULL; completes deferred
  * work first and synchronizes. */
 bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int64_t *idx, double *err2);
@@ -207,8 +219,8 @@ bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int
 /* The k largest singular values of the current bidiagonal Bd (those of A when
  * Q and P are orthogonal; Sec. 2), in descending order, computed on the device
  * by multisection with Sturm counts on the Golub-Kahan tridiagonal matrix of
- * Bd (absolute accuracy about 1e-15 of the largest).  0 <= k <= n (BDU_EINVAL
- * otherwise); sv is a host buffer of k doubles.  Needs no deferred work to
+ * Bd (absolute accuracy about 1e-15 of the largest).  0 <= k <= min(m, n)
+ * (BDU_EINVAL otherwise); sv is a host buffer of k doubles.  Needs no deferred work to
  * complete (Bd is current after every update); synchronizes. */
 bdu_status bdu_singular_values(bdu_handle h, int64_t k, double *sv);
 

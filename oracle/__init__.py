@@ -9,6 +9,7 @@ Functions
 ---------
 rot(f, g)                       rotation generator (Eqs. giv, giv1)
 update(Q, d, e, P, B, C)        full update, Eqs. rk1 / bidiagsubproblem / bidiagplus
+update_lower(Q, d, e, P, B, C)  the same for m < n (lower bidiagonal, by transposition)
 generate(m, n, d, e, U, V)      the reduction only: rotation lists + new (d, e)
 apply_rows(X, rows, rotlist)    X(rows, :) <- X(rows, :) * prod(rotations)
 jacobi_sv(X)                    one-sided Jacobi singular values (tiny inputs)
@@ -131,6 +132,36 @@ def update(Q, d, e, P, B, C, check=True):
     if rc != 0 and check:
         raise OracleError(_ERR.get(rc, str(rc)) + f" ({_counts_dict(cnt)})")
     return Q, d, e[: n - 1], P, _counts_dict(cnt)
+
+
+def update_lower(Q, d, e, P, B, C, check=True):
+    """m < n: A = Q L P^T with L lower bidiagonal (L(i,i) = d_i, L(i+1,i) = e_i,
+    m x n, columns m+1..n zero).  Sec. 1 states the factorization with an upper
+    bidiagonal and Algorithm 2 for m >= n; the m < n case is read as the
+    transposed problem A^T = P L^T Q^T (L^T upper bidiagonal, n x m), updated
+    with A^T + C B^T by the m >= n update.  Returns (Q+, d+, e+, P+, counts)
+    with counts' "left" the rotations on Q (the transposed problem's right
+    rotations) and "right" those on P."""
+    Q = _f64(Q); P = _f64(P)
+    m, n = Q.shape[0], P.shape[0]
+    if m >= n:
+        raise ValueError("update_lower is for m < n")
+    B = np.asarray(B, dtype=np.float64).reshape(m, -1)
+    C = np.asarray(C, dtype=np.float64).reshape(n, -1)
+    P2, d2, e2, Q2, cnt = update(P, d, e, Q, C, B, check)
+    cnt = dict(cnt)
+    cnt["left"], cnt["right"] = cnt["right"], cnt["left"]
+    return Q2, d2, e2, P2, cnt
+
+
+def lower_bidiag_dense(d, e, m, n):
+    """The m x n lower bidiagonal with diagonal d and subdiagonal e (m < n)."""
+    L = np.zeros((m, n))
+    k = len(d)
+    L[np.arange(k), np.arange(k)] = d
+    if k > 1:
+        L[np.arange(1, k), np.arange(k - 1)] = e[: k - 1]
+    return L
 
 
 class RotationList:

@@ -176,7 +176,9 @@ def update_batch(factorizations, ptrB, ptrC, ranks, stream=None):
 
 
 class Factorization:
-    """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read)."""
+    """A = Q diag-band(d, e) P^T resident on the GPU (bdu_create / bdu_update / bdu_read).
+    The band is upper bidiagonal for m >= n and lower bidiagonal for m < n;
+    d has min(m, n) entries and e one fewer."""
 
     def __init__(self, Q, d, e, P, precision=FP64, stream=None, device=0, reorth_tol=None,
                  check_every=None, engine=0, overlap=False, graphs=True, nb=0,
@@ -184,6 +186,7 @@ class Factorization:
         L = load()
         Q = _f64(Q); P = _f64(P); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.n = Q.shape[0], P.shape[0]
+        self.k = min(self.m, self.n)
         if e.size == 0:
             e = np.zeros(1)
         opt = Options()
@@ -247,17 +250,17 @@ class Factorization:
         _check(self._L, self._h, self._L.bdu_flush(self._h))
 
     def read(self):
-        m, n = self.m, self.n
+        m, n, k = self.m, self.n, self.k
         Q = np.zeros((m, m), order="F"); P = np.zeros((n, n), order="F")
-        d = np.zeros(n); e = np.zeros(max(n - 1, 1))
+        d = np.zeros(k); e = np.zeros(max(k - 1, 1))
         _check(self._L, self._h, self._L.bdu_read(self._h, _dp(Q), _dp(d), _dp(e), _dp(P)))
-        return Q, d, e[: n - 1], P
+        return Q, d, e[: k - 1], P
 
     def read_bidiagonal(self):
-        n = self.n
-        d = np.zeros(n); e = np.zeros(max(n - 1, 1))
+        k = self.k
+        d = np.zeros(k); e = np.zeros(max(k - 1, 1))
         _check(self._L, self._h, self._L.bdu_read(self._h, None, _dp(d), _dp(e), None))
-        return d, e[: n - 1]
+        return d, e[: k - 1]
 
     def read_rotations(self, side):
         cnt = ctypes.c_int64()
@@ -281,7 +284,7 @@ class Factorization:
 
     def singular_values(self, k=None):
         """The k largest singular values of Bd, descending (bdu_singular_values)."""
-        k = self.n if k is None else int(k)
+        k = self.k if k is None else int(k)
         sv = np.zeros(max(k, 1))
         _check(self._L, self._h, self._L.bdu_singular_values(self._h, k, _dp(sv)))
         return sv[:k]

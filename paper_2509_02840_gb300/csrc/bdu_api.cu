@@ -61,7 +61,12 @@ struct Alloc {
 }  // namespace
 
 struct bdu_ctx {
-  int64_t m, n, N;
+  int64_t m, n, N;  // of the problem held: m >= n (the transpose of the caller's when tr)
+  // The caller's m < n: A = Q L P^T with L lower bidiagonal is held as
+  // A^T = P L^T Q^T, whose L^T is upper bidiagonal with the same d, e.  The
+  // entry points swap Q and P, B and C, the sides of rotations and the
+  // per-factor statistics; everything below works on the m >= n problem.
+  bool tr = false;
   bdu_options opt;
   int device;
   cudaStream_t stream;
@@ -1123,7 +1128,13 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
                       const double *e, const double *P, const bdu_options *opt) {
   if (!out) return fail(nullptr, BDU_EINVAL, "bdu_create: output handle pointer is NULL");
   *out = nullptr;
-  if (n < 1 || m < n) return fail(nullptr, BDU_EINVAL, "bdu_create: need m >= n >= 1 (m=%lld n=%lld)", (long long)m, (long long)n);
+  if (n < 1 || m < 1) return fail(nullptr, BDU_EINVAL, "bdu_create: need m, n >= 1 (m=%lld n=%lld)", (long long)m, (long long)n);
+  if (m < n) {
+    // the transposed problem: A^T = P L^T Q^T (n x m, upper bidiagonal L^T)
+    const bdu_status st = bdu_create(out, n, m, P, d, e, Q, opt);
+    if (st == BDU_OK) (*out)->tr = true;
+    return st;
+  }
   if (m > (1LL << 20)) return fail(nullptr, BDU_EINVAL, "bdu_create: m=%lld exceeds the supported 2^20", (long long)m);
   if (!Q || !d || !P || (n > 1 && !e)) return fail(nullptr, BDU_EINVAL, "bdu_create: NULL input pointer");
   bdu_options o;
@@ -1283,15 +1294,31 @@ static bdu_status update_common(bdu_handle h, const double *B, const double *C, 
 }
 
 bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r) {
+  // transposed form: A^T + C B^T
+  if (h && h->tr) return update_common(h, C, B, r, true);
   return update_common(h, B, C, r, true);
 }
 
 bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r) {
+  if (h && h->tr) return update_common(h, dC, dB, r, false);
   return update_common(h, dB, dC, r, false);
 }
 
+static bdu_status update_batch_held(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
+                                    const int64_t *r, void *stream);
+
 bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
                             const int64_t *r, void *stream) {
+  if (count <= 0 || !hs || !dB || !dC) return update_batch_held(hs, count, dB, dC, r, stream);
+  // B and C trade places for the handles held in transposed form
+  std::vector<const double *> b(dB, dB + count), c(dC, dC + count);
+  for (int i = 0; i < count; i++)
+    if (hs[i] && hs[i]->tr) std::swap(b[i], c[i]);
+  return update_batch_held(hs, count, b.data(), c.data(), r, stream);
+}
+
+static bdu_status update_batch_held(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
+                                    const int64_t *r, void *stream) {
   if (count < 0) return fail(nullptr, BDU_EINVAL, "bdu_update_batch: negative count");
   if (count == 0) return BDU_OK;
   if (!hs || !dB || !dC || !r) return fail(nullptr, BDU_EINVAL, "bdu_update_batch: NULL argument");
@@ -1519,6 +1546,7 @@ bdu_status bdu_flush(bdu_handle h) {
 
 bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
   if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  if (h->tr) std::swap(Q, P);
   Guard g(h);
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   cudaSetDevice(h->device);
@@ -1550,6 +1578,7 @@ bdu_status bdu_read(bdu_handle h, double *Q, double *d, double *e, double *P) {
 bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int32_t *a,
                               int64_t cap, int64_t *count) {
   if (!h || !count || (side != 0 && side != 1)) return fail(h, BDU_EINVAL, "bdu_read_rotations: bad argument");
+  if (h->tr) side ^= 1;  // the rotations on the caller's Q act on the held P
   Guard g(h);
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
   cudaSetDevice(h->device);
@@ -1610,9 +1639,10 @@ bdu_status bdu_read_rotations(bdu_handle h, int side, double *c, double *s, int3
 
 bdu_status bdu_read_truncated(bdu_handle h, int64_t r, double *L, double *R, int64_t *idx, double *err2) {
   if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  if (h->tr) std::swap(L, R);  // A_r = (L' R'^T)^T for the held A^T
   Guard g(h);
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
-  if (r < 0 || r > h->n) return fail(h, BDU_EINVAL, "bdu_read_truncated: need 0 <= r <= n (r=%lld)", (long long)r);
+  if (r < 0 || r > h->n) return fail(h, BDU_EINVAL, "bdu_read_truncated: need 0 <= r <= min(m, n) (r=%lld)", (long long)r);
   cudaSetDevice(h->device);
   bdu_status st = BDU_OK;
   if (!h->poisoned) st = flush_apply(h);
@@ -1685,7 +1715,7 @@ bdu_status bdu_singular_values(bdu_handle h, int64_t k, double *sv) {
   if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
   Guard g(h);
   if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
-  if (k < 0 || k > h->n) return fail(h, BDU_EINVAL, "bdu_singular_values: need 0 <= k <= n (k=%lld)", (long long)k);
+  if (k < 0 || k > h->n) return fail(h, BDU_EINVAL, "bdu_singular_values: need 0 <= k <= min(m, n) (k=%lld)", (long long)k);
   if (k > 0 && !sv) return fail(h, BDU_EINVAL, "bdu_singular_values: NULL output");
   cudaSetDevice(h->device);
   bdu_status st = BDU_OK;
@@ -1765,6 +1795,14 @@ bdu_status bdu_stats(bdu_handle h, bdu_stats_t *out) {
   out->apply_variant[0] = h->apply_var[0];
   out->apply_variant[1] = h->apply_var[1];
   out->tunings = h->tunings;
+  if (h->tr) {
+    // left = on the caller's Q, which is the held P
+    for (int q = 0; q < 4; q++) std::swap(out->rot_left[q], out->rot_right[q]);
+    std::swap(out->ortho_q, out->ortho_p);
+    std::swap(out->reorth_q, out->reorth_p);
+    std::swap(out->ms_apply_q, out->ms_apply_p);
+    std::swap(out->apply_variant[0], out->apply_variant[1]);
+  }
   return BDU_OK;
 }
 
@@ -1779,6 +1817,7 @@ bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est) {
   if (st == BDU_OK) st = probe_factor(h, 0, &e0);
   if (st == BDU_OK) st = probe_factor(h, 1, &e1);
   if (st != BDU_OK) return st;
+  if (h->tr) std::swap(e0, e1);
   if (q_est) *q_est = e0;
   if (p_est) *p_est = e1;
   return BDU_OK;

@@ -38,12 +38,14 @@ def householder_orthogonal(n: int, g: np.random.Generator, reflectors: int = 8) 
 
 
 def factorization(m: int, n: int, config: int = 0, which: int = 0):
-    """Returns (Q, d, e, P) in FP64, column-major."""
+    """Returns (Q, d, e, P) in FP64, column-major; d has min(m, n) entries
+    (the band is lower bidiagonal when m < n)."""
     g = rng(config, 1_000_000 + which)
     Q = householder_orthogonal(m, g)
     P = householder_orthogonal(n, g)
-    d = g.uniform(1.0, 10.0, n)
-    e = g.standard_normal(max(n - 1, 0))
+    k = min(m, n)
+    d = g.uniform(1.0, 10.0, k)
+    e = g.standard_normal(max(k - 1, 0))
     return Q, d, e, P
 
 

@@ -49,6 +49,8 @@ def reserve_bytes(m, n, precision, max_rank=4):
     the workspace of a rank-max_rank update and, in the mixed form, the
     re-orthogonalization workspace that the first re-orthogonalization adds."""
     es = 8 if precision == bdu.FP64 else 4
+    if m < n:
+        m, n = n, m  # held as the transposed problem
     N = n + 1 if m > n else n
     T = (N - 1) + max(n - 2, 0) + 2 * (n if N == n + 1 else n - 1)
     tc = T * (n // 2 + 4)

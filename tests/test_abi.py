@@ -38,11 +38,19 @@ def _create(lib, m, n, Q, d, e, P):
 
 def test_create_rejects_bad_arguments_without_a_gpu(lib):
     I4 = np.eye(4); I3 = np.eye(3); d = np.ones(4); e = np.ones(3)
-    code, h = _create(lib, 3, 4, I3, d, e, I4)          # m < n
+    code, h = _create(lib, 0, 4, I3, d, e, I4)          # m < 1
     assert code == 1 and not h.value
-    assert b"m >= n" in lib.bdu_last_error(None)
+    assert b"m, n >= 1" in lib.bdu_last_error(None)
     code, _ = _create(lib, 4, 0, I4, d, e, I4)          # n < 1
     assert code == 1
+    # m < n is held as the transposed problem: its arguments are checked the same way
+    code, _ = _create(lib, 3, 4, None, d, e, I4)        # NULL Q
+    assert code == 1
+    code, _ = _create(lib, 3, 4, I3, d, None, I4)       # NULL e with min(m, n) > 1
+    assert code == 1
+    bad3 = I3.copy(); bad3[0, 1] = np.nan
+    code, _ = _create(lib, 3, 4, bad3, d, e, I4)        # non-finite Q
+    assert code == 1 and b"non-finite" in lib.bdu_last_error(None)
     code, _ = _create(lib, 4, 4, None, d, e, I4)        # NULL Q
     assert code == 1
     code, _ = _create(lib, 4, 4, I4, d, None, I4)       # NULL e with n > 1
