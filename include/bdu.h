@@ -294,6 +294,57 @@ void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx);
 bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, double *d, double *e,
                                     double *P, const double *b, const double *c, void *stream);
 
+/* ---- Rank-k subspace tracking (Sec. 5, Eqs. lrup, defup, qrlr, equivlrup,
+ * bdlrup) --------------------------------------------------------------------
+ * A thin factorization A ~ Q1 B P1^T with Q1 (m x k) and P1 (n x k) of
+ * orthonormal columns and B k x k upper bidiagonal (diagonal d, superdiagonal
+ * e) is updated by A+ = Q1 B P1^T + b c^T and truncated back to rank k:
+ *   b+ = Q1^T b, b_perp = b - Q1 b+, delta = ||b_perp|| (Eq. defup; classical
+ *   Gram-Schmidt applied twice), likewise c+, c_perp, gamma; the middle matrix
+ *   [B 0; 0 0] + [b+; delta][c+; gamma]^T (Eq. equivlrup) is reduced by the
+ *   bidiagonal update of this library (Algorithm 2, FP64, on the device) to
+ *   Q2 Bbar+ P2^T; then A+ = [Q1, b_perp/delta] Q2 Bbar+ ([P1, c_perp/gamma] P2)^T
+ *   exactly (Eq. bdlrup).  The index i with the smallest column norm
+ *   alpha_i^2 + beta_{i-1}^2 of Bbar+ (ties: the last such i) is removed with
+ *   its row and column (the superdiagonal entry across it is zero) and
+ *   Q1+ = [Q1, b_perp/delta] Q2(:, kept), P1+ likewise (cuBLAS GEMMs).
+ *   When delta <= 2^-40 ||b|| (b in span(Q1)) delta is taken as 0 and the new
+ *   column is the fixed vector z_i = frac(i * 0.6180339887498949) - 0.5
+ *   orthogonalized against Q1 in the same way (likewise for c).
+ * FP64 only (opt->precision must be BDU_FP64; overlap is ignored).  Errors are
+ * status codes; the message of the most recent failure is returned by
+ * bdu_thin_last_error (of NULL after a failed bdu_thin_create). */
+typedef struct bdu_thin_ctx *bdu_thin_handle;
+
+/* Q1: m*k, P1: n*k host doubles (column-major, orthonormal columns, not
+ * checked), d: k, e: k-1 (may be NULL when k == 1).  1 <= k < min(m, n),
+ * k < 16384.  Errors: BDU_EINVAL, BDU_ENOMEM, BDU_ECUDA. */
+bdu_status bdu_thin_create(bdu_thin_handle *h, int64_t m, int64_t n, int64_t k, const double *Q1,
+                           const double *d, const double *e, const double *P1, const bdu_options *opt);
+
+/* One step with host vectors b (m) and c (n) (Eq. lrup); returns once it is
+ * complete.  *dropped (may be NULL) receives the removed index i (0-based,
+ * 0..k) and *err2 (may be NULL) the truncation error
+ * ||A+ - Q1+ B+ P1+^T||_F^2 = alpha_i^2 + beta_{i-1}^2 + beta_i^2 (exact for
+ * orthonormal factors).  Errors: BDU_EINVAL, BDU_EBUSY, BDU_EPOISONED,
+ * BDU_ECUDA, BDU_ETIMEOUT, BDU_EINTERNAL. */
+bdu_status bdu_thin_update(bdu_thin_handle h, const double *b, const double *c, int64_t *dropped, double *err2);
+
+/* As bdu_thin_update with b and c in device memory (FP64). */
+bdu_status bdu_thin_update_dev(bdu_thin_handle h, const double *db, const double *dc, int64_t *dropped,
+                               double *err2);
+
+/* Copies Q1 (m*k), d (k), e (k-1), P1 (n*k) to host buffers (any may be NULL). */
+bdu_status bdu_thin_read(bdu_thin_handle h, double *Q1, double *d, double *e, double *P1);
+
+/* Steps taken, and how many of them found b (c) inside span(Q1) (span(P1)). */
+bdu_status bdu_thin_stats(bdu_thin_handle h, int64_t *updates, int64_t *in_span_b, int64_t *in_span_c);
+
+const char *bdu_thin_last_error(bdu_thin_handle h);
+
+/* Releases the handle's device memory.  NULL is accepted. */
+void bdu_thin_destroy(bdu_thin_handle h);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bdu_version(void);
 

@@ -15,6 +15,7 @@ apply_rows(X, rows, rotlist)    X(rows, :) <- X(rows, :) * prod(rotations)
 jacobi_sv(X)                    one-sided Jacobi singular values (tiny inputs)
 truncated_bd(Q, d, e, P, r)     truncated bidiagonal approximation, Eqs. trBD / errtrBD
 singular_values(d, e)           singular values of the bidiagonal (library SVD)
+thin_update(Q1, d, e, P1, b, c) rank-k subspace tracking step, Eqs. lrup - bdlrup
 """
 import ctypes
 import os
@@ -301,3 +302,89 @@ def singular_values(d, e):
     """Singular values of the upper bidiagonal (d, e), descending: the plain
     definition, evaluated by a library SVD of the dense n x n matrix."""
     return np.linalg.svd(bidiag_dense(d, e), compute_uv=False)
+
+
+# ---------------------------------------------------------------------------
+# Thin (rank-k) tracking, Sec. 5 (Eqs. lrup, defup, qrlr, equivlrup, bdlrup)
+# ---------------------------------------------------------------------------
+THIN_TAU = 2.0 ** -40          # b is taken to lie in span(Q1) when ||b_perp|| <= THIN_TAU ||b||
+GOLDEN = 0.6180339887498949    # the FP64 value nearest (sqrt(5) - 1) / 2
+
+
+def fill_vector(m):
+    """The fixed direction used when b lies in span(Q1): z_i = frac(i * GOLDEN) - 0.5,
+    i = 0..m-1, each step one IEEE operation."""
+    t = np.arange(m, dtype=np.float64) * GOLDEN
+    return t - np.floor(t) - 0.5
+
+
+def _cgs2(X, b):
+    """Classical Gram-Schmidt against the columns of X, run twice: returns
+    (X^T b accumulated over both passes, the remainder)."""
+    h1 = X.T @ b
+    r = b - X @ h1
+    h2 = X.T @ r
+    r = r - X @ h2
+    return h1 + h2, r
+
+
+def _augment(X, b):
+    """Eq. defup and Eq. qrlr: (projection, delta, new unit column)."""
+    bh, r = _cgs2(X, b)
+    delta = float(np.linalg.norm(r))
+    if delta > THIN_TAU * float(np.linalg.norm(b)):
+        return bh, delta, r / delta
+    _, rz = _cgs2(X, fill_vector(X.shape[0]))
+    return bh, 0.0, rz / np.linalg.norm(rz)
+
+
+def thin_update(Q1, d, e, P1, b, c, full=False):
+    """One step of rank-k tracking (Sec. 5): A+ = Q1 B P1^T + b c^T with Q1 (m x k),
+    P1 (n x k) orthonormal and B = diag-band(d, e) k x k upper bidiagonal.
+
+    b+ = Q1^T b, b_perp = b - Q1 b+, delta = ||b_perp|| (Eq. defup; the
+    projection is taken twice, classical Gram-Schmidt with one reorthogonalization);
+    Q1bar = [Q1, b_perp / delta] (Eq. qrlr), likewise for c.  The middle matrix
+    [B 0; 0 0] + [b+; delta][c+; gamma]^T (Eq. equivlrup) is reduced by the update
+    of this module (Algorithm 2 on the (k+1)-order problem with identity factors),
+    giving Q2, Bbar+, P2 and A+ = (Q1bar Q2) Bbar+ (P1bar P2)^T (Eq. bdlrup).  The
+    index i with the smallest column norm alpha_i^2 + beta_{i-1}^2 of Bbar+ (ties:
+    the last such i) is removed with its row and column; the kept superdiagonal
+    entry between the neighbours of i is zero.  When ||b_perp|| <= THIN_TAU ||b||
+    (b in span(Q1)), delta = 0 and the new column is the fixed vector
+    orthogonalized against Q1 the same way (it then carries a zero row of the
+    middle matrix).
+
+    Returns (Q1+, d+, e+, P1+, i (0-based removed index), err2 = ||A+ - Q1+ B+ P1+^T||_F^2
+    = alpha_i^2 + beta_{i-1}^2 + beta_i^2); with full=True also the untruncated
+    (Q1bar Q2, dbar, ebar, P1bar P2)."""
+    Q1 = np.asarray(Q1, dtype=np.float64); P1 = np.asarray(P1, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64).ravel(); e = np.asarray(e, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel(); c = np.asarray(c, dtype=np.float64).ravel()
+    k = Q1.shape[1]
+    if k < 1 or P1.shape[1] != k or len(d) != k or len(e) != k - 1:
+        raise ValueError("Q1 m x k, P1 n x k, d (k), e (k-1) with k >= 1 required")
+    bh, delta, qa = _augment(Q1, b)
+    ch, gamma, pa = _augment(P1, c)
+    Qb = np.column_stack([Q1, qa])
+    Pb = np.column_stack([P1, pa])
+    I = np.eye(k + 1)
+    Q2, d2, e2, P2, _ = update(I, np.append(d, 0.0), np.append(e, 0.0), I,
+                               np.append(bh, delta), np.append(ch, gamma))
+    w = d2 * d2
+    w[1:] = w[1:] + e2 * e2
+    i = int(np.flatnonzero(w == w.min())[-1])
+    keep = [j for j in range(k + 1) if j != i]
+    Q1n = Qb @ Q2[:, keep]
+    P1n = Pb @ P2[:, keep]
+    dn = d2[keep]
+    en = np.array([e2[keep[t]] if keep[t + 1] == keep[t] + 1 else 0.0 for t in range(k - 1)])
+    err2 = d2[i] * d2[i]
+    if i > 0:
+        err2 = err2 + e2[i - 1] * e2[i - 1]
+    if i < k:
+        err2 = err2 + e2[i] * e2[i]
+    out = (Q1n, dn, en, P1n, i, float(err2))
+    if full:
+        out = out + ((Qb @ Q2, d2, e2, Pb @ P2),)
+    return out

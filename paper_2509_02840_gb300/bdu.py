@@ -105,6 +105,22 @@ def load(build_if_missing: bool = True):
     L.bdu_set_allocator.restype = None
     L.bdu_version.argtypes = []
     L.bdu_version.restype = ctypes.c_int
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.bdu_thin_create.argtypes = [ctypes.POINTER(H), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
+                                  ctypes.POINTER(Options)]
+    L.bdu_thin_create.restype = ctypes.c_int
+    L.bdu_thin_update.argtypes = [H, dp, dp, i64p, dp]
+    L.bdu_thin_update.restype = ctypes.c_int
+    L.bdu_thin_update_dev.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, i64p, dp]
+    L.bdu_thin_update_dev.restype = ctypes.c_int
+    L.bdu_thin_read.argtypes = [H, dp, dp, dp, dp]
+    L.bdu_thin_read.restype = ctypes.c_int
+    L.bdu_thin_stats.argtypes = [H, i64p, i64p, i64p]
+    L.bdu_thin_stats.restype = ctypes.c_int
+    L.bdu_thin_last_error.argtypes = [H]
+    L.bdu_thin_last_error.restype = ctypes.c_char_p
+    L.bdu_thin_destroy.argtypes = [H]
+    L.bdu_thin_destroy.restype = None
     _lib = L
     return L
 
@@ -308,3 +324,81 @@ class Factorization:
 
     def set_timing(self, on=True):
         _check(self._L, self._h, self._L.bdu_set_timing(self._h, 1 if on else 0))
+
+
+class ThinTracker:
+    """Rank-k subspace tracking A ~ Q1 B P1^T under rank-1 updates, truncated
+    back to rank k after each (bdu_thin_create / bdu_thin_update / bdu_thin_read;
+    Sec. 5).  FP64."""
+
+    def __init__(self, Q1, d, e, P1, stream=None, device=0, engine=0, graphs=True):
+        L = load()
+        Q1 = _f64(Q1); P1 = _f64(P1); d = _f64(d).ravel(); e = _f64(e).ravel()
+        self.m, self.k = Q1.shape
+        self.n = P1.shape[0]
+        if e.size == 0:
+            e = np.zeros(1)
+        opt = Options()
+        L.bdu_default_options(ctypes.byref(opt))
+        opt.device = int(device)
+        opt.engine = int(engine)
+        opt.graphs = 1 if graphs else 0
+        if stream is not None:
+            opt.cuda_stream = ctypes.c_void_p(int(stream))
+        h = ctypes.c_void_p()
+        code = L.bdu_thin_create(ctypes.byref(h), self.m, self.n, self.k, _dp(Q1), _dp(d), _dp(e), _dp(P1),
+                                 ctypes.byref(opt))
+        if code != 0:
+            raise BduError(code, L.bdu_thin_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    def _check(self, code):
+        if code != 0:
+            msg = self._L.bdu_thin_last_error(self._h)
+            raise BduError(code, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bdu_thin_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def update(self, b, c):
+        """One step; returns (removed index (0-based, 0..k), truncation error ||.||_F^2)."""
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).ravel())
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).ravel())
+        if b.size != self.m or c.size != self.n:
+            raise ValueError("b needs m entries and c n entries")
+        i = ctypes.c_int64(); err2 = ctypes.c_double()
+        self._check(self._L.bdu_thin_update(self._h, _dp(b), _dp(c), ctypes.byref(i), ctypes.byref(err2)))
+        return i.value, err2.value
+
+    def update_dev(self, ptr_b: int, ptr_c: int):
+        i = ctypes.c_int64(); err2 = ctypes.c_double()
+        self._check(self._L.bdu_thin_update_dev(self._h, ctypes.c_void_p(ptr_b), ctypes.c_void_p(ptr_c),
+                                                ctypes.byref(i), ctypes.byref(err2)))
+        return i.value, err2.value
+
+    def read(self):
+        m, n, k = self.m, self.n, self.k
+        Q1 = np.zeros((m, k), order="F"); P1 = np.zeros((n, k), order="F")
+        d = np.zeros(k); e = np.zeros(max(k - 1, 1))
+        self._check(self._L.bdu_thin_read(self._h, _dp(Q1), _dp(d), _dp(e), _dp(P1)))
+        return Q1, d, e[: k - 1], P1
+
+    def stats(self):
+        u, sb, sc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._L.bdu_thin_stats(self._h, ctypes.byref(u), ctypes.byref(sb), ctypes.byref(sc)))
+        return {"updates": u.value, "in_span_b": sb.value, "in_span_c": sc.value}

@@ -1832,4 +1832,337 @@ bdu_status bdu_set_timing(bdu_handle h, int on) {
   return BDU_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Rank-k tracking (Sec. 5, Eqs. lrup, defup, qrlr, equivlrup, bdlrup).  The
+// thin factors [Q1, new column] and [P1, new column] live in FP64 device
+// buffers of k+1 columns; the (k+1)-order middle matrix is reduced by an
+// internal FP64 handle (the chase and application kernels of the full
+// update) whose factors are reset to the identity before every step, so that
+// afterwards they hold Q2 and P2.  The projections (classical Gram-Schmidt,
+// twice) and the products [Q1, q] Q2(:, kept) are cuBLAS BLAS-2/3 calls: the
+// products are plain GEMMs, the step's largest cost for m, n >> k.
+// ---------------------------------------------------------------------------
+struct bdu_thin_ctx {
+  int64_t m, n, k;
+  bdu_ctx *core = nullptr;
+  double *Qb = nullptr, *Pb = nullptr, *Qn = nullptr, *Pn = nullptr;
+  double *x = nullptr, *y = nullptr, *r = nullptr, *zq = nullptr, *zp = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *u = nullptr, *v = nullptr, *ones = nullptr, *K2 = nullptr;
+  std::vector<double> d, e;
+  double delta_host[2] = {0.0, 0.0};
+  int64_t updates = 0, in_span_b = 0, in_span_c = 0;
+  std::atomic<int> busy{0};
+};
+
+namespace {
+
+constexpr double kThinTau = 0x1p-40;                  // b in span(Q1) when ||b_perp|| <= kThinTau ||b||
+constexpr double kGolden = 0.6180339887498949;        // FP64 nearest (sqrt(5) - 1) / 2
+
+struct ThinGuard {
+  bdu_thin_ctx *t;
+  bool ok;
+  explicit ThinGuard(bdu_thin_ctx *tt) : t(tt), ok(false) {
+    int expect = 0;
+    ok = t->busy.compare_exchange_strong(expect, 1);
+  }
+  ~ThinGuard() {
+    if (ok) t->busy.store(0);
+  }
+};
+
+// The middle matrix's factorization starts from Q = P = I and Bd = [B 0; 0 0]
+// (beta_k = 0 between B and the zero block).
+bdu_status thin_reset_core(bdu_thin_ctx *t) {
+  bdu_ctx *h = t->core;
+  const int64_t N = t->k + 1;
+  cudaStream_t s = h->stream;
+  cublasHandle_t cb = (cublasHandle_t)h->cublas;
+  cudaError_t ce = cudaMemsetAsync(h->Q, 0, sizeof(double) * N * N, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->P, 0, sizeof(double) * N * N, s);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: resetting the middle factors");
+  if (cublasDcopy(cb, (int)N, t->ones, 1, (double *)h->Q, (int)N + 1) != CUBLAS_STATUS_SUCCESS ||
+      cublasDcopy(cb, (int)N, t->ones, 1, (double *)h->P, (int)N + 1) != CUBLAS_STATUS_SUCCESS)
+    return fail(h, BDU_ECUDA, "rank-k step: cuBLAS copy failed");
+  std::vector<double> hb(band_doubles(N, N), 0.0);
+  BandPtrs hp = band_ptrs(hb.data(), N, N);
+  hp.r1[1] = t->d[0];
+  hp.r1[2] = t->k > 1 ? t->e[0] : 0.0;
+  for (int64_t i = 2; i <= t->k; i++) hp.dg[2][i] = t->d[i - 1];
+  for (int64_t i = 2; i <= t->k - 1; i++) hp.dg[3][i] = t->e[i - 1];
+  ce = cudaMemcpyAsync(h->band, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  return ce == cudaSuccess ? BDU_OK : cuda_fail(h, ce, "rank-k step: resetting the middle band");
+}
+
+// Eq. defup and Eq. qrlr for one side: w[0:k] = X^T b (two Gram-Schmidt
+// passes, accumulated), the remainder's norm delta into w[k], and the unit
+// remainder into column k of X (len x (k+1)); when b lies in span(X) the
+// fixed fill vector is orthogonalized instead and delta = 0.
+bdu_status thin_side(bdu_thin_ctx *t, double *X, int64_t len, const double *b, const double *fill, double *w,
+                     int which, bool *in_span) {
+  bdu_ctx *h = t->core;
+  cublasHandle_t cb = (cublasHandle_t)h->cublas;
+  const int L = (int)len, k = (int)t->k;
+  const double one = 1.0, zero = 0.0, mone = -1.0;
+  auto ok = [](cublasStatus_t st) { return st == CUBLAS_STATUS_SUCCESS; };
+  auto cgs2 = [&](const double *src, double *proj) {
+    return ok(cublasDgemv(cb, CUBLAS_OP_T, L, k, &one, X, L, src, 1, &zero, t->h1, 1)) &&
+           ok(cublasDcopy(cb, L, src, 1, t->r, 1)) &&
+           ok(cublasDgemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, t->h1, 1, &one, t->r, 1)) &&
+           ok(cublasDgemv(cb, CUBLAS_OP_T, L, k, &one, X, L, t->r, 1, &zero, proj, 1)) &&
+           ok(cublasDgemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, proj, 1, &one, t->r, 1)) &&
+           ok(cublasDaxpy(cb, k, &one, t->h1, 1, proj, 1));
+  };
+  double nb = 0.0, dl = 0.0;
+  if (!cgs2(b, w) || !ok(cublasDnrm2(cb, L, b, 1, &nb)) || !ok(cublasDnrm2(cb, L, t->r, 1, &dl)))
+    return fail(h, BDU_ECUDA, "rank-k step: cuBLAS projection failed");
+  double *col = X + (size_t)k * len;
+  *in_span = !(dl > kThinTau * nb);
+  double scale_norm = dl;
+  if (*in_span) {
+    dl = 0.0;
+    if (!cgs2(fill, t->h2) || !ok(cublasDnrm2(cb, L, t->r, 1, &scale_norm)))
+      return fail(h, BDU_ECUDA, "rank-k step: cuBLAS projection failed");
+    if (!(scale_norm > 0.0)) return fail(h, BDU_EINTERNAL, "rank-k step: no direction left outside the subspace");
+  }
+  const double inv = 1.0 / scale_norm;
+  if (!ok(cublasDcopy(cb, L, t->r, 1, col, 1)) || !ok(cublasDscal(cb, L, &inv, col, 1)))
+    return fail(h, BDU_ECUDA, "rank-k step: cuBLAS scaling failed");
+  t->delta_host[which] = dl;
+  cudaError_t ce = cudaMemcpyAsync(w + k, &t->delta_host[which], sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  return ce == cudaSuccess ? BDU_OK : cuda_fail(h, ce, "rank-k step: staging delta");
+}
+
+bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
+  bdu_ctx *h = t->core;
+  const int64_t m = t->m, n = t->n, k = t->k, N = k + 1;
+  cudaStream_t s = h->stream;
+  cublasHandle_t cb = (cublasHandle_t)h->cublas;
+  if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS || cublasSetPointerMode(cb, CUBLAS_POINTER_MODE_HOST) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetMathMode(cb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS)
+    return fail(h, BDU_ECUDA, "rank-k step: cuBLAS set-up failed");
+  bool sb = false, sc = false;
+  bdu_status st = thin_side(t, t->Qb, m, t->x, t->zq, t->u, 0, &sb);
+  if (st == BDU_OK) st = thin_side(t, t->Pb, n, t->y, t->zp, t->v, 1, &sc);
+  if (st == BDU_OK) st = thin_reset_core(t);
+  if (st != BDU_OK) return st;
+  // Algorithm 2 on the middle matrix (Eq. equivlrup): u = I^T u, v = I^T v exactly
+  st = bdu_update_dev(h, t->u, t->v, 1);
+  if (st != BDU_OK) return st;
+  std::vector<double> d2(N), e2(N);
+  cudaError_t ce = read_bidiagonal(h, d2.data(), e2.data());
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: reading the middle bidiagonal");
+  // the index of the smallest column norm alpha_i^2 + beta_{i-1}^2 (ties: the last)
+  int64_t drop = 0;
+  double wmin = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    volatile double a2 = d2[i] * d2[i];
+    double w = a2;
+    if (i > 0) {
+      volatile double b2 = e2[i - 1] * e2[i - 1];
+      w = a2 + b2;
+    }
+    if (i == 0 || w <= wmin) {
+      wmin = w;
+      drop = i;
+    }
+  }
+  volatile double er = d2[drop] * d2[drop];
+  double err = er;
+  if (drop > 0) {
+    volatile double t2 = e2[drop - 1] * e2[drop - 1];
+    err = err + t2;
+  }
+  if (drop < k) {
+    volatile double t3 = e2[drop] * e2[drop];
+    err = err + t3;
+  }
+  // [X, column] X2(:, kept) for X2 = Q2, P2 (Eq. bdlrup), into the spare buffer
+  const double one = 1.0, zero = 0.0;
+  for (int side = 0; side < 2; side++) {
+    const double *X2 = (const double *)(side == 0 ? h->Q : h->P);
+    if (drop > 0) ce = cudaMemcpyAsync(t->K2, X2, sizeof(double) * N * drop, cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess && drop < k)
+      ce = cudaMemcpyAsync(t->K2 + N * drop, X2 + N * (drop + 1), sizeof(double) * N * (k - drop),
+                           cudaMemcpyDeviceToDevice, s);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: gathering the kept columns");
+    const int64_t len = side == 0 ? m : n;
+    double *Xb = side == 0 ? t->Qb : t->Pb, *Xn = side == 0 ? t->Qn : t->Pn;
+    if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)len, (int)k, (int)N, &one, Xb, (int)len, t->K2, (int)N, &zero,
+                    Xn, (int)len) != CUBLAS_STATUS_SUCCESS)
+      return fail(h, BDU_ECUDA, "rank-k step: cuBLAS GEMM failed");
+  }
+  std::swap(t->Qb, t->Qn);
+  std::swap(t->Pb, t->Pn);
+  // B+ = Bbar+(kept, kept): the superdiagonal entry across the removed index is zero
+  std::vector<double> dn, en;
+  for (int64_t i = 0; i < N; i++)
+    if (i != drop) dn.push_back(d2[i]);
+  for (int64_t i = 0; i + 1 < N; i++) {
+    if (i == drop || i + 1 == drop) continue;
+    en.push_back(e2[i]);
+  }
+  if (drop > 0 && drop < k) en.insert(en.begin() + (drop - 1), 0.0);
+  t->d = dn;
+  t->e = en;
+  t->e.resize(k > 1 ? k - 1 : 0);
+  t->updates++;
+  t->in_span_b += sb;
+  t->in_span_c += sc;
+  if (dropped) *dropped = drop;
+  if (err2) *err2 = err;
+  ce = cudaStreamSynchronize(s);
+  return ce == cudaSuccess ? BDU_OK : cuda_fail(h, ce, "rank-k step");
+}
+
+}  // namespace
+
+bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k, const double *Q1, const double *d,
+                           const double *e, const double *P1, const bdu_options *opt) {
+  if (!out) return fail(nullptr, BDU_EINVAL, "bdu_thin_create: output handle pointer is NULL");
+  *out = nullptr;
+  if (k < 1 || k >= m || k >= n || k > 16383)
+    return fail(nullptr, BDU_EINVAL, "bdu_thin_create: need 1 <= k < min(m, n), k < 16384 (m=%lld n=%lld k=%lld)",
+                (long long)m, (long long)n, (long long)k);
+  if (m > (1LL << 24) || n > (1LL << 24) || m * (k + 1) > (1LL << 31) || n * (k + 1) > (1LL << 31))
+    return fail(nullptr, BDU_EINVAL, "bdu_thin_create: factors too large for one GEMM call");
+  if (!Q1 || !d || !P1 || (k > 1 && !e)) return fail(nullptr, BDU_EINVAL, "bdu_thin_create: NULL input pointer");
+  bdu_options o;
+  bdu_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != BDU_FP64) return fail(nullptr, BDU_EINVAL, "bdu_thin_create: rank-k tracking is FP64 only");
+  o.overlap = 0;
+  if (!all_finite(Q1, m * k) || !all_finite(P1, n * k) || !all_finite(d, k) || (k > 1 && !all_finite(e, k - 1)))
+    return fail(nullptr, BDU_EINVAL, "bdu_thin_create: non-finite value in Q1, d, e or P1");
+  bdu_thin_ctx *t = new (std::nothrow) bdu_thin_ctx();
+  if (!t) return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: host allocation failed");
+  t->m = m; t->n = n; t->k = k;
+  t->d.assign(d, d + k);
+  t->e.assign(k > 1 ? e : d, k > 1 ? e + (k - 1) : d);
+  const int64_t N = k + 1;
+  std::vector<double> eye(N * N, 0.0), dpad(N, 0.0), epad(N, 0.0);
+  for (int64_t i = 0; i < N; i++) eye[i * N + i] = 1.0;
+  for (int64_t i = 0; i < k; i++) dpad[i] = d[i];
+  for (int64_t i = 0; i + 1 < k; i++) epad[i] = e[i];
+  bdu_status st = bdu_create(&t->core, N, N, eye.data(), dpad.data(), epad.data(), eye.data(), &o);
+  if (st != BDU_OK) {
+    delete t;
+    return st;
+  }
+  bdu_ctx *h = t->core;
+  cublasHandle_t hb = nullptr;
+  if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) {
+    bdu_destroy(h);
+    delete t;
+    return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: cublasCreate failed");
+  }
+  h->cublas = hb;
+  const int64_t L = m > n ? m : n;
+  t->Qb = (double *)dev_alloc(h, sizeof(double) * m * N);
+  t->Qn = (double *)dev_alloc(h, sizeof(double) * m * N);
+  t->Pb = (double *)dev_alloc(h, sizeof(double) * n * N);
+  t->Pn = (double *)dev_alloc(h, sizeof(double) * n * N);
+  t->x = (double *)dev_alloc(h, sizeof(double) * m);
+  t->y = (double *)dev_alloc(h, sizeof(double) * n);
+  t->r = (double *)dev_alloc(h, sizeof(double) * L);
+  t->zq = (double *)dev_alloc(h, sizeof(double) * m);
+  t->zp = (double *)dev_alloc(h, sizeof(double) * n);
+  t->h1 = (double *)dev_alloc(h, sizeof(double) * N);
+  t->h2 = (double *)dev_alloc(h, sizeof(double) * N);
+  t->u = (double *)dev_alloc(h, sizeof(double) * N);
+  t->v = (double *)dev_alloc(h, sizeof(double) * N);
+  t->ones = (double *)dev_alloc(h, sizeof(double) * N);
+  t->K2 = (double *)dev_alloc(h, sizeof(double) * N * k);
+  if (!t->Qb || !t->Qn || !t->Pb || !t->Pn || !t->x || !t->y || !t->r || !t->zq || !t->zp || !t->h1 || !t->h2 ||
+      !t->u || !t->v || !t->ones || !t->K2) {
+    bdu_destroy(h);
+    delete t;
+    return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: device allocation failed");
+  }
+  // the fill vector z_i = frac(i * golden) - 0.5 (each step one IEEE operation)
+  std::vector<double> z(L), ones(N, 1.0);
+  for (int64_t i = 0; i < L; i++) {
+    const double a = (double)i * kGolden;
+    z[i] = (a - floor(a)) - 0.5;
+  }
+  cudaStream_t s = h->stream;
+  cudaError_t ce = cudaMemcpyAsync(t->Qb, Q1, sizeof(double) * m * k, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->Pb, P1, sizeof(double) * n * k, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zq, z.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zp, z.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->ones, ones.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    fail(nullptr, BDU_ECUDA, "bdu_thin_create: %s", cudaGetErrorString(ce));
+    bdu_destroy(h);
+    delete t;
+    return BDU_ECUDA;
+  }
+  *out = t;
+  return BDU_OK;
+}
+
+static bdu_status thin_update_common(bdu_thin_handle t, const double *b, const double *c, bool host,
+                                     int64_t *dropped, double *err2) {
+  if (!t) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  bdu_ctx *h = t->core;
+  ThinGuard g(t);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure: %s", h->err);
+  if (!b || !c) return fail(h, BDU_EINVAL, "NULL update vector");
+  if (host && (!all_finite(b, t->m) || !all_finite(c, t->n))) return fail(h, BDU_EINVAL, "non-finite value in b or c");
+  cudaError_t ce = cudaSetDevice(h->device);
+  cudaStream_t s = h->stream;
+  const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->x, b, sizeof(double) * t->m, kind, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->y, c, sizeof(double) * t->n, kind, s);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: staging b, c");
+  return thin_step(t, dropped, err2);
+}
+
+bdu_status bdu_thin_update(bdu_thin_handle t, const double *b, const double *c, int64_t *dropped, double *err2) {
+  return thin_update_common(t, b, c, true, dropped, err2);
+}
+
+bdu_status bdu_thin_update_dev(bdu_thin_handle t, const double *db, const double *dc, int64_t *dropped,
+                               double *err2) {
+  return thin_update_common(t, db, dc, false, dropped, err2);
+}
+
+bdu_status bdu_thin_read(bdu_thin_handle t, double *Q1, double *d, double *e, double *P1) {
+  if (!t) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  bdu_ctx *h = t->core;
+  ThinGuard g(t);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  cudaSetDevice(h->device);
+  cudaStream_t s = h->stream;
+  cudaError_t ce = cudaSuccess;
+  if (Q1) ce = cudaMemcpyAsync(Q1, t->Qb, sizeof(double) * t->m * t->k, cudaMemcpyDeviceToHost, s);
+  if (P1 && ce == cudaSuccess) ce = cudaMemcpyAsync(P1, t->Pb, sizeof(double) * t->n * t->k, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_thin_read");
+  if (d) std::copy(t->d.begin(), t->d.end(), d);
+  if (e) std::copy(t->e.begin(), t->e.end(), e);
+  return BDU_OK;
+}
+
+bdu_status bdu_thin_stats(bdu_thin_handle t, int64_t *updates, int64_t *in_span_b, int64_t *in_span_c) {
+  if (!t) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  if (updates) *updates = t->updates;
+  if (in_span_b) *in_span_b = t->in_span_b;
+  if (in_span_c) *in_span_c = t->in_span_c;
+  return BDU_OK;
+}
+
+const char *bdu_thin_last_error(bdu_thin_handle t) { return t ? t->core->err : t_create_err; }
+
+void bdu_thin_destroy(bdu_thin_handle t) {
+  if (!t) return;
+  bdu_destroy(t->core);
+  delete t;
+}
+
 }  // extern "C"
