@@ -28,6 +28,12 @@ reads the updated bidiagonal back every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
+  python bench.py --thin KR [--size M] [--steps K] [--warmup W]
+    rank-KR tracking (bdu_thin_*, Sec. 5) on the network edge stream at
+    m = n = M: each step is one symmetric edge insertion, i.e. two rank-1
+    tracking steps; wall clock (every tracking step completes before it
+    returns), with the CPU oracle timed on one tracking step beside it.
+
 With N > 1 (launched by torchrun) every rank updates its own factorization:
 the path does not shard, so ranks are independent replicas (weak scaling).
 The reference arm times the CPU oracle (the library's plain FP64 reference
@@ -65,6 +71,8 @@ def parse():
                     help="m = n of the workload (4096 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="mixed form only: no FP64 form, e2e or CPU baseline (profiling runs)")
+    ap.add_argument("--thin", type=int, default=0,
+                    help="rank of the thin (rank-k tracking) benchmark instead of the headline")
     a = ap.parse_args()
     global M, N
     M = N = a.size
@@ -428,8 +436,58 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_thin(args):
+    """Rank-k tracking on the network edge stream (Sec. 5 applied to the
+    Chung-Lu edge insertions): wall-clock rank-1 tracking steps per second."""
+    import numpy as np
+    import torch
+
+    from paper_2509_02840_gb300 import bdu, inputs as I
+
+    m = n = M
+    k = args.thin
+    Q1, d, e, P1 = I.thin_factors(m, n, k)
+    K, W = args.steps, max(args.warmup, 1)
+    ups = [I.network_update(n, h) for h in range(W + K)]
+    with bdu.ThinTracker(Q1, d, e, P1) as T:
+        for B, C in ups[:W]:
+            for j in range(2):
+                T.update(B[:, j], C[:, j])
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        t0 = time.perf_counter()
+        err = 0.0
+        for B, C in ups[W:]:
+            for j in range(2):
+                err += T.update(B[:, j], C[:, j])[1]
+        dt = time.perf_counter() - t0
+        clk = clocks.stop()
+        Qg, dg, eg, Pg = T.read()
+    ortho = max(float(np.linalg.norm(Qg.T @ Qg - np.eye(k), 2)), float(np.linalg.norm(Pg.T @ Pg - np.eye(k), 2)))
+    steps = 2 * K
+    line = {"metric": f"rank-{k} tracking steps/s at m=n={m} (Sec. 5, FP64)", "value": steps / dt,
+            "unit": "rank-1 tracking steps/s", "n_gpus": 1, "steps": steps, "warmup": 2 * W,
+            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"network edge stream (Chung-Lu, exponent 2.1), m=n={m}, rank {k}",
+                       "m": m, "n": n, "k": k},
+            "truncation_err2_per_step": err / steps, "orthogonality": ortho, "clocks": clk}
+    if not args.no_cpu_baseline:
+        import oracle as O
+        B, C = ups[0]
+        t0 = time.perf_counter()
+        O.thin_update(Q1, d, e, P1, B[:, 0], C[:, 0])
+        sec = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "rank-1 tracking steps/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": "one tracking step of the same stream"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.thin:
+        run_thin(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

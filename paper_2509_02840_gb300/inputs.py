@@ -97,6 +97,17 @@ def network_update(n: int, h: int, config: int = 3, exponent: float = 2.1):
     return np.asfortranarray(B), np.asfortranarray(C)
 
 
+def thin_factors(m: int, n: int, k: int, config: int = 3, which: int = 0):
+    """(Q1 m x k, d k, e k-1, P1 n x k): orthonormal columns from the QR
+    factorization of Gaussian matrices, d ~ U(1, 10), e ~ N(0, 1)."""
+    g = rng(config, 2_000_000 + which)
+    Q1 = np.linalg.qr(g.standard_normal((m, k)))[0]
+    P1 = np.linalg.qr(g.standard_normal((n, k)))[0]
+    d = g.uniform(1.0, 10.0, k)
+    e = g.standard_normal(max(k - 1, 0))
+    return np.asfortranarray(Q1), d, e, np.asfortranarray(P1)
+
+
 def serving_mix(count: int = 256, lo: int = 64, hi: int = 2048, config: int = 4):
     """(m, n) pairs, each log-uniform in [lo, hi], swapped so that m >= n."""
     g = rng(config, 0)
