@@ -28,8 +28,8 @@ reads the updated bidiagonal back every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
-  python bench.py --thin KR [--size M] [--steps K] [--warmup W]
-    rank-KR tracking (bdu_thin_*, Sec. 5) on the network edge stream at
+  python bench.py --thin KR [--thin-fp64] [--size M] [--steps K] [--warmup W]
+    rank-KR tracking (bdu_thin_*, Sec. 5; mixed form unless --thin-fp64) on the network edge stream at
     m = n = M: each step is one symmetric edge insertion, i.e. two rank-1
     tracking steps; wall clock (every tracking step completes before it
     returns), with the CPU oracle timed on one tracking step beside it.
@@ -73,6 +73,7 @@ def parse():
                     help="mixed form only: no FP64 form, e2e or CPU baseline (profiling runs)")
     ap.add_argument("--thin", type=int, default=0,
                     help="rank of the thin (rank-k tracking) benchmark instead of the headline")
+    ap.add_argument("--thin-fp64", action="store_true", help="the FP64 form of rank-k tracking (default: mixed)")
     a = ap.parse_args()
     global M, N
     M = N = a.size
@@ -449,7 +450,8 @@ def run_thin(args):
     Q1, d, e, P1 = I.thin_factors(m, n, k)
     K, W = args.steps, max(args.warmup, 1)
     ups = [I.network_update(n, h) for h in range(W + K)]
-    with bdu.ThinTracker(Q1, d, e, P1) as T:
+    prec = bdu.FP64 if args.thin_fp64 else bdu.MIXED
+    with bdu.ThinTracker(Q1, d, e, P1, precision=prec) as T:
         for B, C in ups[:W]:
             for j in range(2):
                 T.update(B[:, j], C[:, j])
@@ -466,9 +468,11 @@ def run_thin(args):
         Qg, dg, eg, Pg = T.read()
     ortho = max(float(np.linalg.norm(Qg.T @ Qg - np.eye(k), 2)), float(np.linalg.norm(Pg.T @ Pg - np.eye(k), 2)))
     steps = 2 * K
-    line = {"metric": f"rank-{k} tracking steps/s at m=n={m} (Sec. 5, FP64)", "value": steps / dt,
+    form = "FP64" if args.thin_fp64 else "mixed: FP32 factors, FP64 middle band"
+    line = {"metric": f"rank-{k} tracking steps/s at m=n={m} (Sec. 5, {form})", "value": steps / dt,
             "unit": "rank-1 tracking steps/s", "n_gpus": 1, "steps": steps, "warmup": 2 * W,
-            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "dtype": "f64" if args.thin_fp64 else "f32+f64",
+            "data": "synthetic",
             "config": {"workload": f"network edge stream (Chung-Lu, exponent 2.1), m=n={m}, rank {k}",
                        "m": m, "n": n, "k": k},
             "truncation_err2_per_step": err / steps, "orthogonality": ortho, "clocks": clk}

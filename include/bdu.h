@@ -311,8 +311,12 @@ bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, double *d, 
  *   When delta <= 2^-40 ||b|| (b in span(Q1)) delta is taken as 0 and the new
  *   column is the fixed vector z_i = frac(i * 0.6180339887498949) - 0.5
  *   orthogonalized against Q1 in the same way (likewise for c).
- * FP64 only (opt->precision must be BDU_FP64; overlap is ignored).  Errors are
- * status codes; the message of the most recent failure is returned by
+ * opt->precision: BDU_FP64, or BDU_MIXED: Q1, P1, Q2, P2 in FP32 (the middle
+ * band and its rotations in FP64), FP32 products, one Newton-Schulz step on Q1
+ * and P1 after every step, and b in span(Q1) below delta <= 2^-16 ||b||.
+ * overlap, check_every and the re-orthogonalization options are not used for
+ * the middle matrix (its factors start from the identity at every step).
+ * Errors are status codes; the message of the most recent failure is returned by
  * bdu_thin_last_error (of NULL after a failed bdu_thin_create). */
 typedef struct bdu_thin_ctx *bdu_thin_handle;
 

@@ -329,9 +329,9 @@ class Factorization:
 class ThinTracker:
     """Rank-k subspace tracking A ~ Q1 B P1^T under rank-1 updates, truncated
     back to rank k after each (bdu_thin_create / bdu_thin_update / bdu_thin_read;
-    Sec. 5).  FP64."""
+    Sec. 5).  precision FP64, or MIXED (FP32 thin factors, FP64 middle band)."""
 
-    def __init__(self, Q1, d, e, P1, stream=None, device=0, engine=0, graphs=True):
+    def __init__(self, Q1, d, e, P1, precision=FP64, stream=None, device=0, engine=0, graphs=True):
         L = load()
         Q1 = _f64(Q1); P1 = _f64(P1); d = _f64(d).ravel(); e = _f64(e).ravel()
         self.m, self.k = Q1.shape
@@ -340,6 +340,7 @@ class ThinTracker:
             e = np.zeros(1)
         opt = Options()
         L.bdu_default_options(ctypes.byref(opt))
+        opt.precision = int(precision)
         opt.device = int(device)
         opt.engine = int(engine)
         opt.graphs = 1 if graphs else 0

@@ -388,7 +388,7 @@ bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s) {
       return fail(h, BDU_ENOMEM, "re-orthogonalization workspace allocation failed");
     }
   }
-  cudaError_t e = launch_reorth32((float *)(which == 0 ? h->Q : h->P), (int)k, (float *)h->rx_E, (float *)h->rx_W,
+  cudaError_t e = launch_reorth32((float *)(which == 0 ? h->Q : h->P), k, (int)k, (float *)h->rx_E, (float *)h->rx_W,
                                   h->cublas, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "re-orthogonalization");
   h->reorth[which]++;
@@ -1833,22 +1833,29 @@ bdu_status bdu_set_timing(bdu_handle h, int on) {
 }
 
 
+}  // extern "C"
+
 // ---------------------------------------------------------------------------
 // Rank-k tracking (Sec. 5, Eqs. lrup, defup, qrlr, equivlrup, bdlrup).  The
-// thin factors [Q1, new column] and [P1, new column] live in FP64 device
-// buffers of k+1 columns; the (k+1)-order middle matrix is reduced by an
-// internal FP64 handle (the chase and application kernels of the full
-// update) whose factors are reset to the identity before every step, so that
-// afterwards they hold Q2 and P2.  The projections (classical Gram-Schmidt,
-// twice) and the products [Q1, q] Q2(:, kept) are cuBLAS BLAS-2/3 calls: the
-// products are plain GEMMs, the step's largest cost for m, n >> k.
+// thin factors [Q1, new column] and [P1, new column] live in device buffers of
+// k+1 columns (FP64, or FP32 in the mixed form); the (k+1)-order middle matrix
+// is reduced by an internal handle of the same form (the chase and application
+// kernels of the full update) whose factors are reset to the identity before
+// every step, so that afterwards they hold Q2 and P2.  The projections
+// (classical Gram-Schmidt, twice) and the products [Q1, q] Q2(:, kept) are
+// cuBLAS BLAS-2/3 calls: the products are plain GEMMs, the step's largest cost
+// for m, n >> k.  The mixed form follows each step with one Newton-Schulz step
+// on Q1 and P1 (as the full mixed form does for Q and P).
 // ---------------------------------------------------------------------------
 struct bdu_thin_ctx {
   int64_t m, n, k;
+  bool mixed = false;
   bdu_ctx *core = nullptr;
-  double *Qb = nullptr, *Pb = nullptr, *Qn = nullptr, *Pn = nullptr;
-  double *x = nullptr, *y = nullptr, *r = nullptr, *zq = nullptr, *zp = nullptr;
-  double *h1 = nullptr, *h2 = nullptr, *u = nullptr, *v = nullptr, *ones = nullptr, *K2 = nullptr;
+  void *Qb = nullptr, *Pb = nullptr, *Qn = nullptr, *Pn = nullptr;  // m x (k+1), n x (k+1)
+  void *x = nullptr, *y = nullptr, *r = nullptr, *zq = nullptr, *zp = nullptr;
+  void *h1 = nullptr, *h2 = nullptr, *wq = nullptr, *wp = nullptr, *ones = nullptr, *K2 = nullptr;
+  double *u = nullptr, *v = nullptr, *xd = nullptr;  // FP64 middle-matrix vectors; FP64 staging (mixed)
+  float *E = nullptr, *W = nullptr;                  // re-orthogonalization workspace (mixed)
   std::vector<double> d, e;
   double delta_host[2] = {0.0, 0.0};
   int64_t updates = 0, in_span_b = 0, in_span_c = 0;
@@ -1857,7 +1864,8 @@ struct bdu_thin_ctx {
 
 namespace {
 
-constexpr double kThinTau = 0x1p-40;                  // b in span(Q1) when ||b_perp|| <= kThinTau ||b||
+constexpr double kThinTau64 = 0x1p-40;                // b in span(Q1) when ||b_perp|| <= tau ||b||
+constexpr double kThinTau32 = 0x1p-16;                // the same for FP32 factors
 constexpr double kGolden = 0.6180339887498949;        // FP64 nearest (sqrt(5) - 1) / 2
 
 struct ThinGuard {
@@ -1872,18 +1880,65 @@ struct ThinGuard {
   }
 };
 
+// cuBLAS by element type
+inline cublasStatus_t bl_gemv(cublasHandle_t h, cublasOperation_t op, int m, int n, const double *a,
+                              const double *A, int lda, const double *x, const double *b, double *y) {
+  return cublasDgemv(h, op, m, n, a, A, lda, x, 1, b, y, 1);
+}
+inline cublasStatus_t bl_gemv(cublasHandle_t h, cublasOperation_t op, int m, int n, const float *a, const float *A,
+                              int lda, const float *x, const float *b, float *y) {
+  return cublasSgemv(h, op, m, n, a, A, lda, x, 1, b, y, 1);
+}
+inline cublasStatus_t bl_copy(cublasHandle_t h, int n, const double *x, int incx, double *y, int incy) {
+  return cublasDcopy(h, n, x, incx, y, incy);
+}
+inline cublasStatus_t bl_copy(cublasHandle_t h, int n, const float *x, int incx, float *y, int incy) {
+  return cublasScopy(h, n, x, incx, y, incy);
+}
+inline cublasStatus_t bl_axpy(cublasHandle_t h, int n, const double *a, const double *x, double *y) {
+  return cublasDaxpy(h, n, a, x, 1, y, 1);
+}
+inline cublasStatus_t bl_axpy(cublasHandle_t h, int n, const float *a, const float *x, float *y) {
+  return cublasSaxpy(h, n, a, x, 1, y, 1);
+}
+inline cublasStatus_t bl_nrm2(cublasHandle_t h, int n, const double *x, double *out) {
+  return cublasDnrm2(h, n, x, 1, out);
+}
+inline cublasStatus_t bl_nrm2(cublasHandle_t h, int n, const float *x, double *out) {
+  float f = 0.0f;
+  const cublasStatus_t st = cublasSnrm2(h, n, x, 1, &f);
+  *out = f;
+  return st;
+}
+inline cublasStatus_t bl_scal(cublasHandle_t h, int n, double a, double *x) { return cublasDscal(h, n, &a, x, 1); }
+inline cublasStatus_t bl_scal(cublasHandle_t h, int n, double a, float *x) {
+  const float f = (float)a;
+  return cublasSscal(h, n, &f, x, 1);
+}
+inline cublasStatus_t bl_gemm(cublasHandle_t h, int m, int n, int k, const double *A, int lda, const double *B,
+                              int ldb, double *C, int ldc) {
+  const double one = 1.0, zero = 0.0;
+  return cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+}
+inline cublasStatus_t bl_gemm(cublasHandle_t h, int m, int n, int k, const float *A, int lda, const float *B, int ldb,
+                              float *C, int ldc) {
+  const float one = 1.0f, zero = 0.0f;
+  return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
+}
+
 // The middle matrix's factorization starts from Q = P = I and Bd = [B 0; 0 0]
 // (beta_k = 0 between B and the zero block).
+template <typename T>
 bdu_status thin_reset_core(bdu_thin_ctx *t) {
   bdu_ctx *h = t->core;
   const int64_t N = t->k + 1;
   cudaStream_t s = h->stream;
   cublasHandle_t cb = (cublasHandle_t)h->cublas;
-  cudaError_t ce = cudaMemsetAsync(h->Q, 0, sizeof(double) * N * N, s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->P, 0, sizeof(double) * N * N, s);
+  cudaError_t ce = cudaMemsetAsync(h->Q, 0, sizeof(T) * N * N, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->P, 0, sizeof(T) * N * N, s);
   if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: resetting the middle factors");
-  if (cublasDcopy(cb, (int)N, t->ones, 1, (double *)h->Q, (int)N + 1) != CUBLAS_STATUS_SUCCESS ||
-      cublasDcopy(cb, (int)N, t->ones, 1, (double *)h->P, (int)N + 1) != CUBLAS_STATUS_SUCCESS)
+  if (bl_copy(cb, (int)N, (const T *)t->ones, 1, (T *)h->Q, (int)N + 1) != CUBLAS_STATUS_SUCCESS ||
+      bl_copy(cb, (int)N, (const T *)t->ones, 1, (T *)h->P, (int)N + 1) != CUBLAS_STATUS_SUCCESS)
     return fail(h, BDU_ECUDA, "rank-k step: cuBLAS copy failed");
   std::vector<double> hb(band_doubles(N, N), 0.0);
   BandPtrs hp = band_ptrs(hb.data(), N, N);
@@ -1897,56 +1952,61 @@ bdu_status thin_reset_core(bdu_thin_ctx *t) {
 }
 
 // Eq. defup and Eq. qrlr for one side: w[0:k] = X^T b (two Gram-Schmidt
-// passes, accumulated), the remainder's norm delta into w[k], and the unit
-// remainder into column k of X (len x (k+1)); when b lies in span(X) the
-// fixed fill vector is orthogonalized instead and delta = 0.
-bdu_status thin_side(bdu_thin_ctx *t, double *X, int64_t len, const double *b, const double *fill, double *w,
-                     int which, bool *in_span) {
+// passes, accumulated), the remainder's norm delta into u[k] (FP64, with
+// u[0:k] = w), and the unit remainder into column k of X (len x (k+1)); when
+// b lies in span(X) the fixed fill vector is orthogonalized instead and
+// delta = 0.
+template <typename T>
+bdu_status thin_side(bdu_thin_ctx *t, T *X, int64_t len, const T *b, const T *fill, T *w, double *u, int which,
+                     bool *in_span) {
   bdu_ctx *h = t->core;
   cublasHandle_t cb = (cublasHandle_t)h->cublas;
   const int L = (int)len, k = (int)t->k;
-  const double one = 1.0, zero = 0.0, mone = -1.0;
+  const T one = 1, zero = 0, mone = -1;
+  T *r = (T *)t->r, *h1 = (T *)t->h1;
   auto ok = [](cublasStatus_t st) { return st == CUBLAS_STATUS_SUCCESS; };
-  auto cgs2 = [&](const double *src, double *proj) {
-    return ok(cublasDgemv(cb, CUBLAS_OP_T, L, k, &one, X, L, src, 1, &zero, t->h1, 1)) &&
-           ok(cublasDcopy(cb, L, src, 1, t->r, 1)) &&
-           ok(cublasDgemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, t->h1, 1, &one, t->r, 1)) &&
-           ok(cublasDgemv(cb, CUBLAS_OP_T, L, k, &one, X, L, t->r, 1, &zero, proj, 1)) &&
-           ok(cublasDgemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, proj, 1, &one, t->r, 1)) &&
-           ok(cublasDaxpy(cb, k, &one, t->h1, 1, proj, 1));
+  auto cgs2 = [&](const T *src, T *proj) {
+    return ok(bl_gemv(cb, CUBLAS_OP_T, L, k, &one, X, L, src, &zero, h1)) && ok(bl_copy(cb, L, src, 1, r, 1)) &&
+           ok(bl_gemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, h1, &one, r)) &&
+           ok(bl_gemv(cb, CUBLAS_OP_T, L, k, &one, X, L, r, &zero, proj)) &&
+           ok(bl_gemv(cb, CUBLAS_OP_N, L, k, &mone, X, L, proj, &one, r)) && ok(bl_axpy(cb, k, &one, h1, proj));
   };
   double nb = 0.0, dl = 0.0;
-  if (!cgs2(b, w) || !ok(cublasDnrm2(cb, L, b, 1, &nb)) || !ok(cublasDnrm2(cb, L, t->r, 1, &dl)))
+  if (!cgs2(b, w) || !ok(bl_nrm2(cb, L, b, &nb)) || !ok(bl_nrm2(cb, L, r, &dl)))
     return fail(h, BDU_ECUDA, "rank-k step: cuBLAS projection failed");
-  double *col = X + (size_t)k * len;
-  *in_span = !(dl > kThinTau * nb);
+  T *col = X + (size_t)k * len;
+  *in_span = !(dl > (sizeof(T) == 8 ? kThinTau64 : kThinTau32) * nb);
   double scale_norm = dl;
   if (*in_span) {
     dl = 0.0;
-    if (!cgs2(fill, t->h2) || !ok(cublasDnrm2(cb, L, t->r, 1, &scale_norm)))
+    if (!cgs2(fill, (T *)t->h2) || !ok(bl_nrm2(cb, L, r, &scale_norm)))
       return fail(h, BDU_ECUDA, "rank-k step: cuBLAS projection failed");
     if (!(scale_norm > 0.0)) return fail(h, BDU_EINTERNAL, "rank-k step: no direction left outside the subspace");
   }
-  const double inv = 1.0 / scale_norm;
-  if (!ok(cublasDcopy(cb, L, t->r, 1, col, 1)) || !ok(cublasDscal(cb, L, &inv, col, 1)))
+  if (!ok(bl_copy(cb, L, r, 1, col, 1)) || !ok(bl_scal(cb, L, 1.0 / scale_norm, col)))
     return fail(h, BDU_ECUDA, "rank-k step: cuBLAS scaling failed");
+  cudaError_t ce = cudaSuccess;
+  if (sizeof(T) == 4) ce = launch_convert_f32_to_f64((const float *)w, u, k, h->stream);
   t->delta_host[which] = dl;
-  cudaError_t ce = cudaMemcpyAsync(w + k, &t->delta_host[which], sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(u + k, &t->delta_host[which], sizeof(double), cudaMemcpyHostToDevice, h->stream);
   return ce == cudaSuccess ? BDU_OK : cuda_fail(h, ce, "rank-k step: staging delta");
 }
 
+template <typename T>
 bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
   bdu_ctx *h = t->core;
   const int64_t m = t->m, n = t->n, k = t->k, N = k + 1;
   cudaStream_t s = h->stream;
   cublasHandle_t cb = (cublasHandle_t)h->cublas;
-  if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS || cublasSetPointerMode(cb, CUBLAS_POINTER_MODE_HOST) != CUBLAS_STATUS_SUCCESS ||
+  if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetPointerMode(cb, CUBLAS_POINTER_MODE_HOST) != CUBLAS_STATUS_SUCCESS ||
       cublasSetMathMode(cb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS)
     return fail(h, BDU_ECUDA, "rank-k step: cuBLAS set-up failed");
   bool sb = false, sc = false;
-  bdu_status st = thin_side(t, t->Qb, m, t->x, t->zq, t->u, 0, &sb);
-  if (st == BDU_OK) st = thin_side(t, t->Pb, n, t->y, t->zp, t->v, 1, &sc);
-  if (st == BDU_OK) st = thin_reset_core(t);
+  bdu_status st = thin_side<T>(t, (T *)t->Qb, m, (const T *)t->x, (const T *)t->zq, (T *)t->wq, t->u, 0, &sb);
+  if (st == BDU_OK) st = thin_side<T>(t, (T *)t->Pb, n, (const T *)t->y, (const T *)t->zp, (T *)t->wp, t->v, 1, &sc);
+  if (st == BDU_OK) st = thin_reset_core<T>(t);
   if (st != BDU_OK) return st;
   // Algorithm 2 on the middle matrix (Eq. equivlrup): u = I^T u, v = I^T v exactly
   st = bdu_update_dev(h, t->u, t->v, 1);
@@ -1981,22 +2041,26 @@ bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
     err = err + t3;
   }
   // [X, column] X2(:, kept) for X2 = Q2, P2 (Eq. bdlrup), into the spare buffer
-  const double one = 1.0, zero = 0.0;
+  T *K2 = (T *)t->K2;
   for (int side = 0; side < 2; side++) {
-    const double *X2 = (const double *)(side == 0 ? h->Q : h->P);
-    if (drop > 0) ce = cudaMemcpyAsync(t->K2, X2, sizeof(double) * N * drop, cudaMemcpyDeviceToDevice, s);
+    const T *X2 = (const T *)(side == 0 ? h->Q : h->P);
+    if (drop > 0) ce = cudaMemcpyAsync(K2, X2, sizeof(T) * N * drop, cudaMemcpyDeviceToDevice, s);
     if (ce == cudaSuccess && drop < k)
-      ce = cudaMemcpyAsync(t->K2 + N * drop, X2 + N * (drop + 1), sizeof(double) * N * (k - drop),
-                           cudaMemcpyDeviceToDevice, s);
+      ce = cudaMemcpyAsync(K2 + N * drop, X2 + N * (drop + 1), sizeof(T) * N * (k - drop), cudaMemcpyDeviceToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: gathering the kept columns");
     const int64_t len = side == 0 ? m : n;
-    double *Xb = side == 0 ? t->Qb : t->Pb, *Xn = side == 0 ? t->Qn : t->Pn;
-    if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)len, (int)k, (int)N, &one, Xb, (int)len, t->K2, (int)N, &zero,
-                    Xn, (int)len) != CUBLAS_STATUS_SUCCESS)
+    T *Xb = (T *)(side == 0 ? t->Qb : t->Pb), *Xn = (T *)(side == 0 ? t->Qn : t->Pn);
+    if (bl_gemm(cb, (int)len, (int)k, (int)N, Xb, (int)len, K2, (int)N, Xn, (int)len) != CUBLAS_STATUS_SUCCESS)
       return fail(h, BDU_ECUDA, "rank-k step: cuBLAS GEMM failed");
   }
   std::swap(t->Qb, t->Qn);
   std::swap(t->Pb, t->Pn);
+  if (sizeof(T) == 4) {
+    // FP32 factors: one Newton-Schulz step each, X <- X - X (X^T X - I) / 2
+    ce = launch_reorth32((float *)t->Qb, m, (int)k, t->E, t->W, h->cublas, s);
+    if (ce == cudaSuccess) ce = launch_reorth32((float *)t->Pb, n, (int)k, t->E, t->W, h->cublas, s);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: re-orthogonalization");
+  }
   // B+ = Bbar+(kept, kept): the superdiagonal entry across the removed index is zero
   std::vector<double> dn, en;
   for (int64_t i = 0; i < N; i++)
@@ -2018,7 +2082,20 @@ bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
   return ce == cudaSuccess ? BDU_OK : cuda_fail(h, ce, "rank-k step");
 }
 
+template <typename T>
+void thin_fill_host(std::vector<T> &z, std::vector<T> &ones, int64_t L, int64_t N) {
+  // the fill vector z_i = frac(i * golden) - 0.5 (each step one IEEE operation)
+  z.resize(L);
+  for (int64_t i = 0; i < L; i++) {
+    const double a = (double)i * kGolden;
+    z[i] = (T)((a - floor(a)) - 0.5);
+  }
+  ones.assign(N, (T)1);
+}
+
 }  // namespace
+
+extern "C" {
 
 bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k, const double *Q1, const double *d,
                            const double *e, const double *P1, const bdu_options *opt) {
@@ -2033,13 +2110,20 @@ bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k
   bdu_options o;
   bdu_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != BDU_FP64) return fail(nullptr, BDU_EINVAL, "bdu_thin_create: rank-k tracking is FP64 only");
+  if (o.precision != BDU_FP64 && o.precision != BDU_MIXED)
+    return fail(nullptr, BDU_EINVAL, "bdu_thin_create: unknown precision %d", o.precision);
+  // the middle matrix's factors start from the identity at every step: no
+  // overlap, no checks or re-orthogonalization of them
   o.overlap = 0;
+  o.reorth_every = 0;
+  o.reorth_tol = 0.0;
+  o.check_every = 0;
   if (!all_finite(Q1, m * k) || !all_finite(P1, n * k) || !all_finite(d, k) || (k > 1 && !all_finite(e, k - 1)))
     return fail(nullptr, BDU_EINVAL, "bdu_thin_create: non-finite value in Q1, d, e or P1");
   bdu_thin_ctx *t = new (std::nothrow) bdu_thin_ctx();
   if (!t) return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: host allocation failed");
   t->m = m; t->n = n; t->k = k;
+  t->mixed = o.precision == BDU_MIXED;
   t->d.assign(d, d + k);
   t->e.assign(k > 1 ? e : d, k > 1 ? e + (k - 1) : d);
   const int64_t N = k + 1;
@@ -2060,40 +2144,63 @@ bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k
     return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: cublasCreate failed");
   }
   h->cublas = hb;
+  const size_t es = t->mixed ? sizeof(float) : sizeof(double);
   const int64_t L = m > n ? m : n;
-  t->Qb = (double *)dev_alloc(h, sizeof(double) * m * N);
-  t->Qn = (double *)dev_alloc(h, sizeof(double) * m * N);
-  t->Pb = (double *)dev_alloc(h, sizeof(double) * n * N);
-  t->Pn = (double *)dev_alloc(h, sizeof(double) * n * N);
-  t->x = (double *)dev_alloc(h, sizeof(double) * m);
-  t->y = (double *)dev_alloc(h, sizeof(double) * n);
-  t->r = (double *)dev_alloc(h, sizeof(double) * L);
-  t->zq = (double *)dev_alloc(h, sizeof(double) * m);
-  t->zp = (double *)dev_alloc(h, sizeof(double) * n);
-  t->h1 = (double *)dev_alloc(h, sizeof(double) * N);
-  t->h2 = (double *)dev_alloc(h, sizeof(double) * N);
+  t->Qb = dev_alloc(h, es * m * N);
+  t->Qn = dev_alloc(h, es * m * N);
+  t->Pb = dev_alloc(h, es * n * N);
+  t->Pn = dev_alloc(h, es * n * N);
+  t->x = dev_alloc(h, es * m);
+  t->y = dev_alloc(h, es * n);
+  t->r = dev_alloc(h, es * L);
+  t->zq = dev_alloc(h, es * m);
+  t->zp = dev_alloc(h, es * n);
+  t->h1 = dev_alloc(h, es * N);
+  t->h2 = dev_alloc(h, es * N);
+  t->ones = dev_alloc(h, es * N);
+  t->K2 = dev_alloc(h, es * N * k);
   t->u = (double *)dev_alloc(h, sizeof(double) * N);
   t->v = (double *)dev_alloc(h, sizeof(double) * N);
-  t->ones = (double *)dev_alloc(h, sizeof(double) * N);
-  t->K2 = (double *)dev_alloc(h, sizeof(double) * N * k);
-  if (!t->Qb || !t->Qn || !t->Pb || !t->Pn || !t->x || !t->y || !t->r || !t->zq || !t->zp || !t->h1 || !t->h2 ||
-      !t->u || !t->v || !t->ones || !t->K2) {
+  bool ok = t->Qb && t->Qn && t->Pb && t->Pn && t->x && t->y && t->r && t->zq && t->zp && t->h1 && t->h2 &&
+            t->ones && t->K2 && t->u && t->v;
+  if (t->mixed) {
+    t->wq = dev_alloc(h, es * N);
+    t->wp = dev_alloc(h, es * N);
+    t->xd = (double *)dev_alloc(h, sizeof(double) * (L * k > m + n ? L * k : m + n));  // b and c, or a factor
+    t->E = (float *)dev_alloc(h, sizeof(float) * k * k);
+    t->W = (float *)dev_alloc(h, sizeof(float) * L * k);
+    ok = ok && t->wq && t->wp && t->xd && t->E && t->W;
+  } else {
+    t->wq = t->u;
+    t->wp = t->v;
+  }
+  if (!ok) {
     bdu_destroy(h);
     delete t;
     return fail(nullptr, BDU_ENOMEM, "bdu_thin_create: device allocation failed");
   }
-  // the fill vector z_i = frac(i * golden) - 0.5 (each step one IEEE operation)
-  std::vector<double> z(L), ones(N, 1.0);
-  for (int64_t i = 0; i < L; i++) {
-    const double a = (double)i * kGolden;
-    z[i] = (a - floor(a)) - 0.5;
-  }
   cudaStream_t s = h->stream;
-  cudaError_t ce = cudaMemcpyAsync(t->Qb, Q1, sizeof(double) * m * k, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->Pb, P1, sizeof(double) * n * k, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zq, z.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zp, z.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->ones, ones.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s);
+  cudaError_t ce = cudaSuccess;
+  std::vector<double> zd, od;
+  std::vector<float> zf, of;
+  if (t->mixed) {
+    thin_fill_host<float>(zf, of, L, N);
+    ce = cudaMemcpyAsync(t->xd, Q1, sizeof(double) * m * k, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(t->xd, (float *)t->Qb, m * k, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->xd, P1, sizeof(double) * n * k, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(t->xd, (float *)t->Pb, n * k, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zq, zf.data(), es * m, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zp, zf.data(), es * n, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->ones, of.data(), es * N, cudaMemcpyHostToDevice, s);
+  } else {
+    thin_fill_host<double>(zd, od, L, N);
+    ce = cudaMemcpyAsync(t->Qb, Q1, sizeof(double) * m * k, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->Pb, P1, sizeof(double) * n * k, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zq, zd.data(), es * m, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->zp, zd.data(), es * n, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->ones, od.data(), es * N, cudaMemcpyHostToDevice, s);
+  }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) {
     fail(nullptr, BDU_ECUDA, "bdu_thin_create: %s", cudaGetErrorString(ce));
@@ -2117,10 +2224,18 @@ static bdu_status thin_update_common(bdu_thin_handle t, const double *b, const d
   cudaError_t ce = cudaSetDevice(h->device);
   cudaStream_t s = h->stream;
   const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->x, b, sizeof(double) * t->m, kind, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->y, c, sizeof(double) * t->n, kind, s);
+  if (!t->mixed) {
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->x, b, sizeof(double) * t->m, kind, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->y, c, sizeof(double) * t->n, kind, s);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: staging b, c");
+    return thin_step<double>(t, dropped, err2);
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->xd, b, sizeof(double) * t->m, kind, s);
+  if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(t->xd, (float *)t->x, t->m, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->xd + t->m, c, sizeof(double) * t->n, kind, s);
+  if (ce == cudaSuccess) ce = launch_convert_f64_to_f32(t->xd + t->m, (float *)t->y, t->n, s);
   if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: staging b, c");
-  return thin_step(t, dropped, err2);
+  return thin_step<float>(t, dropped, err2);
 }
 
 bdu_status bdu_thin_update(bdu_thin_handle t, const double *b, const double *c, int64_t *dropped, double *err2) {
@@ -2140,9 +2255,19 @@ bdu_status bdu_thin_read(bdu_thin_handle t, double *Q1, double *d, double *e, do
   cudaSetDevice(h->device);
   cudaStream_t s = h->stream;
   cudaError_t ce = cudaSuccess;
-  if (Q1) ce = cudaMemcpyAsync(Q1, t->Qb, sizeof(double) * t->m * t->k, cudaMemcpyDeviceToHost, s);
-  if (P1 && ce == cudaSuccess) ce = cudaMemcpyAsync(P1, t->Pb, sizeof(double) * t->n * t->k, cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  for (int side = 0; side < 2 && ce == cudaSuccess; side++) {
+    double *dst = side == 0 ? Q1 : P1;
+    if (!dst) continue;
+    const int64_t cnt = (side == 0 ? t->m : t->n) * t->k;
+    const void *src = side == 0 ? t->Qb : t->Pb;
+    if (t->mixed) {
+      ce = launch_convert_f32_to_f64((const float *)src, t->xd, cnt, s);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(dst, t->xd, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s);
+    } else {
+      ce = cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  }
   if (ce != cudaSuccess) return cuda_fail(h, ce, "bdu_thin_read");
   if (d) std::copy(t->d.begin(), t->d.end(), d);
   if (e) std::copy(t->e.begin(), t->e.end(), e);

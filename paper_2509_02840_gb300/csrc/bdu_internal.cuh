@@ -160,7 +160,7 @@ cudaError_t launch_stage_batch(const ChaseArgs *d_items, const double *const *d_
 cudaError_t launch_ortho_probe(int precision, const void *X, int k, double *ws, int iters, cudaStream_t s);
 // One Newton-Schulz step with FP32 products and an FP64 diagonal of X^T X
 // (E, W: k*k floats of workspace).
-cudaError_t launch_reorth32(float *X, int k, float *E, float *W, void *cublas_handle, cudaStream_t s);
+cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, void *cublas_handle, cudaStream_t s);
 cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, void *cublas_handle,
                           cudaStream_t s);
 

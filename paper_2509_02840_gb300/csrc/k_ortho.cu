@@ -80,13 +80,13 @@ __global__ void k_minus_identity(double *__restrict__ E, int64_t ld, int k) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) E[(size_t)i * ld + i] -= 1.0;
 }
 
-// E(i, i) = sum_r X(r, i)^2 - 1 in FP64 (one warp per column)
-__global__ void k_diag_gram(const float *__restrict__ X, int k, float *__restrict__ E) {
+// E(i, i) = sum_r X(r, i)^2 - 1 in FP64 (X rows x k, one warp per column)
+__global__ void k_diag_gram(const float *__restrict__ X, int64_t rows, int k, float *__restrict__ E) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= k) return;
-  const float *col = X + (size_t)warp * k;
+  const float *col = X + (size_t)warp * rows;
   double s = 0.0;
-  for (int i = lane; i < k; i += 32) {
+  for (int64_t i = lane; i < rows; i += 32) {
     const double v = (double)col[i];
     s = fma(v, v, s);
   }
@@ -156,19 +156,23 @@ cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, voi
   return cudaGetLastError();
 }
 
-// One Newton-Schulz step on X (k x k, FP32), E and W: k*k floats of workspace.
-cudaError_t launch_reorth32(float *X, int k, float *E, float *W, void *cublas_handle, cudaStream_t s) {
+// One Newton-Schulz step on X (rows x k, FP32, leading dimension rows; a
+// square factor or the thin factor of rank-k tracking), E: k*k and W: rows*k
+// floats of workspace.
+cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, void *cublas_handle,
+                            cudaStream_t s) {
   cublasHandle_t hb = (cublasHandle_t)cublas_handle;
   if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
   if (cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
   const float one = 1.0f, zero = 0.0f;
+  const int r = (int)rows;
   // E = X^T X (FP32; its diagonal is replaced by the FP64 one minus 1)
-  if (cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, k, k, &one, X, k, X, k, &zero, E, k) != CUBLAS_STATUS_SUCCESS)
+  if (cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, k, r, &one, X, r, X, r, &zero, E, k) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
-  k_diag_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(X, k, E);
-  if (cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, X, k, E, k, &zero, W, k) != CUBLAS_STATUS_SUCCESS)
+  k_diag_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(X, rows, k, E);
+  if (cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, r, k, k, &one, X, r, E, k, &zero, W, r) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
-  k_finish_reorth32<<<1216, 256, 0, s>>>(W, X, (int64_t)k * k);
+  k_finish_reorth32<<<1216, 256, 0, s>>>(W, X, rows * k);
   return cudaGetLastError();
 }
 
