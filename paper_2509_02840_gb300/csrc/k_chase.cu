@@ -974,7 +974,10 @@ cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (a.engine != 1 && (a.engine == 2 || n >= 512)) {
+  // by size: one CTA up to the measured crossover (n = 512: 17.2 vs 20.0 ms
+  // per mixed column, 26.2 vs 28.0 FP64; n = 1024: 42.9 vs 40.9, 69.4 vs 56.9)
+  const int cluster_from = FAST ? 896 : 640;
+  if (a.engine != 1 && (a.engine == 2 || n >= cluster_from)) {
     // cluster engine
     const int CS = kMaxCluster;
     const size_t dyn = 0;
