@@ -144,6 +144,23 @@ def workload(rank, steps):
     return Q, d, e, P, ups
 
 
+def slowest_rank_ms(ms, dist, device):
+    """The timed region of the whole job: the largest of every rank's (the job
+    ends with its slowest replica).  dist is torch.distributed or None."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms):
+    """Whole-job units per second: the units every rank processed over the
+    slowest rank's time (the replicas are independent: weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -342,10 +359,7 @@ def run_gpu(args):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest_rank_ms(total_ms, dist, "cuda")
     st = Fm.stats()
     rot_per_update = (sum(st["rot_left"]) + sum(st["rot_right"]) - sum(st0["rot_left"]) - sum(st0["rot_right"])) / K
     launches = (st["launches"] - st0["launches"])
@@ -358,7 +372,7 @@ def run_gpu(args):
 
     if args.quick:
         Fm.close()
-        line = {"metric": METRIC, "value": world * K / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": job_throughput(world, K, total_ms), "unit": UNIT, "n_gpus": world,
                 "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": f"recommender stream m=n={M} (quick profiling run)", "m": M, "n": N},
@@ -399,7 +413,7 @@ def run_gpu(args):
 
     if dist:
         dist.barrier()
-    value = world * K / (total_ms / 1e3)
+    value = job_throughput(world, K, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
