@@ -94,7 +94,7 @@ typedef struct {
                          before that application and rotated by its rotations (the same
                          quantity, rounded differently; Sec. 3.2).  Doubles the memory
                          of the rotation records.  0 = off (default); ignored in the
-                         FP64 form and when max(m, n) exceeds about 50000. */
+                         FP64 form and when max(m, n) exceeds about 39000. */
   int graphs;         /* 1 = capture the launch sequence of an update (projection, the
                          chase and the applications of each rank-1 column) in a CUDA
                          graph the first time a rank and pair of input buffers are seen,

@@ -10,7 +10,7 @@
 // two entries of one row of Q.  This lets the application of column j-1 to Q
 // and P run concurrently with the chase of column j.
 //
-// One block per side; the vector sits in shared memory.  The spike chain
+// One block per vector; the vector sits in shared memory.  The spike chain
 // (left side, m > n) is sequential: its records are staged in shared memory a
 // chunk at a time and one thread runs through them.  The chases' rotations
 // then come as the FP32 coefficients the apply uses and the per-chase
@@ -18,7 +18,9 @@
 // records and streams them into a ring of shared-memory slots with bulk copies
 // (full/empty mbarriers, bounded waits), so that many copies are in flight at
 // once; the compute threads apply a chunk's rotations, which act on disjoint
-// pairs, all at once, and meet at a barrier only where a chase ends.  A pair's
+// pairs, all at once (kPerThread each), and meet at a barrier only where a
+// chase ends.  A chunk holds a whole chase of up to kRecs records, so the
+// barriers, not the data, set the pace: about one per chase.  A pair's
 // first column comes from the chase's progression (first + step * index), or
 // from the recorded positions for a chase with a gap.
 //
@@ -35,7 +37,8 @@ namespace {
 
 constexpr int kCompute = 512;            // compute threads
 constexpr int kThreads = kCompute + 32;  // + the producer warp
-constexpr int kRecs = 512;               // records per chunk
+constexpr int kRecs = 2048;              // records per chunk (a chase holds at most n/2 + 4)
+constexpr int kPerThread = kRecs / kCompute;
 constexpr int kSpike = 512;              // spike records staged at a time
 constexpr size_t kSmemBudget = 220 * 1024;
 constexpr size_t kSlot = 16 + (kRecs + 2) * 8;  // header + coefficients (from a 16-byte boundary)
@@ -74,10 +77,11 @@ struct RvLayout {
 };
 
 // Chunk header: x = index within its chase of the chunk's first record;
-// y = count | last << 10 | gap << 11 | shift << 12 | stop << 13;
+// y = count | last << 12 | gap << 13 | shift << 14 | stop << 15;
 // z = first column of the chase's first pair; w = step, or for a chase with a
 // gap the index of its first record in the record arrays.
-constexpr int kLast = 1 << 10, kGap = 1 << 11, kShift = 1 << 12, kStop = 1 << 13;
+constexpr int kCountMask = (1 << 12) - 1, kLast = 1 << 12, kGap = 1 << 13, kShift = 1 << 14, kStop = 1 << 15;
+static_assert(kRecs <= kCountMask && kRecs % kCompute == 0, "chunk layout");
 
 // Blocks 0 .. nl-1: vector b of w_left (m entries, stride ldl) by the left
 // stream into the same place of dst_left; blocks nl .. nl+nr-1: vector b-nl of
@@ -190,15 +194,37 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
     const unsigned char *slot = raw + L.ring + (size_t)s * kSlot;
     const int4 hd = *reinterpret_cast<const int4 *>(slot);
     if (hd.y & kStop) break;
-    const int k = hd.y & 1023;
+    const int k = min(hd.y & kCountMask, kRecs);
     const float2 *cf = reinterpret_cast<const float2 *>(slot + 16) + ((hd.y & kShift) ? 1 : 0);
-    if (tid < k) {
-      const int ri = hd.x + tid;  // index of the record within its chase
-      const int a = (hd.y & kGap) ? Ca[(size_t)hd.w + ri] - 1 : hd.z + hd.w * ri;
-      const float2 g = cf[tid];
-      if (a >= 0 && a + 1 < len) rot32(g.x, g.y, v[a], v[a + 1]);
-      else atomicOr(status, ERR_RANGE);
+    // records tid, tid + kCompute, ... of the chunk: disjoint pairs of one
+    // chase, so all are loaded before any is stored
+    int a4[kPerThread];
+    float2 g4[kPerThread];
+    float x4[kPerThread], y4[kPerThread];
+#pragma unroll
+    for (int u = 0; u < kPerThread; u++) {
+      const int j = tid + u * kCompute;
+      a4[u] = -1;
+      if (j < k) {
+        const int ri = hd.x + j;  // index of the record within its chase
+        const int a = (hd.y & kGap) ? Ca[(size_t)hd.w + ri] - 1 : hd.z + hd.w * ri;
+        if (a >= 0 && a + 1 < len) {
+          a4[u] = a;
+          g4[u] = cf[j];
+          x4[u] = v[a];
+          y4[u] = v[a + 1];
+        } else {
+          atomicOr(status, ERR_RANGE);
+        }
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kPerThread; u++)
+      if (a4[u] >= 0) {
+        rot32(g4[u].x, g4[u].y, x4[u], y4[u]);
+        v[a4[u]] = x4[u];
+        v[a4[u] + 1] = y4[u];
+      }
     if (hd.y & kLast) async::named_sync(1, kCompute);  // the chase done by all: its values visible
     __syncwarp();
     if ((tid & 31) == 0) async::mbar_arrive(&empty[s]);
