@@ -69,3 +69,39 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.bdu_read(None, None, None, None, None) == 1
     lib.bdu_destroy(None)  # accepted
     assert lib.bdu_last_error(None) is not None
+
+
+def test_thin_create_rejects_bad_arguments_without_a_gpu(lib):
+    dp = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    m, n = 12, 9
+    Q1 = np.zeros((m, 3), order="F"); P1 = np.zeros((n, 3), order="F")
+    d = np.ones(3); e = np.ones(2)
+
+    def create(m_, n_, k_, q, dd, ee, p, precision=None):
+        h = ctypes.c_void_p()
+        o = None
+        if precision is not None:
+            o = bdu.Options()
+            lib.bdu_default_options(ctypes.byref(o))
+            o.precision = precision
+        code = lib.bdu_thin_create(ctypes.byref(h), m_, n_, k_, dp(q), dp(dd), dp(ee), dp(p),
+                                   None if o is None else ctypes.byref(o))
+        return code, h
+
+    for k in (0, 9, 12):  # k must satisfy 1 <= k < min(m, n)
+        code, h = create(m, n, k, Q1, d, e, P1)
+        assert code == 1 and not h.value
+    assert b"min(m, n)" in lib.bdu_thin_last_error(None)
+    assert create(m, n, 3, None, d, e, P1)[0] == 1          # NULL Q1
+    assert create(m, n, 3, Q1, d, None, P1)[0] == 1         # NULL e with k > 1
+    assert create(m, n, 3, Q1, d, e, P1, precision=5)[0] == 1
+    bad = Q1.copy(); bad[0, 0] = np.inf
+    assert create(m, n, 3, bad, d, e, P1)[0] == 1
+    assert b"non-finite" in lib.bdu_thin_last_error(None)
+
+
+def test_thin_null_handle_calls_are_rejected(lib):
+    assert lib.bdu_thin_update(None, None, None, None, None) == 1
+    assert lib.bdu_thin_read(None, None, None, None, None) == 1
+    assert lib.bdu_thin_stats(None, None, None, None) == 1
+    lib.bdu_thin_destroy(None)  # accepted
