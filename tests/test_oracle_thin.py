@@ -86,3 +86,18 @@ def test_fill_vector_is_orthogonalizable():
     z = O.fill_vector(1000)
     assert np.all(np.abs(z) <= 0.5) and abs(z.mean()) < 0.01
     assert z[0] == -0.5 and z[1] == O.GOLDEN - 0.5
+
+
+def test_hand_derived_rank_one_step():
+    """k = 1, m = n = 2, Q1 = P1 = e1, B = [alpha], b = beta e2, c = e1:
+    A+ = (alpha e1 + beta e2) e1^T has sigma = hypot(alpha, beta), so one
+    tracking step loses nothing and gives Q1+ = +-(alpha, beta) / sigma,
+    P1+ = +-e1 (c lies in span(P1): gamma = 0)."""
+    alpha, beta = 3.0, -4.0
+    Q1 = np.array([[1.0], [0.0]]); P1 = np.array([[1.0], [0.0]])
+    Q2, d2, e2, P2, i, err2 = O.thin_update(Q1, [alpha], [], P1, [0.0, beta], [1.0, 0.0])
+    assert abs(abs(d2[0]) - 5.0) <= 1e-15 * 5.0 and len(e2) == 0
+    assert err2 == 0.0 and i == 1
+    q = Q2[:, 0] * np.sign(Q2[0, 0])
+    np.testing.assert_allclose(q, [0.6, -0.8], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(np.abs(P2[:, 0]), [1.0, 0.0], rtol=0, atol=1e-15)
