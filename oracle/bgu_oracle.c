@@ -467,6 +467,13 @@ int orc_num_threads(void) {
 /* receives the column norms after convergence (unsorted).                   */
 /* ------------------------------------------------------------------------ */
 int orc_jacobi_sv(double *X, int rows, int cols, double *sv, int max_sweeps) {
+  /* A column whose squared norm falls below (rows eps)^2 ||X||_F^2 is
+   * numerically zero (X is rank deficient): it cannot be made orthogonal to
+   * the others beyond rounding, so its pairs count as converged.  The
+   * rotations preserve ||X||_F, so it is taken once. */
+  double fro2 = 0.0;
+  for (size_t i = 0; i < (size_t)rows * cols; i++) fro2 += X[i] * X[i];
+  const double null2 = (rows * 0x1p-52) * (rows * 0x1p-52) * fro2;
   for (int sweep = 0; sweep < max_sweeps; sweep++) {
     double off = 0.0;
     for (int p = 0; p < cols - 1; p++)
@@ -478,7 +485,7 @@ int orc_jacobi_sv(double *X, int rows, int cols, double *sv, int max_sweeps) {
           beta += xq[i] * xq[i];
           gamma += xp[i] * xq[i];
         }
-        if (gamma == 0.0) continue;
+        if (gamma == 0.0 || alpha <= null2 || beta <= null2) continue;
         double rel = fabs(gamma) / sqrt(alpha * beta);
         if (rel > off) off = rel;
         if (rel < 1e-15) continue;
