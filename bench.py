@@ -62,8 +62,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=100,
+                    help="updates of the end-to-end run (at least --steps); their wall times give the latency")
+    ap.add_argument("--serving-seconds", type=float, default=8.0,
+                    help="Poisson phase of the serving measurement per form (0 = no serving measurement)")
+    ap.add_argument("--serving-sessions", type=int, default=256)
     ap.add_argument("--oracle-rows", type=int, default=256,
                     help="rows of Q and P the CPU oracle applies in its bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -185,7 +189,7 @@ ALU_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # root, 2 divisions counted as one flop each).
 CHASE_FLOPS_PER_ROTATION = 26
 # DRAM bytes (read + write) of one mixed-form chase launch at m = n = 4096, from one
-# ncu capture (profiles/launches_recommender_4096.md): the rotation records written
+# ncu capture of this benchmark's launches: the rotation records written
 # (FP32 (c, s) and an int32 pair index per rotation, 12 B x 25.2M = 302 MB, part of
 # which is still in L2 when the launch ends).
 CHASE_TRAFFIC_4096 = 6.08e6 + 248.72e6
@@ -226,6 +230,53 @@ def roofline(st, precision, rotations_per_update, launches_per_update, steps_per
             "peak": ALU_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / ALU_FP64_TFLOPS, "traffic": None,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
             "share": ms["apply"] / sum(ms.values())}
+
+
+def latency_summary(samples, what):
+    """p50 and p99 when there are at least 100 samples; otherwise the median
+    and the maximum (a p99 of fewer samples would only be the maximum)."""
+    xs = sorted(samples)
+    out = {"samples": len(xs), "what": what, "p50": statistics.median(xs), "max": xs[-1]}
+    if len(xs) >= 100:
+        out["p99"] = xs[min(len(xs) - 1, int(round(0.99 * (len(xs) - 1))))]
+    return out
+
+
+def apply_roofline(st, rotations_per_update):
+    """The rotation apply (mixed form) against HBM: algorithmic bytes per
+    launch = one read and one write of the factor in FP32 plus one read of its
+    side's FP32 coefficient records (8 B per rotation), over the launch's
+    average device time (CUDA events around each launch)."""
+    launches = max(st["apply_launches"], 1)
+    per_launch_ms = (st["ms_apply_q"] + st["ms_apply_p"]) / launches
+    alg = 2 * M * M * 4 + 8 * rotations_per_update / 2
+    hbm = peaks().get("hbm_gbs")
+    ach = alg / (per_launch_ms * 1e-3) / 1e9
+    return {"kernel": "rotation apply to Q or P (mixed form, one rank-1 column per launch)", "bound": "hbm",
+            "algorithmic_bytes": alg, "ms_per_launch": per_launch_ms, "achieved": ach, "unit": "GB/s",
+            "peak": hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None,
+            "frac": ach / hbm if hbm else None,
+            "note": "timed beside the concurrent chase of the next update (overlapped form)"}
+
+
+def serving(args):
+    """A short run of the serving mix (256 resident factorizations, m, n
+    log-uniform in [64, 2048], rank 1..4 requests, a device budget of a third
+    of what all sessions need) in both forms: saturated updates/s, then p50/p99
+    latency under Poisson arrivals at 80 % of the saturated rate."""
+    from paper_2509_02840_gb300 import bdu, serve as S
+    out = {}
+    for form, prec in (("mixed", bdu.MIXED), ("fp64", bdu.FP64)):
+        r = S.serve(args.serving_sessions, args.serving_seconds, prec, sat_per_session=1)
+        out[form] = {"saturated_updates_per_s": r["saturated"]["updates_per_s"],
+                     "poisson_updates_per_s": r["poisson"]["updates_per_s"],
+                     "offered_requests_per_s": r["offered_requests_per_s"],
+                     "latency_ms": r["poisson"]["latency_ms"], "requests": r["poisson"]["requests"],
+                     "evictions": r["saturated"]["evictions"] + r["poisson"]["evictions"]}
+    out["config"] = {"sessions": args.serving_sessions, "budget_fraction": 1 / 3,
+                     "poisson_seconds": args.serving_seconds, "load": 0.8,
+                     "saturation": "one request per session, all present at the start"}
+    return out
 
 
 def residual(F, A0_parts, ups):
@@ -273,12 +324,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = [oracle_sample(args.oracle_rows, 1)["seconds_per_update"] for _ in range(args.warmup)]
-    t = [oracle_sample(args.oracle_rows, 1)["seconds_per_update"] for _ in range(args.steps)]
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_sample(args.oracle_rows, 1)
+    t_meas = time.perf_counter()
+    samples = [oracle_sample(args.oracle_rows, 1) for _ in range(args.steps)]
+    t_meas = time.perf_counter() - t_meas
+    t = [x["seconds_per_update"] for x in samples]
     import oracle as O
     per = statistics.mean(t)
     line = {"impl": "reference", "metric": METRIC, "value": 1.0 / per, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "ms_per_step_kind": ("extrapolated: each step generates all rotations of one full update and "
+                                 f"applies them to {args.oracle_rows} of {M} rows of Q and of P; the apply "
+                                 "time is scaled to all rows (rows are independent)"),
+            "measured_wall_s": {"timed_steps": t_meas, "per_step": t_meas / max(args.steps, 1),
+                                "whole_run": time.perf_counter() - t_all},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "recommender stream m=n=4096, rank-1 set-item-column updates",
                                             "m": M, "n": N, "l2": "n/a (CPU)"},
@@ -305,7 +366,8 @@ def run_gpu(args):
     from paper_2509_02840_gb300 import bdu
     bdu.load()
     K, W = args.steps, args.warmup
-    Q, d, e, P, ups = workload(rank, W + K + args.e2e_steps + 1 + args.fp64_steps)
+    n_e2e = max(args.e2e_steps, K)
+    Q, d, e, P, ups = workload(rank, W + K + n_e2e + 1 + args.fp64_steps)
     stream = torch.cuda.Stream()
     dev_ups = []
     with torch.cuda.stream(stream):
@@ -390,8 +452,12 @@ def run_gpu(args):
             print(json.dumps(line), flush=True)
         return
 
-    # ---- e2e through the host-pointer ABI (pinned buffers, result read back)
-    e2e_seq = ups[W + K:W + K + args.e2e_steps]
+    # ---- e2e through the host-pointer ABI (pinned buffers, result read back):
+    # each update's wall time from its bdu_update call to the return of the
+    # bdu_read of its d, e is one latency sample; the region ends after
+    # bdu_flush and bdu_sync, so the last update's deferred application to Q
+    # and P is inside it
+    e2e_seq = ups[W + K:W + K + n_e2e]
     pinned = []
     for B, C in e2e_seq:
         pb = torch.from_numpy(np.asfortranarray(B).reshape(-1, order="F")).pin_memory()
@@ -402,12 +468,17 @@ def run_gpu(args):
     import ctypes
     dp = ctypes.POINTER(ctypes.c_double)
     Fm.sync()
+    lat = []
     t0 = time.perf_counter()
     for pb, pc in pinned:
+        ts = time.perf_counter()
         code = Fm._L.bdu_update(Fm._h, ctypes.cast(pb.data_ptr(), dp), ctypes.cast(pc.data_ptr(), dp), 1)
         bdu._check(Fm._L, Fm._h, code)
         code = Fm._L.bdu_read(Fm._h, None, dbuf.ctypes.data_as(dp), ebuf.ctypes.data_as(dp), None)
         bdu._check(Fm._L, Fm._h, code)
+        lat.append(1e3 * (time.perf_counter() - ts))
+    Fm.flush()
+    Fm.sync()
     e2e_s = (time.perf_counter() - t0) / len(pinned)
     Fm.close()
 
@@ -430,8 +501,11 @@ def run_gpu(args):
                    "m": M, "n": N, "rank": 1, "form": "mixed", "parallelism": f"replicas x{world}",
                    "overlap": "apply of step h concurrent with the chase of step h+1",
                    "l2": "not flushed: each step streams ~1.2 GB (rotation records, Q, P) > 129 MB L2"},
-        "latency_ms": {"p50": statistics.median(ms), "p99": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
-                       "max": max(ms)},
+        "latency_ms": latency_summary(lat, "wall time of one update through the C ABI: bdu_update with pinned "
+                                           "host B, C until bdu_read of its d, e returns (overlapped form: "
+                                           "the application to Q, P runs behind it)"),
+        "step_interval_ms": {"median": statistics.median(ms), "max": max(ms), "samples": len(ms),
+                             "what": "interval between the chase ends of consecutive timed steps"},
         "fp64_form": {"value": 1e3 / statistics.mean(ms64), "unit": UNIT, "ms_per_step": statistics.mean(ms64),
                       "steps": len(ms64), "relative_residual": res64},
         "mixed_relative_residual": res_mixed,
@@ -445,11 +519,15 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": 1.0 / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": 8 * (M + N), "d2h_bytes_per_step": 8 * (2 * N - 1),
-                "path": "bdu_update (pinned host B, C) + bdu_read of d, e per step, wall clock"},
+                "h2d_bytes_per_step": 8 * (M + N), "d2h_bytes_per_step": 8 * (2 * N - 1), "steps": len(lat),
+                "path": "bdu_update (pinned host B, C) + bdu_read of d, e per step, wall clock; the region "
+                        "ends after bdu_flush + bdu_sync (the last deferred application included)"},
         "gpu_launches": launches,
         "wall_s_timed": t_wall,
     }
+    line["apply_roofline"] = apply_roofline(st, rot_per_update)
+    if rank == 0 and world == 1 and args.serving_seconds > 0:
+        line["serving"] = serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.oracle_rows, 1)
     if rank == 0:

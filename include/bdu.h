@@ -284,13 +284,25 @@ void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx);
  * work), as well as m >= n >= 1.  Every intermediate lives in one fixed
  * __device__ array of the library (about 5.5 MB, held by every GPU that loads
  * the library until the process exits); no cudaMalloc, cudaFree or allocating
- * library routine is called.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current, so
- * that first call should come before any stream capture.  All calls share the
- * array and each call clears what must start at zero; calls that overlap on
- * the GPU (from several host threads or unordered streams) race on it.
- * Errors: BDU_EINVAL, BDU_ECUDA, BDU_ETIMEOUT, BDU_EINTERNAL (status codes
- * only; bdu_last_error is not updated). */
+ * library routine is called by this entry point.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so that first call should come before any stream capture.  Under
+ * CUDA's lazy module loading that first call is also when the driver loads
+ * the module and commits the array's memory on that device: a caller that
+ * lets a host framework reserve the GPU's memory should make its first call
+ * before the framework does (it can fail with BDU_ECUDA otherwise).  The
+ * looked-up address is kept per device ordinal for the life of the process,
+ * so the device's primary context must stay alive (no cudaDeviceReset between
+ * calls).  Each call waits for its stream (cudaStreamSynchronize) before it
+ * returns.  All calls share the array and each call clears what must start at
+ * zero; calls that overlap on the GPU (from several host threads or unordered
+ * streams) race on it.
+ * Errors: BDU_EINVAL, BDU_ECUDA, BDU_ETIMEOUT (the chase's watchdog ran out),
+ * BDU_EINTERNAL (a device invariant check failed) -- status codes only;
+ * bdu_last_error is not updated.  After BDU_ETIMEOUT or BDU_EINTERNAL the
+ * caller's Q, d, e and P are unchanged (the kernels that write them skip
+ * their work when the chase has reported a failure); after BDU_ECUDA their
+ * contents are undefined. */
 bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, double *d, double *e,
                                     double *P, const double *b, const double *c, void *stream);
 
@@ -348,6 +360,32 @@ const char *bdu_thin_last_error(bdu_thin_handle h);
 
 /* Releases the handle's device memory.  NULL is accepted. */
 void bdu_thin_destroy(bdu_thin_handle h);
+
+/* ---- Failure injection ----------------------------------------------------
+ * Drives the library's bounded device-side waits and its chase watchdog to
+ * expiry without a GPU fault, for tests of failure detection (process-wide:
+ * it applies to kernels launched after the call, on every handle and on
+ * bdu_update_rank1_noalloc).  site:
+ *   BDU_INJECT_NONE: off (the default; value ignored);
+ *   BDU_INJECT_STEP_BUDGET: a chase launched with no step budget of its own
+ *     (bdu_options.step_budget = 0, and the allocation-free entry point) stops
+ *     after `value` synchronous steps per rank-1 column;
+ *   BDU_INJECT_APPLY_STALL: the FP32 register-resident rotation apply (mixed
+ *     form) starts no copy of rotation records, and its compute warps give up
+ *     after `value` polls of a wait;
+ *   BDU_INJECT_ROTVEC_STALL: likewise for the rotation of projected vectors
+ *     (overlapped mixed form and mixed rank-r updates).
+ * In each case nothing is in flight when the waits give up; the expiry sets a
+ * bit of the handle's device status word, the next synchronizing call reports
+ * BDU_ETIMEOUT and the handle is poisoned.  Returns BDU_EINVAL for an unknown
+ * site or value < 1 (the setting is then unchanged). */
+enum {
+  BDU_INJECT_NONE = 0,
+  BDU_INJECT_STEP_BUDGET = 1,
+  BDU_INJECT_APPLY_STALL = 2,
+  BDU_INJECT_ROTVEC_STALL = 3
+};
+bdu_status bdu_set_fault_injection(int site, int64_t value);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bdu_version(void);

@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
     L.bdu_set_allocator.restype = None
     L.bdu_version.argtypes = []
     L.bdu_version.restype = ctypes.c_int
+    L.bdu_set_fault_injection.argtypes = [ctypes.c_int, ctypes.c_int64]
+    L.bdu_set_fault_injection.restype = ctypes.c_int
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.bdu_thin_create.argtypes = [ctypes.POINTER(H), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
                                   ctypes.POINTER(Options)]
@@ -123,6 +125,17 @@ def load(build_if_missing: bool = True):
     L.bdu_thin_destroy.restype = None
     _lib = L
     return L
+
+
+INJECT_NONE, INJECT_STEP_BUDGET, INJECT_APPLY_STALL, INJECT_ROTVEC_STALL = 0, 1, 2, 3
+
+
+def set_fault_injection(site: int, value: int = 1) -> None:
+    """bdu_set_fault_injection: process-wide failure injection for tests of
+    the bounded device-side waits (INJECT_NONE switches it off)."""
+    code = load().bdu_set_fault_injection(int(site), int(value))
+    if code != 0:
+        raise BduError(code, "bdu_set_fault_injection: unknown site or value < 1")
 
 
 def declared_functions(header: str = HEADER):

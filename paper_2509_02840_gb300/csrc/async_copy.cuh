@@ -28,10 +28,10 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
                : "memory");
 }
 // Waits for the completion of the phase with the given parity; false if the
-// bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// bound (spin polls) ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int spin = kSpin) {
   const unsigned a = smem_addr(bar);
-  for (int i = 0; i < kSpin; i++) {
+  for (int i = 0; i < spin; i++) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -20,6 +20,12 @@
 #include "bdu_internal.cuh"
 
 namespace bdu {
+namespace {
+std::atomic<int> g_inject_site{BDU_INJECT_NONE};
+std::atomic<long long> g_inject_value{0};
+}  // namespace
+Injection injection() { return Injection{g_inject_site.load(), g_inject_value.load()}; }
+
 cudaError_t launch_project_nz(int precision, const void *X, int64_t ld, int nrow, int ncol,
                               const double *B, int64_t ldb, int r, double *U, int64_t ldu,
                               int32_t *nz_ws, cudaStream_t s);
@@ -1820,6 +1826,18 @@ bdu_status bdu_check_orthogonality(bdu_handle h, double *q_est, double *p_est) {
   if (h->tr) std::swap(e0, e1);
   if (q_est) *q_est = e0;
   if (p_est) *p_est = e1;
+  return BDU_OK;
+}
+
+bdu_status bdu_set_fault_injection(int site, int64_t value) {
+  if (site == BDU_INJECT_NONE) {
+    g_inject_site.store(BDU_INJECT_NONE);
+    g_inject_value.store(0);
+    return BDU_OK;
+  }
+  if (site < BDU_INJECT_STEP_BUDGET || site > BDU_INJECT_ROTVEC_STALL || value < 1) return BDU_EINVAL;
+  g_inject_value.store(value);
+  g_inject_site.store(site);
   return BDU_OK;
 }
 

@@ -18,6 +18,14 @@ enum : int {
   ERR_RANGE = 64,    // a record named a pair outside the vector (skipped)
 };
 
+// Failure injection for tests of the bounded waits (bdu_set_fault_injection):
+// the site set (BDU_INJECT_*) and its value; site BDU_INJECT_NONE when off.
+struct Injection {
+  int site;
+  long long value;
+};
+Injection injection();
+
 // The working core M = band + u v^T of one rank-1 step, in global memory.
 // 1-based arrays.  dg[o+2][i] = M(i, i+o) for rows i >= 2 and offsets
 // o = -2..3; row 1 is kept densely in r1[j] = M(1, j), j = 1..n, in every
@@ -118,11 +126,13 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 // R > 0 = rows per thread block of the slab kernel (even, <= 64); mixed form:
 // 1..4 = a register layout of launch_apply_reg, kSlabVariant = the slab
 // kernel.  cudaErrorNotSupported when the variant does not cover the shape.
+// gate (slab kernel only; may be null): a device error word; when an earlier
+// kernel on the stream has made it nonzero, X is left untouched.
 constexpr int kSlabVariant = 5;
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s,
                          int *status = nullptr, int sm_reserve = 0, bool desc_ready = false,
-                         int variant = 0);
+                         int variant = 0, const int *gate = nullptr);
 
 cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, int max_band_doubles,
                                int fast, cudaStream_t s);

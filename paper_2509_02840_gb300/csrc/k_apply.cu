@@ -186,10 +186,13 @@ __device__ __forceinline__ void apply_slab_body(T *__restrict__ X, int64_t ld, i
   }
 }
 
+// gate (may be null): a device error word written by an earlier kernel on
+// the stream; when it is nonzero the kernel leaves X untouched.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_apply_slab(T *__restrict__ X, int64_t ld, int nrow,
                                                          int ncol, int R, int csw, RotStream st,
-                                                         int side, int with_spike) {
+                                                         int side, int with_spike, const int *gate) {
+  if (gate && *(volatile const int *)gate) return;
   apply_slab_body<T>(X, ld, nrow, ncol, R, csw, st, side, with_spike, blockIdx.x);
 }
 
@@ -247,7 +250,7 @@ cudaError_t launch_apply_batch(int precision, const ApplyItem *d_items, const in
 
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status,
-                         int sm_reserve, bool desc_ready, int variant) {
+                         int sm_reserve, bool desc_ready, int variant, const int *gate) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
   if (precision == BDU_MIXED && variant != kSlabVariant) {
     const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, sm_reserve,
@@ -287,12 +290,12 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
     e = cudaFuncSetAttribute(k_apply_slab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_apply_slab<double><<<blocks, kThreads, smem, s>>>((double *)X, ld, nrow, ncol, best_R, best_csw, st,
-                                                        side, with_spike ? 1 : 0);
+                                                        side, with_spike ? 1 : 0, gate);
   } else {
     e = cudaFuncSetAttribute(k_apply_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_apply_slab<float><<<blocks, kThreads, smem, s>>>((float *)X, ld, nrow, ncol, best_R, best_csw, st,
-                                                       side, with_spike ? 1 : 0);
+                                                       side, with_spike ? 1 : 0, gate);
   }
   return cudaGetLastError();
 }

@@ -27,7 +27,11 @@
 // whose columns the chase does not reach skips it.
 //
 // Every wait is bounded; one that runs out sets ERR_APPLY in the status word
-// and the kernel carries on (the result is then reported as invalid).
+// (the result is then reported as invalid): the producer issues no further
+// copies and waits for those in flight, a compute warp stops.  Failure
+// injection (bdu_set_fault_injection) can keep the producer from issuing any
+// copy and shorten the bound, so that a test drives these waits to expiry
+// with nothing in flight.
 //
 // Arithmetic: the generator's FP32 copies of (c, s), x' = fma(c, x, s*y),
 // y' = fma(c, y, -s*x) -- the operations of the shared-memory slab kernel, so
@@ -35,56 +39,21 @@
 // and runs before, one thread per row.
 #include <climits>
 
+#include "async_copy.cuh"
 #include "bdu_internal.cuh"
 
 namespace bdu {
 namespace {
 
+using async::bulk_g2s;
+using async::mbar_arrive;
+using async::mbar_arrive_tx;
+using async::mbar_init;
+using async::mbar_wait;
+
 constexpr int kMaxThreads = 384;  // compute warps + the producer warp
 constexpr int kMaxCompute = 352;  // compute threads
-constexpr int kSpin = 1 << 22;    // bound on every wait loop
 constexpr size_t kSmemBudget = 200 * 1024;
-
-// ---------------------------------------------------------------------------
-// mbarrier and bulk-copy primitives
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
-                   smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// Waits for the completion of the phase with the given parity; false if the
-// bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  const unsigned a = smem_addr(bar);
-  for (int i = 0; i < kSpin; i++) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
 
 __device__ __forceinline__ void rot32(float c, float s, float &x, float &y) {
   const float xo = x, yo = y;
@@ -215,10 +184,12 @@ struct Layout {
 // xl = column c0-1.  Across warps through shared memory and flags: a warp
 // publishes its edges before it waits for its neighbours', so no wait cycle
 // can form.
+// Returns false (for the whole warp) when a wait ran out.
 template <int W, int V>
-__device__ __forceinline__ void exchange(const float (&x)[V][W], float (&xl)[V], float (&yr)[V], float *edge,
+__device__ __forceinline__ bool exchange(const float (&x)[V][W], float (&xl)[V], float (&yr)[V], float *edge,
                                          volatile int *flag, int slot, int q, int lane, int warp, int nwc,
-                                         bool lact, bool ract, int *status) {
+                                         bool lact, bool ract, int spin, int *status) {
+  bool ok = true;
 #pragma unroll
   for (int r = 0; r < V; r++) {
     yr[r] = __shfl_down_sync(0xffffffffu, x[r][0], 1);
@@ -240,8 +211,8 @@ __device__ __forceinline__ void exchange(const float (&x)[V][W], float (&xl)[V],
   if (lane == 31 && ract) {
     const int nb = base + 1;  // the right neighbour's column 0
     int i = 0;
-    while (flag[nb * 2 + 0] != q && i < kSpin) i++;
-    if (i == kSpin) atomicOr(status, ERR_APPLY);
+    while (flag[nb * 2 + 0] != q && i < spin) i++;
+    if (i == spin) { atomicOr(status, ERR_APPLY); ok = false; }
     __threadfence_block();
 #pragma unroll
     for (int r = 0; r < V; r++) yr[r] = edge[(nb * 2 + 0) * V + r];
@@ -249,13 +220,13 @@ __device__ __forceinline__ void exchange(const float (&x)[V][W], float (&xl)[V],
   if (lane == 0 && lact) {
     const int nb = base - 1;  // the left neighbour's column W-1
     int i = 0;
-    while (flag[nb * 2 + 1] != q && i < kSpin) i++;
-    if (i == kSpin) atomicOr(status, ERR_APPLY);
+    while (flag[nb * 2 + 1] != q && i < spin) i++;
+    if (i == spin) { atomicOr(status, ERR_APPLY); ok = false; }
     __threadfence_block();
 #pragma unroll
     for (int r = 0; r < V; r++) xl[r] = edge[(nb * 2 + 1) * V + r];
   }
-  __syncwarp();
+  return !__any_sync(0xffffffffu, !ok);
 }
 
 // The halves of the straddling pairs a thread keeps: (c0+W-1, c0+W) gives the
@@ -327,7 +298,7 @@ template <int W, int V>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     k_apply_reg(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float2 *__restrict__ coef,
                 const int32_t *__restrict__ Ca, const int4 *__restrict__ desc, int T, int cap, Layout L,
-                int *__restrict__ status) {
+                int spin, int stall, int *__restrict__ status) {
   extern __shared__ __align__(128) unsigned char raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwc = L.nwc, R = L.R, rs = L.rshift, rmask = L.R - 1;
@@ -351,9 +322,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
   if (warp == nwc) {
     // ---- producer warp: one bulk copy per chase into the ring; the
-    // descriptors come 32 at a time, one per lane
+    // descriptors come 32 at a time, one per lane.  After a wait that ran out
+    // it issues nothing more.  With stall set (failure injection) it issues
+    // nothing at all, so that the compute warps' waits run out while no copy
+    // is in flight.
+    if (stall) return;
     const int4 none = make_int4(0, kEmptyCode << 24, INT_MAX, INT_MIN);
     int4 dcur = none;
+    int issued = 0;
     for (int q = 0, u = 0; q < layers; q++, u = (u + 1 == T) ? 0 : u + 1) {
       if ((u & 31) == 0) dcur = (u + lane < T) ? desc[u + lane] : none;
       int4 d;
@@ -361,24 +337,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       d.y = __shfl_sync(0xffffffffu, dcur.y, u & 31);
       d.z = __shfl_sync(0xffffffffu, dcur.z, u & 31);
       d.w = __shfl_sync(0xffffffffu, dcur.w, u & 31);
+      bool ok = true;
       if (lane == 0) {
         const int s = q & rmask;
-        if (q >= R && !mbar_wait(&empty[s], (unsigned)(((q >> rs) - 1) & 1))) atomicOr(status, ERR_APPLY);
-        unsigned char *slot = raw + (size_t)s * L.slot_bytes;
-        *reinterpret_cast<int4 *>(slot) = d;
-        const int cnt = d.y & 0xffffff;
-        const size_t first = (size_t)u * cap;  // the chase's first record
-        const size_t start = first & ~(size_t)1;
-        const unsigned bytes = cnt > 0 ? (unsigned)(((first - start + cnt + 1) / 2) * 16) : 0u;
-        mbar_arrive_tx(&full[s], bytes);
-        if (bytes) bulk_g2s(slot + 16, coef + start, bytes, &full[s]);
+        if (q >= R && !mbar_wait(&empty[s], (unsigned)(((q >> rs) - 1) & 1), spin)) {
+          atomicOr(status, ERR_APPLY);
+          ok = false;
+        } else {
+          unsigned char *slot = raw + (size_t)s * L.slot_bytes;
+          *reinterpret_cast<int4 *>(slot) = d;
+          const int cnt = d.y & 0xffffff;
+          const size_t first = (size_t)u * cap;  // the chase's first record
+          const size_t start = first & ~(size_t)1;
+          const unsigned bytes = cnt > 0 ? (unsigned)(((first - start + cnt + 1) / 2) * 16) : 0u;
+          mbar_arrive_tx(&full[s], bytes);
+          if (bytes) bulk_g2s(slot + 16, coef + start, bytes, &full[s]);
+        }
       }
-      __syncwarp();
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      issued = q + 1;
     }
-    // the last copies have landed before the block may exit
+    // the last copies issued have landed before the block may exit
     if (lane == 0)
-      for (int q = layers > R ? layers - R : 0; q < layers; q++)
-        if (!mbar_wait(&full[q & rmask], (unsigned)((q >> rs) & 1))) atomicOr(status, ERR_APPLY);
+      for (int q = issued > R ? issued - R : 0; q < issued; q++)
+        if (!mbar_wait(&full[q & rmask], (unsigned)((q >> rs) & 1), spin)) atomicOr(status, ERR_APPLY);
     return;
   }
 
@@ -401,7 +383,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     for (int t = 0; t < T; t++, q++) {
       const int s = q & rmask;
-      if (!mbar_wait(&full[s], (unsigned)((q >> rs) & 1))) atomicOr(status, ERR_APPLY);
+      // after a wait that ran out the warp stops (the result is reported invalid)
+      if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (unsigned)((q >> rs) & 1), spin))) {
+        if (lane == 0) atomicOr(status, ERR_APPLY);
+        return;
+      }
       const unsigned char *slot = raw + (size_t)s * L.slot_bytes;
       const int4 d = *reinterpret_cast<const int4 *>(slot);
       const int cnt = d.y & 0xffffff, code = d.y >> 24;
@@ -413,7 +399,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
           // chase starts (ends) within its reach
           const bool lact = warp > 0 && d.z <= wlo;
           const bool ract = warp + 1 < nwc && d.w >= whi;
-          exchange<W, V>(x, xl, yr, edge, flag, s, q, lane, warp, nwc, lact, ract, status);
+          if (!exchange<W, V>(x, xl, yr, edge, flag, s, q, lane, warp, nwc, lact, ract, spin, status)) return;
         }
         switch (code) {
           case 0: apply_prog<W, V, 2, 0>(x, rec, d.x + tid * (W / 2), cnt, xl, yr); break;
@@ -465,7 +451,10 @@ struct RegLaunch {
   }
   void launch(float *X, int64_t ld, int nrow, int ncol, const float2 *coef, const int32_t *Ca, const int4 *desc,
               int T, int cap, int *status, cudaStream_t s) const {
-    k_apply_reg<W, V><<<grid, nth, L.total, s>>>(X, ld, nrow, ncol, coef, Ca, desc, T, cap, L, status);
+    const Injection inj = injection();
+    const int stall = inj.site == BDU_INJECT_APPLY_STALL ? 1 : 0;
+    const int spin = stall ? (int)(inj.value < async::kSpin ? inj.value : async::kSpin) : async::kSpin;
+    k_apply_reg<W, V><<<grid, nth, L.total, s>>>(X, ld, nrow, ncol, coef, Ca, desc, T, cap, L, spin, stall, status);
   }
 };
 

@@ -1076,7 +1076,12 @@ cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s) {
+// Failure injection (BDU_INJECT_STEP_BUDGET) sets the step budget of a
+// column whose caller set none.
+cudaError_t launch_chase(const ChaseArgs &a0, cudaStream_t s) {
+  ChaseArgs a = a0;
+  const Injection inj = injection();
+  if (a.step_budget == 0 && inj.site == BDU_INJECT_STEP_BUDGET) a.step_budget = inj.value;
   return a.fast ? launch_engine<true>(a, s) : launch_engine<false>(a, s);
 }
 

@@ -127,8 +127,10 @@ __global__ void k_band_from_de(const double *__restrict__ d, const double *__res
   }
 }
 
+// Leaves d, e untouched when the status word reports a failure of the chase.
 __global__ void k_de_from_band(const double *__restrict__ band, double *__restrict__ d,
-                               double *__restrict__ e, int m, int n) {
+                               double *__restrict__ e, int m, int n, const int *__restrict__ status) {
+  if (*(volatile const int *)status) return;
   BandPtrs b = dev_band_ptrs(const_cast<double *>(band), m, n);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x + 1; i <= n; i += gridDim.x * blockDim.x) {
     d[i - 1] = (i == 1) ? b.r1[1] : b.dg[2][i];
@@ -194,10 +196,11 @@ extern "C" bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, 
     a.st = st; a.status = status; a.counters = counters;
     ce = launch_chase(a, s);
   }
-  if (ce == cudaSuccess) ce = launch_apply(BDU_FP64, Q, m, (int)m, (int)m, st, 0, m > n, s);
-  if (ce == cudaSuccess) ce = launch_apply(BDU_FP64, P, n, (int)n, (int)n, st, 1, false, s);
+  // a failure of the chase (status word nonzero) leaves Q, P, d and e untouched
+  if (ce == cudaSuccess) ce = launch_apply(BDU_FP64, Q, m, (int)m, (int)m, st, 0, m > n, s, status, 0, false, 0, status);
+  if (ce == cudaSuccess) ce = launch_apply(BDU_FP64, P, n, (int)n, (int)n, st, 1, false, s, status, 0, false, 0, status);
   if (ce == cudaSuccess) {
-    k_de_from_band<<<1, 256, 0, s>>>(band, d, e, (int)m, (int)n);
+    k_de_from_band<<<1, 256, 0, s>>>(band, d, e, (int)m, (int)n, status);
     ce = cudaGetLastError();
   }
   int hst = 0;

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
                                                              int nl, int m, const double *w_right, double *dst_right,
                                                              int64_t ldr, int n,
                                                              RotStream st, int with_spike, RvLayout L,
-                                                             int *__restrict__ status) {
+                                                             int spin, int stall, int *__restrict__ status) {
   extern __shared__ __align__(128) unsigned char raw[];
   const bool left = (int)blockIdx.x < nl;
   const int vec = left ? (int)blockIdx.x : (int)blockIdx.x - nl;
@@ -138,10 +138,15 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
   const int cap = st.cap, T = st.T;
 
   if (tid >= kCompute) {
-    // ---- producer warp: descriptors 32 at a time, one bulk copy per chunk
+    // ---- producer warp: descriptors 32 at a time, one bulk copy per chunk.
+    // After a wait that ran out it issues nothing more; with stall set
+    // (failure injection) nothing at all, so that the compute threads' waits
+    // run out while no copy is in flight.
+    if (stall) return;
     const int lane = tid - kCompute;
     int q = 0;  // chunks issued
-    for (int t0 = 0; t0 < T; t0 += 32) {
+    bool dead = false;
+    for (int t0 = 0; t0 < T && !dead; t0 += 32) {
       const int4 mine = (t0 + lane < T) ? desc[t0 + lane] : make_int4(0, 7 << 24, 0, 0);
       for (int i = 0; i < 32 && t0 + i < T; i++) {
         const int dy = __shfl_sync(0xffffffffu, mine.y, i);
@@ -155,8 +160,11 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
           for (int e0 = 0; e0 < cnt; e0 += kRecs, q++) {
             const int k = min(kRecs, cnt - e0);
             const int s = q & L.rmask;
-            if (q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1)))
+            if (q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1), spin)) {
               atomicOr(status, ERR_ROTVEC);
+              dead = true;
+              break;
+            }
             unsigned char *slot = raw + L.ring + (size_t)s * kSlot;
             const size_t first = (size_t)t * cap + e0;
             const int sh = (int)(first & 1);
@@ -168,18 +176,26 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
           }
         }
         q = __shfl_sync(0xffffffffu, q, 0);
+        dead = __shfl_sync(0xffffffffu, dead, 0);
+        if (dead) break;
       }
     }
     if (lane == 0) {
-      // the end marker, then the last copies have landed before the block may exit
+      // the end marker (unless a wait ran out), then the last copies issued
+      // have landed before the block may exit
       const int s = q & L.rmask;
-      if (q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1)))
+      if (!dead && q >= L.R && !async::mbar_wait(&empty[s], (unsigned)(((q >> L.rshift) - 1) & 1), spin)) {
         atomicOr(status, ERR_ROTVEC);
-      *reinterpret_cast<int4 *>(raw + L.ring + (size_t)s * kSlot) = make_int4(0, kStop, 0, 0);
-      async::mbar_arrive_tx(&full[s], 0u);
+        dead = true;
+      }
+      if (!dead) {
+        *reinterpret_cast<int4 *>(raw + L.ring + (size_t)s * kSlot) = make_int4(0, kStop, 0, 0);
+        async::mbar_arrive_tx(&full[s], 0u);
+      }
       // (chunk q - R shared its slot with the end marker: it was consumed before)
       for (int p = q - L.R + 1 > 0 ? q - L.R + 1 : 0; p < q; p++)
-        if (!async::mbar_wait(&full[p & L.rmask], (unsigned)((p >> L.rshift) & 1))) atomicOr(status, ERR_ROTVEC);
+        if (!async::mbar_wait(&full[p & L.rmask], (unsigned)((p >> L.rshift) & 1), spin))
+          atomicOr(status, ERR_ROTVEC);
     }
     return;
   }
@@ -187,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_rotate_vectors(const double *w_lef
   // ---- compute threads
   for (int q = 0;; q++) {
     const int s = q & L.rmask;
-    if (!async::mbar_wait(&full[s], (unsigned)((q >> L.rshift) & 1))) {
+    if (!async::mbar_wait(&full[s], (unsigned)((q >> L.rshift) & 1), spin)) {
       atomicOr(status, ERR_ROTVEC);
       break;
     }
@@ -265,8 +281,11 @@ cudaError_t launch_rotate_vector_sets(const double *w_left, double *dst_left, in
   if (nl + nr == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_rotate_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
+  const Injection inj = injection();
+  const int stall = inj.site == BDU_INJECT_ROTVEC_STALL ? 1 : 0;
+  const int spin = stall ? (int)(inj.value < async::kSpin ? inj.value : async::kSpin) : async::kSpin;
   k_rotate_vectors<<<nl + nr, kThreads, L.total, s>>>(w_left, dst_left, ldl, nl, m, w_right, dst_right, ldr, n, st,
-                                                     with_spike ? 1 : 0, L, status);
+                                                     with_spike ? 1 : 0, L, spin, stall, status);
   return cudaGetLastError();
 }
 

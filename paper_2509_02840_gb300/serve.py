@@ -229,7 +229,8 @@ class Server:
         ups = sum(q.r for q in self.done)
         return {"requests": len(self.done), "updates": ups, "wall_s": wall, "updates_per_s": ups / wall,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
-                               "p99": float(np.percentile(lat, 99)) if lat.size else None},
+                               "p99": float(np.percentile(lat, 99)) if lat.size else None,
+                               "samples": int(lat.size)},
                 "batches": self.batches - batches0,
                 "evictions": sum(s.evictions for s in self.sessions) - evictions0,
                 "peak_resident_bytes": self.peak_resident, "budget_bytes": self.budget}
@@ -259,15 +260,16 @@ def poisson_arrivals(specs, rate, count, seed=0, config=4, first_update=None):
 
 
 def serve(num_sessions=256, seconds=20.0, precision=bdu.MIXED, budget_fraction=1 / 3, load=0.8,
-          max_batch=64, seed=0):
-    """Saturation first (4 requests per session, all present at the start),
-    then Poisson arrivals at `load` times the saturated request rate for about
-    `seconds`; both on the same sessions, which carry their state over."""
+          max_batch=64, seed=0, sat_per_session=4):
+    """Saturation first (sat_per_session requests per session, all present
+    at the start), then Poisson arrivals at `load` times the saturated request
+    rate for about `seconds`; both on the same sessions, which carry their
+    state over."""
     specs = inputs.serving_mix(num_sessions)
     total = sum(reserve_bytes(m, n, precision) for m, n in specs)
     srv = Server(specs, precision, int(total * budget_fraction), max_batch)
     counter = collections.Counter()
-    sat = srv.run(poisson_arrivals(specs, 0.0, 4 * num_sessions, seed, first_update=counter))
+    sat = srv.run(poisson_arrivals(specs, 0.0, sat_per_session * num_sessions, seed, first_update=counter))
     rate = load * sat["requests"] / sat["wall_s"]
     arr = poisson_arrivals(specs, rate, max(1, int(rate * seconds)), seed + 1, first_update=counter)
     res = srv.run(arr, time_limit=3 * seconds)

@@ -105,3 +105,15 @@ def test_thin_null_handle_calls_are_rejected(lib):
     assert lib.bdu_thin_read(None, None, None, None, None) == 1
     assert lib.bdu_thin_stats(None, None, None, None) == 1
     lib.bdu_thin_destroy(None)  # accepted
+
+
+def test_fault_injection_arguments_without_a_gpu(lib):
+    """bdu_set_fault_injection validates its site and value; the setting is
+    process-wide and switched off again at the end."""
+    assert lib.bdu_set_fault_injection(9, 1) == 1       # unknown site
+    assert lib.bdu_set_fault_injection(-1, 1) == 1
+    assert lib.bdu_set_fault_injection(bdu.INJECT_APPLY_STALL, 0) == 1  # value < 1
+    assert lib.bdu_set_fault_injection(bdu.INJECT_STEP_BUDGET, 7) == 0
+    assert lib.bdu_set_fault_injection(bdu.INJECT_NONE, 0) == 0
+    with pytest.raises(bdu.BduError):
+        bdu.set_fault_injection(bdu.INJECT_ROTVEC_STALL, 0)

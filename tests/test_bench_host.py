@@ -63,3 +63,22 @@ def test_clock_samples_flag_throttling_and_take_the_median():
     assert c["samples"] == 3 and c["sm_mhz"] == 1500.0 and c["reasons"] == ["sw_thermal_slowdown"]
     c = bench.parse_clock_samples([])
     assert c["sm_mhz"] is None and c["samples"] == 0
+
+
+def test_latency_summary_names_p99_only_with_enough_samples():
+    few = bench.latency_summary([5.0, 1.0, 3.0], "x")
+    assert few["p50"] == 3.0 and few["max"] == 5.0 and "p99" not in few and few["samples"] == 3
+    many = bench.latency_summary([float(i) for i in range(1, 201)], "x")
+    assert many["p99"] == 198.0 and many["max"] == 200.0 and many["p50"] == 100.5
+
+
+def test_apply_roofline_counts_factor_and_records_once(size, monkeypatch):
+    size(4096)
+    monkeypatch.setattr(bench, "peaks", lambda: {"hbm_gbs": 6800.0})
+    st = _stats(chase_ms=0.0, apply_ms=100.0, updates=2, apply_launches=4)
+    rot = 25_000_000
+    r = bench.apply_roofline(st, rot)
+    alg = 2 * 4096 * 4096 * 4 + 8 * rot / 2
+    assert r["algorithmic_bytes"] == alg and r["ms_per_launch"] == pytest.approx(25.0)
+    assert r["achieved"] == pytest.approx(alg / 25e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0)

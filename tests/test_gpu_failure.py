@@ -76,3 +76,34 @@ def test_negative_budget_is_rejected():
     Q, d, e, P = I.factorization(20, 10, config=0, which=1)
     with pytest.raises(bdu.BduError):
         bdu.Factorization(Q, d, e, P, step_budget=-1)
+
+
+@pytest.mark.parametrize("site,rank,what", [(bdu.INJECT_APPLY_STALL, 1, "rotation apply"),
+                                            (bdu.INJECT_ROTVEC_STALL, 2, "vector rotation")])
+def test_bounded_waits_expire_and_poison(site, rank, what):
+    """The FP32 register-resident apply's and the vector rotation's waits on
+    their record rings: failure injection keeps the producer warp from
+    starting any copy and shortens the bound, so the compute threads' waits run
+    out with nothing in flight; the kernel records the expiry in the status
+    word and returns.  (nb=1 fixes the register layout, so no autotuning run
+    meets the injection; rank 2 sends the later column's projections through
+    the vector rotation.)"""
+    m, n = 600, 560
+    Q, d, e, P = I.factorization(m, n, config=0, which=4)
+    B, C = I.dense_update(m, n, 0, config=0, r=rank)
+    F = bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, nb=1, graphs=False)
+    try:
+        bdu.set_fault_injection(site, 2000)
+        try:
+            with pytest.raises(bdu.BduError) as info:
+                F.update(B, C)
+                F.sync()
+        finally:
+            bdu.set_fault_injection(bdu.INJECT_NONE)
+        assert info.value.code == ETIMEOUT and what in str(info.value)
+        with pytest.raises(bdu.BduError) as again:
+            F.update(B, C)
+        assert again.value.code == EPOISONED
+    finally:
+        F.close()
+    _healthy_update_still_works(m, n)

@@ -93,3 +93,33 @@ def test_automatic_check_acts_after_a_batch():
     assert st["reorth_q"] == 1
     after = np.linalg.norm(Qg.T @ Qg - np.eye(m), 2)
     assert after < 0.2 * before and after < 5e-6
+
+
+@pytest.mark.parametrize("precision", [bdu.FP64, bdu.MIXED])
+def test_serving_large_sessions_equal_sequential_replay(precision):
+    """The serving mix's full size range (m, n up to 2048): sessions of order
+    >= 512 get a thread-block cluster each inside a batch, the smaller ones one
+    block each on the second stream; every served session still ends bit for
+    bit where its requests applied one by one leave it."""
+    specs = [(2048, 2048), (1900, 1100), (1800, 600), (900, 700), (520, 512), (300, 200), (128, 64), (96, 90)]
+    check_every = 0 if precision == bdu.MIXED else None
+    per = [S.reserve_bytes(m, n, precision) for m, n in specs]
+    budget = max(per) + sorted(per)[len(per) // 2]  # forces evictions
+    srv = S.Server(specs, precision, budget, max_batch=4, check_every=check_every, reorth_every=1)
+    counter = collections.Counter()
+    burst = S.poisson_arrivals(specs, 0.0, 14, seed=13, first_update=counter)
+    res1 = srv.run(burst)
+    trickle = S.poisson_arrivals(specs, 50.0, 10, seed=14, first_update=counter)
+    res2 = srv.run(trickle)
+    assert res1["requests"] == 14 and res2["requests"] == 10
+    assert res1["evictions"] + res2["evictions"] > 0
+    assert srv.peak_resident <= budget
+    final = {s.sid: s.read() for s in srv.sessions}
+    srv.close()
+    want, by_sid = _replay(specs, burst + trickle, precision, check_every)
+    assert any(specs[sid][1] >= 512 for sid in by_sid)  # a cluster-engine session was served
+    for sid, (m, n) in enumerate(specs):
+        if not by_sid[sid]:
+            continue
+        for a, b in zip(final[sid], want[sid]):
+            assert np.array_equal(a, b), (sid, m, n, len(by_sid[sid]))

@@ -35,7 +35,7 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("m,n", [(200, 150), (256, 256)])
+@pytest.mark.parametrize("m,n", [(200, 150), (256, 256), (1024, 256), (1024, 100), (300, 1)])
 def test_noalloc_matches_handle_path_twice(m, n):
     import torch
     f = _fn()
@@ -45,19 +45,59 @@ def test_noalloc_matches_handle_path_twice(m, n):
     tQ = torch.from_numpy(Q.reshape(-1, order="F").copy()).to(dev)
     tP = torch.from_numpy(P.reshape(-1, order="F").copy()).to(dev)
     td = torch.from_numpy(d.copy()).to(dev)
-    te = torch.from_numpy(e.copy()).to(dev)
+    te = torch.from_numpy(e.copy()).to(dev) if n > 1 else None  # e may be NULL when n == 1
     stream = torch.cuda.current_stream(dev)
     with bdu.Factorization(Q, d, e, P, precision=bdu.FP64) as F:
         for B, C in ups:
             tb = torch.from_numpy(B[:, 0].copy()).to(dev)
             tc = torch.from_numpy(C[:, 0].copy()).to(dev)
             torch.cuda.synchronize()
-            code = f(m, n, tQ.data_ptr(), td.data_ptr(), te.data_ptr(), tP.data_ptr(),
-                     tb.data_ptr(), tc.data_ptr(), stream.cuda_stream)
+            code = f(m, n, tQ.data_ptr(), td.data_ptr(), te.data_ptr() if te is not None else None,
+                     tP.data_ptr(), tb.data_ptr(), tc.data_ptr(), stream.cuda_stream)
             assert code == 0
             F.update(B, C)
             Qh, dh, eh, Ph = F.read()
             assert np.array_equal(td.cpu().numpy(), dh)
-            assert np.array_equal(te.cpu().numpy(), eh)
+            if te is not None:
+                assert np.array_equal(te.cpu().numpy(), eh)
             assert np.array_equal(tQ.cpu().numpy().reshape(m, m, order="F"), Qh)
             assert np.array_equal(tP.cpu().numpy().reshape(n, n, order="F"), Ph)
+
+
+@pytest.mark.gpu
+def test_noalloc_failure_leaves_the_callers_buffers_unchanged():
+    """When the chase's watchdog runs out (forced here by failure injection,
+    no GPU fault), the call reports BDU_ETIMEOUT and the kernels that would
+    write Q, P, d and e skip their work; the next call, without injection,
+    gives the handle path's result again."""
+    import torch
+    f = _fn()
+    m, n = 300, 200
+    Q, d, e, P = I.factorization(m, n, config=0, which=32)
+    B, C = I.dense_update(m, n, 43, config=0)
+    dev = torch.device("cuda", 0)
+    tQ = torch.from_numpy(Q.reshape(-1, order="F").copy()).to(dev)
+    tP = torch.from_numpy(P.reshape(-1, order="F").copy()).to(dev)
+    td = torch.from_numpy(d.copy()).to(dev)
+    te = torch.from_numpy(e.copy()).to(dev)
+    tb = torch.from_numpy(B[:, 0].copy()).to(dev)
+    tc = torch.from_numpy(C[:, 0].copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    args = (m, n, tQ.data_ptr(), td.data_ptr(), te.data_ptr(), tP.data_ptr(), tb.data_ptr(), tc.data_ptr(),
+            stream.cuda_stream)
+    bdu.set_fault_injection(bdu.INJECT_STEP_BUDGET, 5)
+    try:
+        assert f(*args) == 4  # BDU_ETIMEOUT
+    finally:
+        bdu.set_fault_injection(bdu.INJECT_NONE)
+    assert np.array_equal(tQ.cpu().numpy().reshape(m, m, order="F"), Q)
+    assert np.array_equal(tP.cpu().numpy().reshape(n, n, order="F"), P)
+    assert np.array_equal(td.cpu().numpy(), d)
+    assert np.array_equal(te.cpu().numpy(), e)
+    assert f(*args) == 0
+    with bdu.Factorization(Q, d, e, P, precision=bdu.FP64) as F:
+        F.update(B, C)
+        Qh, dh, eh, Ph = F.read()
+    assert np.array_equal(td.cpu().numpy(), dh)
+    assert np.array_equal(tQ.cpu().numpy().reshape(m, m, order="F"), Qh)
