@@ -80,7 +80,15 @@ typedef struct {
                          FP64 form: an even number <= 64 = rows of Q/P per thread
                          block of the shared-memory apply.  Mixed form: 1..4 = a
                          register-resident layout of (columns x rows) per thread
-                         12x8, 24x4, 6x16, 18x4; 5 = the shared-memory apply. */
+                         12x8, 24x4, 6x16, 18x4; 5 = the shared-memory apply;
+                         64, 96, 128 = the blocked tensor-core apply, whose
+                         rotations are accumulated into nb x nb orthogonal blocks
+                         (nb/2 consecutive chases over a window of nb/2 columns)
+                         applied as 3xTF32 products (Sec. 3.2, Eq. bidiagplus);
+                         its results agree with the other variants to FP32
+                         rounding, not bit for bit.  With 0, a factor wider than
+                         every register layout covers (about 8448 columns) uses
+                         the blocked apply with nb = 128. */
   double reorth_tol;  /* BDU_MIXED: re-orthogonalize Q (P) when the estimated
                          ||Q^T Q - I||_2 exceeds this; 0 = never (default 5e-6) */
   int check_every;    /* BDU_MIXED: updates between orthogonality estimates (default 10) */

@@ -578,6 +578,7 @@ bdu_status tune_side(bdu_ctx *h, int side, int sm_reserve) {
   } else {
     for (int v = 1; v <= 4; v++) cand.push_back(v);
     cand.push_back(kSlabVariant);
+    for (int v : {64, 96, 128}) cand.push_back(v);
   }
   const size_t bytes = esize(h) * (size_t)dim * dim;
   void *scratch = dev_alloc(h, bytes);
@@ -758,7 +759,10 @@ bool ensure_pipeline(bdu_ctx *h) {
   if (!h->stb[1].La) {
     h->stb[0] = h->st;
     h->cur = 0;
-    if (!alloc_records(h, h->stb[1], h->st.T, h->st.cap, h->m, h->opt.precision == BDU_MIXED)) {
+    const bool got = alloc_records(h, h->stb[1], h->st.T, h->st.cap, h->m, h->opt.precision == BDU_MIXED);
+    h->stb[1].tc_ws = h->st.tc_ws;  // the applications of the two buffers run on one stream
+    h->stb[1].tc_ws_bytes = h->st.tc_ws_bytes;
+    if (!got) {
       for (void *p : {(void *)h->stb[1].Lc, (void *)h->stb[1].Ls, (void *)h->stb[1].Rc, (void *)h->stb[1].Rs,
                       (void *)h->stb[1].La, (void *)h->stb[1].Ra, (void *)h->stb[1].Ln, (void *)h->stb[1].Rn,
                       (void *)h->stb[1].Sc, (void *)h->stb[1].Ss, (void *)h->stb[1].Sa, (void *)h->stb[1].Sn,
@@ -1152,7 +1156,8 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown engine %d", o.engine);
   if (o.step_budget < 0) return fail(nullptr, BDU_EINVAL, "bdu_create: negative step budget");
   if (o.reorth_every < -1) return fail(nullptr, BDU_EINVAL, "bdu_create: reorth_every below -1");
-  if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1)) : (o.nb < 0 || o.nb > kSlabVariant))
+  if (o.precision == BDU_FP64 ? (o.nb < 0 || o.nb > 64 || (o.nb & 1))
+                               : (o.nb < 0 || (o.nb > kSlabVariant && !is_tc_variant(o.nb))))
     return fail(nullptr, BDU_EINVAL, "bdu_create: unknown apply variant nb=%d", o.nb);
   if (!all_finite(Q, m * m) || !all_finite(P, n * n) || !all_finite(d, n) || (n > 1 && !all_finite(e, n - 1)))
     return fail(nullptr, BDU_EINVAL, "bdu_create: non-finite value in Q, d, e or P");
@@ -1190,10 +1195,20 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->band = (double *)dev_alloc(h, sizeof(double) * band_doubles(m, n));
   const bool mixed = o.precision == BDU_MIXED;
   bool rec_ok = alloc_records(h, h->st, T, cap, m, mixed);
+  if (mixed) {
+    // the blocked tensor-core apply's workspace, for every block order and both factors
+    size_t tcb = 0;
+    for (int nb : {64, 96, 128}) tcb = std::max(tcb, tc_workspace_bytes((int)m, T, nb));
+    h->st.tc_ws = dev_alloc(h, tcb);
+    h->st.tc_ws_bytes = h->st.tc_ws ? tcb : 0;
+    rec_ok = rec_ok && h->st.tc_ws;
+  }
   h->ovl = mixed && o.overlap != 0 && rotate_vectors_supported((int)m, (int)n);
   if (h->ovl) {
     h->stb[0] = h->st;
     rec_ok = rec_ok && alloc_records(h, h->stb[1], T, cap, m, mixed);
+    h->stb[1].tc_ws = h->st.tc_ws;  // the applications of the two buffers never overlap
+    h->stb[1].tc_ws_bytes = h->st.tc_ws_bytes;
     // The chase's thread-block cluster needs 16 free SMs of one GPC: its
     // stream outranks the application's, so that when both become ready the
     // chase is placed first and the application fills the other SMs.

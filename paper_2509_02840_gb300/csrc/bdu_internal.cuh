@@ -68,6 +68,8 @@ struct RotStream {
   float2 *Lf, *Rf, *Sf;
   int p1;         // chases 0..p1-1 are phase-1 chases (pairs two columns apart)
   int4 *Lm, *Rm;  // per-chase descriptors for the register-resident FP32 apply (T each), or null
+  void *tc_ws;    // workspace of the blocked tensor-core apply (mixed form), or null
+  size_t tc_ws_bytes;
 };
 
 // Number of chases of the schedule for an m x n problem.
@@ -128,7 +130,11 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 // kernel.  cudaErrorNotSupported when the variant does not cover the shape.
 // gate (slab kernel only; may be null): a device error word; when an earlier
 // kernel on the stream has made it nonzero, X is left untouched.
+// Mixed form, variant 64, 96 or 128: the blocked tensor-core apply with blocks
+// of that order (st.tc_ws must be set); variant 0 uses it (order 128) when no
+// register layout covers the shape.
 constexpr int kSlabVariant = 5;
+inline bool is_tc_variant(int v) { return v == 64 || v == 96 || v == 128; }
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s,
                          int *status = nullptr, int sm_reserve = 0, bool desc_ready = false,
@@ -145,6 +151,16 @@ cudaError_t launch_apply_reg(float *X, int64_t ld, int nrow, int ncol, const Rot
                              bool with_spike, int *status, int sm_reserve, bool desc_ready, int layout,
                              cudaStream_t s);
 cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t s);
+cudaError_t launch_apply_spike32(float *X, int64_t ld, int nrow, const RotStream &st, cudaStream_t s);
+// The blocked tensor-core apply (mixed form): the rotations of nb/2
+// consecutive chases accumulated into nb x nb orthogonal blocks and applied to
+// the FP32 factor with tcgen05 3xTF32 MMAs.  nb in {64, 96, 128}; ws holds
+// tc_workspace_bytes(ncol, T, nb) bytes.  cudaErrorNotSupported when the
+// shape or nb is not covered (nothing launched then).
+size_t tc_workspace_bytes(int ncol, int T, int nb);
+cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
+                            bool with_spike, int *status, bool desc_ready, int nb, void *ws, size_t ws_bytes,
+                            cudaStream_t s);
 bool rotate_vectors_supported(int m, int n);
 cudaError_t launch_rotate_vectors(const double *w_left, double *dst_left, int m, const double *w_right,
                                   double *dst_right, int n, const RotStream &st, bool with_spike, int *status,

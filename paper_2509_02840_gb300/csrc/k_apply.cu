@@ -252,10 +252,18 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status,
                          int sm_reserve, bool desc_ready, int variant, const int *gate) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
+  if (precision == BDU_MIXED && is_tc_variant(variant))
+    return launch_apply_tc((float *)X, ld, nrow, ncol, st, side, with_spike, status, desc_ready, variant, st.tc_ws,
+                           st.tc_ws_bytes, s);
   if (precision == BDU_MIXED && variant != kSlabVariant) {
-    const cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, sm_reserve,
-                                           desc_ready, variant, s);
+    cudaError_t e = launch_apply_reg((float *)X, ld, nrow, ncol, st, side, with_spike, status, sm_reserve,
+                                     desc_ready, variant, s);
     if (e != cudaErrorNotSupported || variant != 0) return e;
+    // no register layout covers the shape: the blocked tensor-core apply
+    e = launch_apply_tc((float *)X, ld, nrow, ncol, st, side, with_spike, status, desc_ready, 128, st.tc_ws,
+                        st.tc_ws_bytes, s);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
   }
   int dev = 0, optin = 0, sms = 1;
   cudaGetDevice(&dev);

@@ -460,6 +460,13 @@ struct RegLaunch {
 
 }  // namespace
 
+// The spike chain (m > n) of st applied to the FP32 rows of X, one thread per row.
+cudaError_t launch_apply_spike32(float *X, int64_t ld, int nrow, const RotStream &st, cudaStream_t s) {
+  if (!st.Sf) return cudaErrorInvalidValue;
+  k_apply_spike32<<<(nrow + 127) / 128, 128, 0, s>>>(X, ld, nrow, st.Sf, st.Sa, st.Sn);
+  return cudaGetLastError();
+}
+
 // Per-chase descriptors of one side of st (see k_chase_descriptors).
 cudaError_t launch_chase_descriptors(const RotStream &st, int side, cudaStream_t s) {
   int4 *desc = side == 0 ? st.Lm : st.Rm;

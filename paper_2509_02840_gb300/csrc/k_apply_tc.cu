@@ -1,0 +1,475 @@
+// K4, mixed form: blocked application of the rotation stream of one rank-1
+// column on the tensor cores (Sec. 3.2, Eq. bidiagplus: Q+ = Q Q1, P+ = P P1,
+// with Q1, P1 the products of the left and right rotations).
+//
+// Tiling.  Chase t's rotations act on disjoint column pairs (a, a+1), and a
+// rotation of chase t depends only on rotations of earlier chases that share
+// a column with it (|a - a'| <= 1).  The chases are cut into bands of K
+// consecutive chases; inside a band, the rotation of local chase i on the pair
+// starting at column a belongs to tile j = floor((a + i + 1) / W): a window of
+// W pair starts that moves one column to the left per chase (a
+// parallelogram).  With that slope every rotation's predecessors lie in its
+// own tile or in tiles to its left, and no rotation of tile j+1 precedes one
+// of tile j, so applying the tiles left to right, each tile's rotations in
+// chase order, gives the sequential result.  Tile j touches the NB = W + K
+// columns [j W - K, j W + W); its rotations compose into an NB x NB
+// orthogonal block G_j (formed by applying them, in order, to the identity),
+// and the tile is applied as the product X(:, cols) <- X(:, cols) G_j.
+// Consecutive tiles of a band overlap in K columns: the last K columns of one
+// product are the first K inputs of the next, and the first W are final.
+//
+// Kernels, per band: k_tc_form builds the band's blocks (one thread block per
+// tile, one thread per row of G, in shared memory) and writes each as the
+// tensor cores' B operand, split into two TF32 parts; k_tc_apply then gives
+// each panel of 128 rows of X to one thread block, which walks the band's
+// tiles left to right: a row thread per TMEM lane holds its row's inputs
+// [carry | W new columns], split into TF32 hi and lo parts, in tensor memory
+// (the A operand), one thread issues tcgen05.mma (kind::tf32, M = 128,
+// N = NB, accumulator in tensor memory) with B streamed into shared memory by
+// bulk copies, and the row threads read the accumulator back (tcgen05.ld),
+// store its first W columns and carry the last K into the next tile.
+//
+// Arithmetic: 3xTF32 with FP32 accumulation, D = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi, where x_hi = x rounded to TF32 (nearest) and x_lo = x - x_hi
+// (exact in FP32); the blocks themselves are formed in FP32 with the
+// generator's FP32 coefficients (x' = fma(c, x, s y), y' = fma(c, y, -s x)).
+// Results agree with the rotation-by-rotation FP32 apply to FP32 rounding
+// (not bit for bit).
+//
+// Every wait is bounded; one that runs out sets ERR_APPLY, the kernel stops
+// issuing work, waits (bounded) for what it has in flight, frees its tensor
+// memory and returns.
+#include <climits>
+
+#include "async_copy.cuh"
+#include "bdu_internal.cuh"
+
+namespace bdu {
+namespace {
+
+constexpr int kRows = 128;          // rows of a panel: the MMA's M and the TMEM lanes
+constexpr int kApplyThreads = 160;  // four row warps + the MMA warp
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColD = 0, kColAH = 128, kColAL = 256;  // accumulator, A hi, A lo (TMEM columns)
+constexpr int kEmpty = 7;           // descriptor code of a chase without rotations
+constexpr unsigned kCopyChunk = 16384;
+
+// ---------------------------------------------------------------------------
+// tcgen05 primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// 32 lanes x 16 consecutive 32-bit columns: lane t of the warp <-> TMEM lane
+// (taddr's lane + t)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+// D (TMEM) (+)= A (TMEM) * B (shared memory, descriptor), kind::tf32
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d),
+      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// arrives on bar once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
+               : "memory");
+}
+// Shared-memory matrix descriptor, no swizzle: start, leading-dimension
+// (K-direction core-matrix) and stride-dimension (M/N-direction 8-row group)
+// byte offsets; descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo exact
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// first index e in [0, cnt) with v[e] >= key (v ascending)
+__device__ __forceinline__ int lower_bound(const int32_t *__restrict__ v, int cnt, int key) {
+  int lo = 0, hi = cnt;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// per-band tile ranges
+// ---------------------------------------------------------------------------
+// ranges[b] = (first, last) tile of band b, or (0, -1) when the band has no
+// rotation.  desc: the per-chase descriptors (z, w = first columns of the
+// chase's first and last pairs, 0-based).
+__global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, int W, int nbands,
+                                 int2 *__restrict__ ranges) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbands) return;
+  int lo = INT_MAX, hi = INT_MIN;
+  for (int i = 0; i < K; i++) {
+    const int t = b * K + i;
+    if (t >= T) break;
+    const int4 d = desc[t];
+    if ((d.y >> 24) == kEmpty) continue;
+    lo = min(lo, (d.z + i + 1) / W);
+    hi = max(hi, (d.w + i + 1) / W);
+  }
+  ranges[b] = lo <= hi ? make_int2(lo, hi) : make_int2(0, -1);
+}
+
+// ---------------------------------------------------------------------------
+// the blocks of one band
+// ---------------------------------------------------------------------------
+// Block x forms tile j = first + x of band b.  Thread r owns row r of G,
+// G(r, c) at Gs[c * S + r] (rows of one column contiguous: conflict-free),
+// starting from the identity; each rotation of the tile updates two entries
+// of every row, so the threads never share data until the output.  Output:
+// blob x = [hi | lo], each the NB x NB block as the MMA's B operand (K = the
+// row index of G, N = its column index), K-major without swizzle: core matrix
+// (n / 8, k / 4) of 8 rows (n) x 16 bytes (4 k) at byte
+// ((n / 8) * (NB / 4) + k / 4) * 128, so the 16-byte chunks are written in
+// order.
+template <int NB>
+__global__ void __launch_bounds__(NB) k_tc_form(const int32_t *__restrict__ Ca, const float2 *__restrict__ Cf,
+                                                const int4 *__restrict__ desc, int T, int cap, int b,
+                                                const int2 *__restrict__ ranges, float *__restrict__ blobs,
+                                                int *__restrict__ status) {
+  constexpr int K = NB / 2, W = NB / 2, S = NB + 4;
+  extern __shared__ __align__(16) float Gs[];
+  const int2 rg = ranges[b];
+  const int j = rg.x + (int)blockIdx.x;
+  if (j > rg.y) return;
+  const int r = threadIdx.x;
+  for (int c = 0; c < NB; c++) Gs[c * S + r] = (c == r) ? 1.f : 0.f;
+  const int base = j * W - K;  // column of X that is column 0 of the tile
+  for (int i = 0; i < K; i++) {
+    const int t = b * K + i;
+    if (t >= T) break;
+    const int4 d = desc[t];
+    const int cnt = d.y & 0xffffff, code = d.y >> 24;
+    if (code == kEmpty) continue;
+    const int lo = j * W - 1 - i, hi = lo + W;  // this tile's pair starts in chase t
+    if (d.w < lo || d.z >= hi) continue;
+    const size_t rb = (size_t)t * cap;
+    int e0, e1, step = 0;
+    if (code < 5) {
+      // gap-free: record e starts at column d.z + step * e
+      step = code < 2 ? 2 : 3;
+      e0 = lo <= d.z ? 0 : (lo - d.z + step - 1) / step;
+      e1 = min(cnt, (hi - d.z + step - 1) / step);
+    } else {
+      e0 = lower_bound(Ca + rb, cnt, lo + 1);  // Ca holds 1-based pair starts
+      e1 = lower_bound(Ca + rb, cnt, hi + 1);
+    }
+    for (int e = e0; e < e1; e++) {
+      const int l = (code < 5 ? d.z + step * e : Ca[rb + e] - 1) - base;
+      if (l < 0 || l > NB - 2) {
+        if (r == 0) atomicOr(status, ERR_RANGE);
+        continue;
+      }
+      const float2 g = Cf[rb + e];
+      float *px = Gs + l * S + r;
+      const float x = px[0], y = px[S];
+      px[0] = fmaf(g.x, x, g.y * y);
+      px[S] = fmaf(g.x, y, -g.y * x);
+    }
+  }
+  __syncthreads();
+  uint4 *oh = reinterpret_cast<uint4 *>(blobs + (size_t)blockIdx.x * 2 * NB * NB);
+  uint4 *ol = oh + NB * NB / 4;
+  for (int idx = r; idx < NB * NB / 4; idx += NB) {
+    const int r8 = idx & 7, kc = (idx >> 3) % (NB / 4), ng = (idx >> 3) / (NB / 4);
+    const float4 v = *reinterpret_cast<const float4 *>(Gs + (ng * 8 + r8) * S + 4 * kc);
+    uint4 h, l;
+    split_tf32(v.x, h.x, l.x);
+    split_tf32(v.y, h.y, l.y);
+    split_tf32(v.z, h.z, l.z);
+    split_tf32(v.w, h.w, l.w);
+    oh[idx] = h;
+    ol[idx] = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the products of one band
+// ---------------------------------------------------------------------------
+// Row thread r (warps 0-3) <-> panel row r <-> TMEM lane r.  Tensor memory:
+// D (the accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo at
+// [256, 256 + NB); A's columns [0, K) hold the carry, [K, NB) the tile's W new
+// columns.  Shared memory: the tile's B blob.  Barriers (one phase per tile):
+// bar_b (the blob has landed), bar_a (the four row warps have written A),
+// bar_m (the tile's MMAs have completed; also frees the blob's buffer).
+// v (n columns of this thread's row) into A hi / A lo at column col0
+template <int N>
+__device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, int col0, const float (&v)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; c += 16) {
+    uint32_t h[16], l[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) split_tf32(v[c + q], h[q], l[q]);
+    tmem_st16(tm + lane_off + kColAH + col0 + c, h);
+    tmem_st16(tm + lane_off + kColAL + col0 + c, l);
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kApplyThreads, 1)
+    k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
+               const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
+  constexpr int K = NB / 2, W = NB / 2;
+  constexpr uint32_t kBlob = 2u * NB * NB * 4u;
+  extern __shared__ __align__(1024) unsigned char sB[];
+  __shared__ uint64_t bar_b, bar_a, bar_m;
+  __shared__ uint32_t tmem_s;
+  __shared__ volatile int dead;
+  const int2 rg = ranges[b];
+  if (rg.y < rg.x) return;  // no rotation in this band (the same for the whole block)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = rg.y - rg.x + 1;
+  if (warp == 0) {
+    tmem_alloc(&tmem_s, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 32) {
+    async::mbar_init(&bar_b, 1);
+    async::mbar_init(&bar_a, 4);
+    async::mbar_init(&bar_m, 1);
+    async::mbar_init_fence();
+    dead = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = tmem_s;
+
+  if (warp == 4) {
+    // ---- MMA warp (one thread): per tile, the blob into shared memory, then
+    // 3 x NB/8 MMAs once the row warps have written A
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kRows, NB);
+      constexpr uint32_t sbo = (NB / 4) * 128;
+      const uint32_t bh = su32(sB), bl = bh + NB * NB * 4;
+      int committed = 0;
+      bool copy_pending = false;
+      for (int q = 0; q < ntiles && !dead; q++) {
+        if (q > 0 && !async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
+          atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        async::mbar_arrive_tx(&bar_b, kBlob);
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(blobs) + (size_t)q * kBlob;
+        for (uint32_t o = 0; o < kBlob; o += kCopyChunk)
+          async::bulk_g2s(sB + o, src + o, kBlob - o < kCopyChunk ? kBlob - o : kCopyChunk, &bar_b);
+        copy_pending = true;
+        if (!async::mbar_wait(&bar_b, (unsigned)(q & 1))) {
+          atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        copy_pending = false;
+        if (!async::mbar_wait(&bar_a, (unsigned)(q & 1))) {
+          atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll 1
+        for (int s = 0; s < NB / 8; s++) {
+          const uint64_t dh = smem_desc(bh + 256u * s, 128u, sbo), dl = smem_desc(bl + 256u * s, 128u, sbo);
+          mma_tf32(tm + kColD, tm + kColAH + 8 * s, dh, idesc, s > 0 ? 1u : 0u);
+          mma_tf32(tm + kColD, tm + kColAH + 8 * s, dl, idesc, 1u);
+          mma_tf32(tm + kColD, tm + kColAL + 8 * s, dh, idesc, 1u);
+        }
+        mma_commit(&bar_m);
+        committed = q + 1;
+      }
+      // nothing of this thread stays in flight: the last copy and MMAs
+      if (copy_pending) async::mbar_wait(&bar_b, (unsigned)((committed) & 1));
+      if (committed > 0 && dead) async::mbar_wait(&bar_m, (unsigned)((committed - 1) & 1));
+    }
+  } else {
+    // ---- row warps
+    const int row = (int)blockIdx.x * kRows + tid;
+    const bool rv = row < nrow;
+    const float *xr = X + (rv ? row : 0);  // read: columns no earlier tile of the band has written
+    float *xw = X + (rv ? row : 0);
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    for (int q = 0; q < ntiles; q++) {
+      if (dead) break;
+      const int j = rg.x + q;
+      float nv[W], cv[K];
+      // the tile's new columns [j W, j W + W), read before waiting on the
+      // previous tile
+#pragma unroll
+      for (int c = 0; c < W; c++) {
+        const int col = j * W + c;
+        nv[c] = (rv && col < ncol) ? xr[(size_t)col * ld] : 0.f;
+      }
+      if (q == 0) {
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+          const int col = j * W - K + c;
+          cv[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
+        }
+      } else {
+        if (!async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
+          if (lane == 0) atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        tc_fence_after();
+        // the previous tile's first W outputs are final: columns [(j-1) W - K, ...)
+        const int g0 = (j - 1) * W - K;
+#pragma unroll
+        for (int c = 0; c < W; c += 16) {
+          uint32_t v[16];
+          tmem_ld16(tm + lane_off + kColD + c, v);
+          tc_wait_ld();
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) {
+            const int col = g0 + c + qq;
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = __uint_as_float(v[qq]);
+          }
+        }
+        // its last K outputs are this tile's first K inputs
+#pragma unroll
+        for (int c = 0; c < K; c += 16) {
+          uint32_t v[16];
+          tmem_ld16(tm + lane_off + kColD + W + c, v);
+          tc_wait_ld();
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) cv[c + qq] = __uint_as_float(v[qq]);
+        }
+      }
+      st_split_cols<K>(tm, lane_off, 0, cv);
+      st_split_cols<W>(tm, lane_off, K, nv);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) async::mbar_arrive(&bar_a);
+    }
+    if (!dead) {
+      if (!async::mbar_wait(&bar_m, (unsigned)((ntiles - 1) & 1))) {
+        if (lane == 0) atomicOr(status, ERR_APPLY);
+        dead = 1;
+      } else {
+        tc_fence_after();
+        const int g0 = rg.y * W - K;  // the last tile's columns, all final
+#pragma unroll 1
+        for (int c = 0; c < NB; c += 16) {
+          uint32_t v[16];
+          tmem_ld16(tm + lane_off + kColD + c, v);
+          tc_wait_ld();
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) {
+            const int col = g0 + c + qq;
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = __uint_as_float(v[qq]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, kTmemCols);
+}
+
+template <int NB>
+cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side, int *status,
+                      int2 *ranges, float *blobs, int nbands, int max_tiles, cudaStream_t s) {
+  const int32_t *Ca = side == 0 ? st.La : st.Ra;
+  const float2 *Cf = side == 0 ? st.Lf : st.Rf;
+  const int4 *desc = side == 0 ? st.Lm : st.Rm;
+  const size_t form_smem = (size_t)NB * (NB + 4) * 4;
+  const size_t apply_smem = (size_t)2 * NB * NB * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_form<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)form_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_apply<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
+  if (e != cudaSuccess) return e;
+  const int panels = (nrow + kRows - 1) / kRows;
+  for (int b = 0; b < nbands; b++) {
+    k_tc_form<NB><<<max_tiles, NB, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
+    k_tc_apply<NB><<<panels, kApplyThreads, apply_smem, s>>>(X, ld, nrow, ncol, blobs, ranges, b, status);
+  }
+  return cudaGetLastError();
+}
+
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+// Workspace of the blocked apply: the band ranges, then one band's blobs.
+// A band's tiles j run over floor((a + i + 1) / W) for pair starts a in
+// [0, ncol - 2] and i < K: at most (ncol + K) / W + 1 of them.
+size_t tc_workspace_bytes(int ncol, int T, int nb) {
+  const int K = nb / 2, W = nb / 2;
+  const int nbands = (T + K - 1) / K;
+  const int max_tiles = (ncol + K) / W + 2;
+  return align256((size_t)(nbands + 1) * sizeof(int2)) + (size_t)max_tiles * 2 * nb * nb * 4;
+}
+
+cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
+                            bool with_spike, int *status, bool desc_ready, int nb, void *ws, size_t ws_bytes,
+                            cudaStream_t s) {
+  const int4 *desc = side == 0 ? st.Lm : st.Rm;
+  const float2 *coef = side == 0 ? st.Lf : st.Rf;
+  if ((nb != 64 && nb != 96 && nb != 128) || !desc || !coef || !status || !ws || nrow < 1 || ncol < 2 ||
+      ws_bytes < tc_workspace_bytes(ncol, st.T, nb))
+    return cudaErrorNotSupported;
+  cudaError_t e = cudaSuccess;
+  if (st.T > 0 && !desc_ready) e = launch_chase_descriptors(st, side, s);
+  if (e == cudaSuccess && with_spike) e = launch_apply_spike32(X, ld, nrow, st, s);
+  if (e != cudaSuccess || st.T <= 0) return e;
+  const int K = nb / 2, W = nb / 2;
+  const int nbands = (st.T + K - 1) / K;
+  const int max_tiles = (ncol + K) / W + 2;
+  int2 *ranges = reinterpret_cast<int2 *>(ws);
+  float *blobs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ws) +
+                                           align256((size_t)(nbands + 1) * sizeof(int2)));
+  k_tc_band_ranges<<<(nbands + 127) / 128, 128, 0, s>>>(desc, st.T, K, W, nbands, ranges);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (nb == 64) return run_bands<64>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
+  if (nb == 96) return run_bands<96>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
+  return run_bands<128>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
+}
+
+}  // namespace bdu

@@ -65,6 +65,7 @@ def reserve_bytes(m, n, precision, max_rank=4):
     if precision == bdu.MIXED:
         b += 8 * m * m + 8 * (m + 1) + 32 * (T + 1)       # FP64 scratch, spike copies, chase descriptors
         b += 16 * m * m                                   # re-orthogonalization workspace
+        b += ((m + 64) // 64 + 2) * 2 * 128 * 128 * 4 + 8 * (T // 32 + 2) + 512  # blocked-apply workspace
     return b
 
 

@@ -1,0 +1,89 @@
+"""The blocked tensor-core apply (mixed form, nb = 64, 96, 128): the rotations
+of nb/2 consecutive chases over a window of nb/2 columns are accumulated into
+an nb x nb orthogonal block and applied as a 3xTF32 product on the tensor
+cores (Sec. 3.2, Eq. bidiagplus).  It rounds differently from the
+rotation-by-rotation FP32 apply, so it is compared with the FP64 oracle within
+the mixed form's tolerances, and with the register-resident apply within FP32
+rounding; the bidiagonal it leaves behind is the chase's, and so identical to
+the other variants' after one update."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_02840_gb300 import bdu, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(Q, d, e, P, ups, nb, overlap=False):
+    with bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, nb=nb, overlap=overlap) as F:
+        out = []
+        for B, C in ups:
+            F.update(B, C)
+            out.append(F.read())
+        st = F.stats()
+    return out, st
+
+
+@pytest.mark.parametrize("nb", [64, 96, 128])
+@pytest.mark.parametrize("m,n", [(256, 256), (300, 200), (777, 500), (130, 129), (65, 3)])
+def test_one_update_matches_the_oracle(m, n, nb):
+    Q, d, e, P = I.factorization(m, n, config=0, which=7)
+    B, C = I.dense_update(m, n, 3, config=0)
+    (got,), st = _run(Q, d, e, P, [(B, C)], nb)
+    assert st["apply_variant"] == [nb, nb]
+    Qo, do, eo, Po, _ = O.update(Q, d, e, P, B, C)
+    Qg, dg, eg, Pg = got
+    # the same FP64 chase on the same (FP32-rounded) projections as nb = 1
+    (ref,), _ = _run(Q, d, e, P, [(B, C)], 1)
+    assert np.array_equal(dg, ref[1]) and np.array_equal(eg, ref[2])
+    # factors: within FP32 rounding of the FP64 oracle and of the register apply
+    assert np.max(np.abs(Qg - Qo)) <= 2e-5 and np.max(np.abs(Pg - Po)) <= 2e-5
+    assert np.max(np.abs(Qg - ref[0])) <= 2e-5 and np.max(np.abs(Pg - ref[3])) <= 2e-5
+    for X in (Qg, Pg):
+        assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
+
+
+@pytest.mark.parametrize("nb", [64, 128])
+def test_stream_keeps_the_mixed_tolerances(nb):
+    """Twelve rank-1 updates and one rank-3 update (the rank-r pipeline) with
+    the default re-orthogonalization cadence: residual against A+ accumulated
+    in FP64, singular values against LAPACK's, orthogonality."""
+    m, n = 600, 450
+    Q, d, e, P = I.factorization(m, n, config=0, which=8)
+    ups = [I.dense_update(m, n, h, config=0) for h in range(12)] + [I.dense_update(m, n, 99, config=0, r=3)]
+    outs, st = _run(Q, d, e, P, ups, nb)
+    Qg, dg, eg, Pg = outs[-1]
+    A = Q @ O.bidiag_dense(d, e, m) @ P.T
+    for B, C in ups:
+        A += B @ C.T
+    R = Qg @ O.bidiag_dense(dg, eg, m) @ Pg.T
+    # FP32 rounding budget of 15 rank-1 columns at this size (the register
+    # apply leaves about 6e-6 here)
+    assert np.linalg.norm(A - R) / np.linalg.norm(A) <= 3e-5
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    s_got = np.linalg.svd(O.bidiag_dense(dg, eg, m), compute_uv=False)
+    assert np.max(np.abs(s_ref - s_got)) <= 1e-5 * s_ref[0]
+    for X in (Qg, Pg):
+        assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
+
+
+def test_overlapped_form_with_the_blocked_apply():
+    m = n = 512
+    Q, d, e, P = I.factorization(m, n, config=1, which=2)
+    ups = [I.recommender_update(m, n, h, config=1) for h in range(6)]
+    a, _ = _run(Q, d, e, P, ups, 128, overlap=True)
+    b, _ = _run(Q, d, e, P, ups, 1, overlap=True)
+    for x, y in zip(a[-1], b[-1]):
+        assert np.max(np.abs(x - y)) <= 1e-4 * max(1.0, np.max(np.abs(y)))
+
+
+def test_autotuner_may_pick_the_blocked_apply_and_results_stay_within_tolerance():
+    m = n = 1024
+    Q, d, e, P = I.factorization(m, n, config=1, which=3)
+    ups = [I.recommender_update(m, n, h, config=1) for h in range(3)]
+    outs, st = _run(Q, d, e, P, ups, 0)
+    assert st["tunings"] >= 1
+    Qg, dg, eg, Pg = outs[-1]
+    for X in (Qg, Pg):
+        assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
