@@ -137,8 +137,10 @@ __device__ __forceinline__ int lower_bound(const int32_t *__restrict__ v, int cn
 // ranges[b] = (first, last) tile of band b, or (0, -1) when the band has no
 // rotation.  desc: the per-chase descriptors (z, w = first columns of the
 // chase's first and last pairs, 0-based).
-__global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, int W, int nbands,
-                                 int2 *__restrict__ ranges) {
+// A band whose range would exceed max_tiles (only possible with corrupt
+// descriptors) is reported (ERR_RANGE) and skipped.
+__global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, int W, int nbands, int max_tiles,
+                                 int2 *__restrict__ ranges, int *__restrict__ status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbands) return;
   int lo = INT_MAX, hi = INT_MIN;
@@ -149,6 +151,11 @@ __global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, in
     if ((d.y >> 24) == kEmpty) continue;
     lo = min(lo, (d.z + i + 1) / W);
     hi = max(hi, (d.w + i + 1) / W);
+  }
+  if (lo <= hi && (lo < 0 || hi - lo + 1 > max_tiles)) {
+    atomicOr(status, ERR_RANGE);
+    lo = 0;
+    hi = -1;
   }
   ranges[b] = lo <= hi ? make_int2(lo, hi) : make_int2(0, -1);
 }
@@ -464,7 +471,7 @@ cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotS
   int2 *ranges = reinterpret_cast<int2 *>(ws);
   float *blobs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ws) +
                                            align256((size_t)(nbands + 1) * sizeof(int2)));
-  k_tc_band_ranges<<<(nbands + 127) / 128, 128, 0, s>>>(desc, st.T, K, W, nbands, ranges);
+  k_tc_band_ranges<<<(nbands + 127) / 128, 128, 0, s>>>(desc, st.T, K, W, nbands, max_tiles, ranges, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (nb == 64) return run_bands<64>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
