@@ -33,8 +33,10 @@
 // A_lo B_hi, where x_hi = x rounded to TF32 (nearest) and x_lo = x - x_hi
 // (exact in FP32); the blocks themselves are formed in FP32 with the
 // generator's FP32 coefficients (x' = fma(c, x, s y), y' = fma(c, y, -s x)).
-// Results agree with the rotation-by-rotation FP32 apply to FP32 rounding
-// (not bit for bit).
+// Each output row is then scaled back to its input norm over the tile (G is
+// orthogonal; the tensor cores' accumulation truncates toward zero, a bias
+// that would otherwise add up over the bands).  Results agree with the
+// rotation-by-rotation FP32 apply to FP32 rounding (not bit for bit).
 //
 // Every wait is bounded; one that runs out sets ERR_APPLY, the kernel stops
 // issuing work, waits (bounded) for what it has in flight, frees its tensor
@@ -255,6 +257,30 @@ __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, in
   }
 }
 
+// Row-norm restoration.  G is orthogonal, so each row's 2-norm over the
+// tile's NB columns is the same before and after the product; the tensor
+// cores' FP32 accumulation truncates toward zero and shrinks it by about one
+// unit in the last place per MMA step.  The row's outputs are scaled back to
+// its input norm (in2 = its squared input norm): the factor is 1 up to that
+// bias, and without it the bias would add up over the bands of every update.
+template <int NB>
+__device__ __forceinline__ float norm_restore_n(uint32_t dcol, float in2) {
+  float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < NB; c += 16) {
+    uint32_t v[16];
+    tmem_ld16(dcol + c, v);
+    tc_wait_ld();
+#pragma unroll
+    for (int qq = 0; qq < 16; qq += 2) {
+      o0 = fmaf(__uint_as_float(v[qq]), __uint_as_float(v[qq]), o0);
+      o1 = fmaf(__uint_as_float(v[qq + 1]), __uint_as_float(v[qq + 1]), o1);
+    }
+  }
+  const float o2 = o0 + o1;
+  return (o2 > 0.f && in2 > 0.f) ? sqrtf(in2 / o2) : 1.f;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kApplyThreads, 1)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
@@ -338,6 +364,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     const float *xr = X + (rv ? row : 0);  // read: columns no earlier tile of the band has written
     float *xw = X + (rv ? row : 0);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t dcol = tm + lane_off + kColD;
+    float in2 = 0.f;  // squared norm of this row's inputs to the tile in flight
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
@@ -362,29 +390,36 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
           break;
         }
         tc_fence_after();
+        const float sc = norm_restore_n<NB>(dcol, in2);
         // the previous tile's first W outputs are final: columns [(j-1) W - K, ...)
         const int g0 = (j - 1) * W - K;
 #pragma unroll
         for (int c = 0; c < W; c += 16) {
           uint32_t v[16];
-          tmem_ld16(tm + lane_off + kColD + c, v);
+          tmem_ld16(dcol + c, v);
           tc_wait_ld();
 #pragma unroll
           for (int qq = 0; qq < 16; qq++) {
             const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = __uint_as_float(v[qq]);
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * __uint_as_float(v[qq]);
           }
         }
         // its last K outputs are this tile's first K inputs
 #pragma unroll
         for (int c = 0; c < K; c += 16) {
           uint32_t v[16];
-          tmem_ld16(tm + lane_off + kColD + W + c, v);
+          tmem_ld16(dcol + W + c, v);
           tc_wait_ld();
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) cv[c + qq] = __uint_as_float(v[qq]);
+          for (int qq = 0; qq < 16; qq++) cv[c + qq] = sc * __uint_as_float(v[qq]);
         }
       }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < K; c++) s0 = fmaf(cv[c], cv[c], s0);
+#pragma unroll
+      for (int c = 0; c < W; c++) s1 = fmaf(nv[c], nv[c], s1);
+      in2 = s0 + s1;
       st_split_cols<K>(tm, lane_off, 0, cv);
       st_split_cols<W>(tm, lane_off, K, nv);
       tc_wait_st();
@@ -398,16 +433,17 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         dead = 1;
       } else {
         tc_fence_after();
+        const float sc = norm_restore_n<NB>(dcol, in2);
         const int g0 = rg.y * W - K;  // the last tile's columns, all final
 #pragma unroll 1
         for (int c = 0; c < NB; c += 16) {
           uint32_t v[16];
-          tmem_ld16(tm + lane_off + kColD + c, v);
+          tmem_ld16(dcol + c, v);
           tc_wait_ld();
 #pragma unroll
           for (int qq = 0; qq < 16; qq++) {
             const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = __uint_as_float(v[qq]);
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * __uint_as_float(v[qq]);
           }
         }
       }
