@@ -124,7 +124,9 @@ typedef struct {
                          of order k: FP32 rounding in the application moves
                          ||X^T X - I||_2 by about 3e-8 sqrt(k) per column (more in the
                          first), a step leaves ~1e-6, so the 1e-5 tolerance holds after
-                         every update.  Graph replay is used only when the cadence is
+                         every update; every column for a factor that the blocked
+                         tensor-core apply (nb = 64, 96, 128) updates, whose drift
+                         is about ten times larger.  Graph replay is used only when the cadence is
                          in the state the graph was captured in. */
 } bdu_options;
 

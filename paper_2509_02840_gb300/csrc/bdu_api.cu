@@ -311,11 +311,18 @@ int auto_cadence(int64_t k) {
 
 // The mixed form's unconditional re-orthogonalization: one Newton-Schulz step
 // on Q (P) behind the application of the first column and then of every
-// reorth_every-th (automatic: auto_cadence of its order), enqueued on s.
+// reorth_every-th (automatic: auto_cadence of its order, or every column for a
+// factor that the blocked tensor-core apply updates), enqueued on s.
 bdu_status reorth_after_column(bdu_ctx *h, cudaStream_t s) {
   if (h->opt.precision != BDU_MIXED || h->opt.reorth_every == 0) return BDU_OK;
   for (int which = 0; which < 2; which++) {
-    const int every = h->opt.reorth_every > 0 ? h->opt.reorth_every : auto_cadence(which == 0 ? h->m : h->n);
+    // The blocked apply's products drift the factor's column norms about ten
+    // times as fast as rotation-by-rotation FP32 application (the tensor
+    // cores' accumulation truncates toward zero); the step removes exactly
+    // that symmetric part of the error, so it follows every column there.
+    const int every = h->opt.reorth_every > 0            ? h->opt.reorth_every
+                      : is_tc_variant(h->apply_var[which]) ? 1
+                                                          : auto_cadence(which == 0 ? h->m : h->n);
     if (++h->cols_since_reorth[which] < every && h->reorth[which] > 0) continue;
     h->cols_since_reorth[which] = 0;
     const bdu_status st = reorth_factor(h, which, s);

@@ -11,15 +11,17 @@
 // parallelogram).  With that slope every rotation's predecessors lie in its
 // own tile or in tiles to its left, and no rotation of tile j+1 precedes one
 // of tile j, so applying the tiles left to right, each tile's rotations in
-// chase order, gives the sequential result.  Tile j touches the NB = W + K
-// columns [j W - K, j W + W); its rotations compose into an NB x NB
+// chase order, gives the sequential result (the argument holds for a grid
+// shifted by any o columns, tile j = floor((a + i + 1 + o) / W); the shift
+// changes from band to band, below).  Tile j touches the NB = W + K
+// columns [j W - K - o, j W + W - o); its rotations compose into an NB x NB
 // orthogonal block G_j (formed by applying them, in order, to the identity),
 // and the tile is applied as the product X(:, cols) <- X(:, cols) G_j.
 // Consecutive tiles of a band overlap in K columns: the last K columns of one
 // product are the first K inputs of the next, and the first W are final.
 //
 // Kernels, per band: k_tc_form builds the band's blocks (one thread block per
-// tile, one thread per row of G, in shared memory) and writes each as the
+// tile, four threads per row of G, in shared memory) and writes each as the
 // tensor cores' B operand, split into two TF32 parts; k_tc_apply then gives
 // each panel of 128 rows of X to one thread block, which walks the band's
 // tiles left to right: a row thread per TMEM lane holds its row's inputs
@@ -29,9 +31,11 @@
 // bulk copies, and the row threads read the accumulator back (tcgen05.ld),
 // store its first W columns and carry the last K into the next tile.
 //
-// Arithmetic: 3xTF32 with FP32 accumulation, D = A_hi B_hi + A_hi B_lo +
-// A_lo B_hi, where x_hi = x rounded to TF32 (nearest) and x_lo = x - x_hi
-// (exact in FP32); the blocks themselves are formed in FP32 with the
+// Arithmetic: 3xTF32 with FP32 accumulation, D = A_hi B_hi + (A_hi B_lo +
+// A_lo B_hi), where x_hi = x rounded to TF32 (nearest) and x_lo = x - x_hi,
+// also rounded to TF32; the two terms accumulate separately in tensor memory
+// (the accumulation truncates toward zero, so the large term sees only one
+// truncation per 8-deep MMA) and are added in FP32; the blocks themselves are formed in FP32 with the
 // generator's FP32 coefficients (x' = fma(c, x, s y), y' = fma(c, y, -s x)).
 // Each output row is then scaled back to its input norm over the tile (G is
 // orthogonal; the tensor cores' accumulation truncates toward zero, a bias
@@ -52,7 +56,9 @@ namespace {
 constexpr int kRows = 128;          // rows of a panel: the MMA's M and the TMEM lanes
 constexpr int kApplyThreads = 160;  // four row warps + the MMA warp
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColD = 0, kColAH = 128, kColAL = 256;  // accumulator, A hi, A lo (TMEM columns)
+// TMEM columns: the main accumulator (A_hi B_hi), A hi, A lo, the correction
+// accumulator (A_hi B_lo + A_lo B_hi)
+constexpr uint32_t kColD = 0, kColAH = 128, kColAL = 256, kColDC = 384;
 constexpr int kEmpty = 7;           // descriptor code of a chase without rotations
 constexpr unsigned kCopyChunk = 16384;
 
@@ -116,10 +122,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-// x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo exact
+// x ~ hi + lo: hi = x rounded to TF32 (nearest, ties away), lo = the exact
+// remainder x - hi rounded to TF32 the same way (so the tensor cores, which
+// read only TF32's bits, do not truncate it)
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
   asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
-  lo = __float_as_uint(x - __uint_as_float(hi));
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(lo) : "f"(x - __uint_as_float(hi)));
 }
 
 // first index e in [0, cnt) with v[e] >= key (v ascending)
@@ -133,6 +141,13 @@ __device__ __forceinline__ int lower_bound(const int32_t *__restrict__ v, int cn
   return lo;
 }
 
+// The tile grid of band b is shifted by o_b columns (tile j covers
+// [j W - K - o_b, j W + W - o_b)); the tiling argument holds for any shift.
+// Shifting it from band to band moves each column of X through every
+// position in a tile, so that the accumulation's residual error, which
+// depends on the position, does not pile up on the same columns.
+__host__ __device__ __forceinline__ int band_offset(int b, int W) { return (int)(((long long)b * 37) % W); }
+
 // ---------------------------------------------------------------------------
 // per-band tile ranges
 // ---------------------------------------------------------------------------
@@ -145,14 +160,15 @@ __global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, in
                                  int2 *__restrict__ ranges, int *__restrict__ status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbands) return;
+  const int o = band_offset(b, W);
   int lo = INT_MAX, hi = INT_MIN;
   for (int i = 0; i < K; i++) {
     const int t = b * K + i;
     if (t >= T) break;
     const int4 d = desc[t];
     if ((d.y >> 24) == kEmpty) continue;
-    lo = min(lo, (d.z + i + 1) / W);
-    hi = max(hi, (d.w + i + 1) / W);
+    lo = min(lo, (d.z + i + 1 + o) / W);
+    hi = max(hi, (d.w + i + 1 + o) / W);
   }
   if (lo <= hi && (lo < 0 || hi - lo + 1 > max_tiles)) {
     atomicOr(status, ERR_RANGE);
@@ -165,64 +181,124 @@ __global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, in
 // ---------------------------------------------------------------------------
 // the blocks of one band
 // ---------------------------------------------------------------------------
-// Block x forms tile j = first + x of band b.  Thread r owns row r of G,
-// G(r, c) at Gs[c * S + r] (rows of one column contiguous: conflict-free),
-// starting from the identity; each rotation of the tile updates two entries
-// of every row, so the threads never share data until the output.  Output:
-// blob x = [hi | lo], each the NB x NB block as the MMA's B operand (K = the
-// row index of G, N = its column index), K-major without swizzle: core matrix
-// (n / 8, k / 4) of 8 rows (n) x 16 bytes (4 k) at byte
+// Block x forms tile j = first + x of band b with kFormThreads threads: thread
+// (g, r) = (tid / NB, tid % NB) works on row r of G, G(r, c) at Gs[c * S + r]
+// (the rows of one column contiguous: a warp's accesses are conflict-free),
+// starting from the identity.  First the tile's rotations are gathered into
+// shared memory, chase by chase (rec = (column of the pair in the tile,
+// c, s)); then the chases are applied in order, separated by barriers, each
+// chase's rotations -- disjoint pairs -- dealt to the kFormGroups groups of
+// threads.  Output: blob x = [hi | lo], each the NB x NB block as the MMA's B
+// operand (K = the row index of G, N = its column index), K-major without
+// swizzle: core matrix (n / 8, k / 4) of 8 rows (n) x 16 bytes (4 k) at byte
 // ((n / 8) * (NB / 4) + k / 4) * 128, so the 16-byte chunks are written in
 // order.
+constexpr int kFormThreads = 512;
+
+struct FormRec {
+  int l;
+  float c, s;
+};
+
 template <int NB>
-__global__ void __launch_bounds__(NB) k_tc_form(const int32_t *__restrict__ Ca, const float2 *__restrict__ Cf,
-                                                const int4 *__restrict__ desc, int T, int cap, int b,
-                                                const int2 *__restrict__ ranges, float *__restrict__ blobs,
-                                                int *__restrict__ status) {
-  constexpr int K = NB / 2, W = NB / 2, S = NB + 4;
+__host__ __device__ constexpr size_t form_smem_bytes() {
+  // G, the per-chase record offsets (K + 1 ints) and the records (at most
+  // W / 2 + 1 per chase: pair starts W apart, two columns apart at least)
+  return (size_t)NB * (NB + 4) * 4 + 16 * ((4 * (NB / 2 + 1) + 15) / 16) +
+         (size_t)(NB / 2) * (NB / 4 + 1) * sizeof(FormRec);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restrict__ Ca, const float2 *__restrict__ Cf,
+                                                          const int4 *__restrict__ desc, int T, int cap, int b,
+                                                          const int2 *__restrict__ ranges, float *__restrict__ blobs,
+                                                          int *__restrict__ status) {
+  constexpr int K = NB / 2, W = NB / 2, S = NB + 4, G = kFormThreads / NB;
   extern __shared__ __align__(16) float Gs[];
+  int *off = reinterpret_cast<int *>(Gs + NB * S);  // K + 1 offsets into rec
+  FormRec *rec = reinterpret_cast<FormRec *>(reinterpret_cast<unsigned char *>(off) + 16 * ((4 * (K + 1) + 15) / 16));
+  __shared__ int cnt_s[K], e0_s[K];
   const int2 rg = ranges[b];
   const int j = rg.x + (int)blockIdx.x;
   if (j > rg.y) return;
-  const int r = threadIdx.x;
-  for (int c = 0; c < NB; c++) Gs[c * S + r] = (c == r) ? 1.f : 0.f;
-  const int base = j * W - K;  // column of X that is column 0 of the tile
-  for (int i = 0; i < K; i++) {
-    const int t = b * K + i;
-    if (t >= T) break;
-    const int4 d = desc[t];
-    const int cnt = d.y & 0xffffff, code = d.y >> 24;
-    if (code == kEmpty) continue;
-    const int lo = j * W - 1 - i, hi = lo + W;  // this tile's pair starts in chase t
-    if (d.w < lo || d.z >= hi) continue;
-    const size_t rb = (size_t)t * cap;
-    int e0, e1, step = 0;
-    if (code < 5) {
-      // gap-free: record e starts at column d.z + step * e
-      step = code < 2 ? 2 : 3;
-      e0 = lo <= d.z ? 0 : (lo - d.z + step - 1) / step;
-      e1 = min(cnt, (hi - d.z + step - 1) / step);
-    } else {
-      e0 = lower_bound(Ca + rb, cnt, lo + 1);  // Ca holds 1-based pair starts
-      e1 = lower_bound(Ca + rb, cnt, hi + 1);
-    }
-    for (int e = e0; e < e1; e++) {
-      const int l = (code < 5 ? d.z + step * e : Ca[rb + e] - 1) - base;
-      if (l < 0 || l > NB - 2) {
-        if (r == 0) atomicOr(status, ERR_RANGE);
-        continue;
+  const int tid = threadIdx.x, r = tid % NB, g = tid / NB;
+  const int o = band_offset(b, W);
+  const int base = j * W - K - o;  // column of X that is column 0 of the tile
+  for (int q = tid; q < NB * NB; q += kFormThreads) {
+    const int c = q / NB, rr = q % NB;
+    Gs[c * S + rr] = (c == rr) ? 1.f : 0.f;
+  }
+  // each chase's records in this tile: [e0, e0 + cnt)
+  if (tid < K) {
+    const int i = tid, t = b * K + i;
+    int e0 = 0, e1 = 0;
+    if (t < T) {
+      const int4 d = desc[t];
+      const int cnt = d.y & 0xffffff, code = d.y >> 24;
+      const int lo = j * W - 1 - i - o, hi = lo + W;  // this tile's pair starts in chase t
+      if (code != kEmpty && d.w >= lo && d.z < hi) {
+        if (code < 5) {
+          // gap-free: record e starts at column d.z + step * e
+          const int step = code < 2 ? 2 : 3;
+          e0 = lo <= d.z ? 0 : (lo - d.z + step - 1) / step;
+          e1 = min(cnt, (hi - d.z + step - 1) / step);
+        } else {
+          const size_t rb = (size_t)t * cap;
+          e0 = lower_bound(Ca + rb, cnt, lo + 1);  // Ca holds 1-based pair starts
+          e1 = lower_bound(Ca + rb, cnt, hi + 1);
+        }
       }
-      const float2 g = Cf[rb + e];
-      float *px = Gs + l * S + r;
-      const float x = px[0], y = px[S];
-      px[0] = fmaf(g.x, x, g.y * y);
-      px[S] = fmaf(g.x, y, -g.y * x);
+    }
+    e0_s[i] = e0;
+    cnt_s[i] = max(0, min(e1 - e0, W / 2 + 1));
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int i = 0; i < K; i++) {
+      off[i] = acc;
+      acc += cnt_s[i];
+    }
+    off[K] = acc;
+  }
+  __syncthreads();
+  // gather: warp w takes chases w, w + 16, ...
+  for (int i = tid >> 5; i < K; i += kFormThreads / 32) {
+    const int t = b * K + i, n = cnt_s[i];
+    if (n == 0) continue;
+    const int4 d = desc[t];
+    const int code = d.y >> 24, step = code < 2 ? 2 : 3;
+    const size_t rb = (size_t)t * cap;
+    for (int q = tid & 31; q < n; q += 32) {
+      const int e = e0_s[i] + q;
+      int l = (code < 5 ? d.z + step * e : Ca[rb + e] - 1) - base;
+      const float2 cs = Cf[rb + e];
+      if (l < 0 || l > NB - 2) {
+        atomicOr(status, ERR_RANGE);
+        l = -1;  // skipped below
+      }
+      rec[off[i] + q] = FormRec{l, cs.x, cs.y};
     }
   }
   __syncthreads();
+  // apply, chase by chase
+  const bool active = g < G;  // threads beyond G whole groups of NB (NB = 96) idle here
+  for (int i = 0; i < K; i++) {
+    const int r0 = off[i], r1 = off[i + 1];
+#pragma unroll 2
+    for (int q = r0 + g; active && q < r1; q += G) {
+      const FormRec f = rec[q];
+      if (f.l < 0) continue;
+      float *px = Gs + f.l * S + r;
+      const float x = px[0], y = px[S];
+      px[0] = fmaf(f.c, x, f.s * y);
+      px[S] = fmaf(f.c, y, -f.s * x);
+    }
+    __syncthreads();
+  }
   uint4 *oh = reinterpret_cast<uint4 *>(blobs + (size_t)blockIdx.x * 2 * NB * NB);
   uint4 *ol = oh + NB * NB / 4;
-  for (int idx = r; idx < NB * NB / 4; idx += NB) {
+  for (int idx = tid; idx < NB * NB / 4; idx += kFormThreads) {
     const int r8 = idx & 7, kc = (idx >> 3) % (NB / 4), ng = (idx >> 3) / (NB / 4);
     const float4 v = *reinterpret_cast<const float4 *>(Gs + (ng * 8 + r8) * S + 4 * kc);
     uint4 h, l;
@@ -239,9 +315,9 @@ __global__ void __launch_bounds__(NB) k_tc_form(const int32_t *__restrict__ Ca, 
 // the products of one band
 // ---------------------------------------------------------------------------
 // Row thread r (warps 0-3) <-> panel row r <-> TMEM lane r.  Tensor memory:
-// D (the accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo at
-// [256, 256 + NB); A's columns [0, K) hold the carry, [K, NB) the tile's W new
-// columns.  Shared memory: the tile's B blob.  Barriers (one phase per tile):
+// D (the main accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo
+// at [256, 256 + NB), the correction accumulator at [384, 384 + NB); A's
+// columns [0, K) hold the carry, [K, NB) the tile's W new columns.  Shared memory: the tile's B blob.  Barriers (one phase per tile):
 // bar_b (the blob has landed), bar_a (the four row warps have written A),
 // bar_m (the tile's MMAs have completed; also frees the blob's buffer).
 // v (n columns of this thread's row) into A hi / A lo at column col0
@@ -263,18 +339,28 @@ __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, in
 // unit in the last place per MMA step.  The row's outputs are scaled back to
 // its input norm (in2 = its squared input norm): the factor is 1 up to that
 // bias, and without it the bias would add up over the bands of every update.
+// 16 outputs of this thread's row from column c of the tile: the two
+// accumulators added in FP32 (round to nearest)
+__device__ __forceinline__ void out16(uint32_t dcol, int c, float (&y)[16]) {
+  uint32_t v[16], w[16];
+  tmem_ld16(dcol + c, v);
+  tmem_ld16(dcol + (kColDC - kColD) + c, w);
+  tc_wait_ld();
+#pragma unroll
+  for (int q = 0; q < 16; q++) y[q] = __uint_as_float(v[q]) + __uint_as_float(w[q]);
+}
+
 template <int NB>
 __device__ __forceinline__ float norm_restore_n(uint32_t dcol, float in2) {
   float o0 = 0.f, o1 = 0.f;
 #pragma unroll
   for (int c = 0; c < NB; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(dcol + c, v);
-    tc_wait_ld();
+    float y[16];
+    out16(dcol, c, y);
 #pragma unroll
     for (int qq = 0; qq < 16; qq += 2) {
-      o0 = fmaf(__uint_as_float(v[qq]), __uint_as_float(v[qq]), o0);
-      o1 = fmaf(__uint_as_float(v[qq + 1]), __uint_as_float(v[qq + 1]), o1);
+      o0 = fmaf(y[qq], y[qq], o0);
+      o1 = fmaf(y[qq + 1], y[qq + 1], o1);
     }
   }
   const float o2 = o0 + o1;
@@ -347,8 +433,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         for (int s = 0; s < NB / 8; s++) {
           const uint64_t dh = smem_desc(bh + 256u * s, 128u, sbo), dl = smem_desc(bl + 256u * s, 128u, sbo);
           mma_tf32(tm + kColD, tm + kColAH + 8 * s, dh, idesc, s > 0 ? 1u : 0u);
-          mma_tf32(tm + kColD, tm + kColAH + 8 * s, dl, idesc, 1u);
-          mma_tf32(tm + kColD, tm + kColAL + 8 * s, dh, idesc, 1u);
+          mma_tf32(tm + kColDC, tm + kColAH + 8 * s, dl, idesc, s > 0 ? 1u : 0u);
+          mma_tf32(tm + kColDC, tm + kColAL + 8 * s, dh, idesc, 1u);
         }
         mma_commit(&bar_m);
         committed = q + 1;
@@ -365,22 +451,23 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     float *xw = X + (rv ? row : 0);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     const uint32_t dcol = tm + lane_off + kColD;
+    const int o = band_offset(b, W);
     float in2 = 0.f;  // squared norm of this row's inputs to the tile in flight
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
       float nv[W], cv[K];
-      // the tile's new columns [j W, j W + W), read before waiting on the
-      // previous tile
+      // the tile's new columns [j W - o, j W - o + W), read before waiting on
+      // the previous tile
 #pragma unroll
       for (int c = 0; c < W; c++) {
-        const int col = j * W + c;
-        nv[c] = (rv && col < ncol) ? xr[(size_t)col * ld] : 0.f;
+        const int col = j * W - o + c;
+        nv[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
       }
       if (q == 0) {
 #pragma unroll
         for (int c = 0; c < K; c++) {
-          const int col = j * W - K + c;
+          const int col = j * W - K - o + c;
           cv[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
         }
       } else {
@@ -391,27 +478,25 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         }
         tc_fence_after();
         const float sc = norm_restore_n<NB>(dcol, in2);
-        // the previous tile's first W outputs are final: columns [(j-1) W - K, ...)
-        const int g0 = (j - 1) * W - K;
+        // the previous tile's first W outputs are final: columns [(j-1) W - K - o, ...)
+        const int g0 = (j - 1) * W - K - o;
 #pragma unroll
         for (int c = 0; c < W; c += 16) {
-          uint32_t v[16];
-          tmem_ld16(dcol + c, v);
-          tc_wait_ld();
+          float y[16];
+          out16(dcol, c, y);
 #pragma unroll
           for (int qq = 0; qq < 16; qq++) {
             const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * __uint_as_float(v[qq]);
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
           }
         }
         // its last K outputs are this tile's first K inputs
 #pragma unroll
         for (int c = 0; c < K; c += 16) {
-          uint32_t v[16];
-          tmem_ld16(dcol + W + c, v);
-          tc_wait_ld();
+          float y[16];
+          out16(dcol, W + c, y);
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) cv[c + qq] = sc * __uint_as_float(v[qq]);
+          for (int qq = 0; qq < 16; qq++) cv[c + qq] = sc * y[qq];
         }
       }
       float s0 = 0.f, s1 = 0.f;
@@ -434,16 +519,15 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
       } else {
         tc_fence_after();
         const float sc = norm_restore_n<NB>(dcol, in2);
-        const int g0 = rg.y * W - K;  // the last tile's columns, all final
+        const int g0 = rg.y * W - K - o;  // the last tile's columns, all final
 #pragma unroll 1
         for (int c = 0; c < NB; c += 16) {
-          uint32_t v[16];
-          tmem_ld16(dcol + c, v);
-          tc_wait_ld();
+          float y[16];
+          out16(dcol, c, y);
 #pragma unroll
           for (int qq = 0; qq < 16; qq++) {
             const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * __uint_as_float(v[qq]);
+            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
           }
         }
       }
@@ -461,7 +545,7 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   const int32_t *Ca = side == 0 ? st.La : st.Ra;
   const float2 *Cf = side == 0 ? st.Lf : st.Rf;
   const int4 *desc = side == 0 ? st.Lm : st.Rm;
-  const size_t form_smem = (size_t)NB * (NB + 4) * 4;
+  const size_t form_smem = form_smem_bytes<NB>();
   const size_t apply_smem = (size_t)2 * NB * NB * 4;
   cudaError_t e = cudaFuncSetAttribute(k_tc_form<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)form_smem);
   if (e == cudaSuccess)
@@ -469,7 +553,7 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   if (e != cudaSuccess) return e;
   const int panels = (nrow + kRows - 1) / kRows;
   for (int b = 0; b < nbands; b++) {
-    k_tc_form<NB><<<max_tiles, NB, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
+    k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
     k_tc_apply<NB><<<panels, kApplyThreads, apply_smem, s>>>(X, ld, nrow, ncol, blobs, ranges, b, status);
   }
   return cudaGetLastError();
@@ -480,12 +564,13 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 // Workspace of the blocked apply: the band ranges, then one band's blobs.
-// A band's tiles j run over floor((a + i + 1) / W) for pair starts a in
-// [0, ncol - 2] and i < K: at most (ncol + K) / W + 1 of them.
+// A band's tiles j run over floor((a + i + 1 + o) / W) for pair starts a in
+// [0, ncol - 2], i < K and o < W: at most (ncol + K + W) / W + 1 of them.
+static int tc_max_tiles(int ncol, int nb) { return (ncol + nb) / (nb / 2) + 2; }
 size_t tc_workspace_bytes(int ncol, int T, int nb) {
-  const int K = nb / 2, W = nb / 2;
+  const int K = nb / 2;
   const int nbands = (T + K - 1) / K;
-  const int max_tiles = (ncol + K) / W + 2;
+  const int max_tiles = tc_max_tiles(ncol, nb);
   return align256((size_t)(nbands + 1) * sizeof(int2)) + (size_t)max_tiles * 2 * nb * nb * 4;
 }
 
@@ -503,7 +588,7 @@ cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotS
   if (e != cudaSuccess || st.T <= 0) return e;
   const int K = nb / 2, W = nb / 2;
   const int nbands = (st.T + K - 1) / K;
-  const int max_tiles = (ncol + K) / W + 2;
+  const int max_tiles = tc_max_tiles(ncol, nb);
   int2 *ranges = reinterpret_cast<int2 *>(ws);
   float *blobs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ws) +
                                            align256((size_t)(nbands + 1) * sizeof(int2)));

@@ -1,11 +1,18 @@
 """The blocked tensor-core apply (mixed form, nb = 64, 96, 128): the rotations
 of nb/2 consecutive chases over a window of nb/2 columns are accumulated into
 an nb x nb orthogonal block and applied as a 3xTF32 product on the tensor
-cores (Sec. 3.2, Eq. bidiagplus).  It rounds differently from the
-rotation-by-rotation FP32 apply, so it is compared with the FP64 oracle within
-the mixed form's tolerances, and with the register-resident apply within FP32
-rounding; the bidiagonal it leaves behind is the chase's, and so identical to
-the other variants' after one update."""
+cores (Sec. 3.2, Eq. bidiagplus).
+
+It rounds differently from the rotation-by-rotation FP32 apply.  After one
+update both start from the same factors and run the same FP64 chase, so the
+bidiagonal is identical and the factors agree to FP32 rounding, element by
+element.  From the second update on, the projections differ by that rounding,
+and the trailing entries of the bidiagonal of these synthetic factorizations
+are ill-conditioned functions of the data (every mixed-form variant then
+differs from the FP64 oracle element by element, by O(1)), so longer streams
+are checked through what the paper fixes: the residual against A+ accumulated
+in FP64, the singular values (Sec. 2: sigma(Bd) = sigma(A)) and orthogonality.
+"""
 import numpy as np
 import pytest
 
@@ -44,6 +51,23 @@ def test_one_update_matches_the_oracle(m, n, nb):
         assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
 
 
+def _check_invariants(Q, d, e, P, ups, got, res_tol):
+    """Residual against A+ accumulated in FP64, every singular value against
+    LAPACK's, and orthogonality of both factors."""
+    m, n = Q.shape[0], P.shape[0]
+    Qg, dg, eg, Pg = got
+    A = Q @ O.bidiag_dense(d, e, m) @ P.T
+    for B, C in ups:
+        A += B @ C.T
+    R = Qg @ O.bidiag_dense(dg, eg, m) @ Pg.T
+    assert np.linalg.norm(A - R) / np.linalg.norm(A) <= res_tol
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    s_got = np.linalg.svd(O.bidiag_dense(dg, eg, m), compute_uv=False)
+    assert np.max(np.abs(s_ref - s_got)) <= 1e-5 * s_ref[0]
+    for X in (Qg, Pg):
+        assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
+
+
 @pytest.mark.parametrize("nb", [64, 128])
 def test_stream_keeps_the_mixed_tolerances(nb):
     """Twelve rank-1 updates and one rank-3 update (the rank-r pipeline) with
@@ -53,29 +77,19 @@ def test_stream_keeps_the_mixed_tolerances(nb):
     Q, d, e, P = I.factorization(m, n, config=0, which=8)
     ups = [I.dense_update(m, n, h, config=0) for h in range(12)] + [I.dense_update(m, n, 99, config=0, r=3)]
     outs, st = _run(Q, d, e, P, ups, nb)
-    Qg, dg, eg, Pg = outs[-1]
-    A = Q @ O.bidiag_dense(d, e, m) @ P.T
-    for B, C in ups:
-        A += B @ C.T
-    R = Qg @ O.bidiag_dense(dg, eg, m) @ Pg.T
     # FP32 rounding budget of 15 rank-1 columns at this size (the register
     # apply leaves about 6e-6 here)
-    assert np.linalg.norm(A - R) / np.linalg.norm(A) <= 3e-5
-    s_ref = np.linalg.svd(A, compute_uv=False)
-    s_got = np.linalg.svd(O.bidiag_dense(dg, eg, m), compute_uv=False)
-    assert np.max(np.abs(s_ref - s_got)) <= 1e-5 * s_ref[0]
-    for X in (Qg, Pg):
-        assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
+    _check_invariants(Q, d, e, P, ups, outs[-1], 3e-5)
 
 
-def test_overlapped_form_with_the_blocked_apply():
+@pytest.mark.parametrize("nb", [64, 128])
+def test_overlapped_form_with_the_blocked_apply(nb):
     m = n = 512
     Q, d, e, P = I.factorization(m, n, config=1, which=2)
-    ups = [I.recommender_update(m, n, h, config=1) for h in range(6)]
-    a, _ = _run(Q, d, e, P, ups, 128, overlap=True)
-    b, _ = _run(Q, d, e, P, ups, 1, overlap=True)
-    for x, y in zip(a[-1], b[-1]):
-        assert np.max(np.abs(x - y)) <= 1e-4 * max(1.0, np.max(np.abs(y)))
+    ups = [I.recommender_update(m, n, h, config=1) for h in range(8)]
+    a, st = _run(Q, d, e, P, ups, nb, overlap=True)
+    assert st["apply_variant"] == [nb, nb]
+    _check_invariants(Q, d, e, P, ups, a[-1], 3e-5)
 
 
 def test_autotuner_may_pick_the_blocked_apply_and_results_stay_within_tolerance():
