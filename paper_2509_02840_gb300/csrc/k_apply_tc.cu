@@ -81,15 +81,8 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
-// 32 lanes x 16 consecutive 32-bit columns: lane t of the warp <-> TMEM lane
-// (taddr's lane + t)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
+// tcgen05.st of 16 consecutive 32-bit columns: lane t of the warp <-> TMEM
+// lane (taddr's lane + t)
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
@@ -314,13 +307,19 @@ __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restr
 // ---------------------------------------------------------------------------
 // the products of one band
 // ---------------------------------------------------------------------------
-// Row thread r (warps 0-3) <-> panel row r <-> TMEM lane r.  Tensor memory:
-// D (the main accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo
-// at [256, 256 + NB), the correction accumulator at [384, 384 + NB); A's
-// columns [0, K) hold the carry, [K, NB) the tile's W new columns.  Shared memory: the tile's B blob.  Barriers (one phase per tile):
-// bar_b (the blob has landed), bar_a (the four row warps have written A),
-// bar_m (the tile's MMAs have completed; also frees the blob's buffer).
-// v (n columns of this thread's row) into A hi / A lo at column col0
+// 32 lanes x 32 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// v (N columns of this thread's row) into A hi / A lo at column col0
 template <int N>
 __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, int col0, const float (&v)[N]) {
 #pragma unroll
@@ -333,32 +332,32 @@ __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, in
   }
 }
 
+// 32 outputs of this thread's row from column c of the tile: the two
+// accumulators added in FP32 (round to nearest)
+__device__ __forceinline__ void out32(uint32_t dcol, int c, float (&y)[32]) {
+  uint32_t v[32], w[32];
+  tmem_ld32(dcol + c, v);
+  tmem_ld32(dcol + (kColDC - kColD) + c, w);
+  tc_wait_ld();
+#pragma unroll
+  for (int q = 0; q < 32; q++) y[q] = __uint_as_float(v[q]) + __uint_as_float(w[q]);
+}
+
 // Row-norm restoration.  G is orthogonal, so each row's 2-norm over the
 // tile's NB columns is the same before and after the product; the tensor
 // cores' FP32 accumulation truncates toward zero and shrinks it by about one
 // unit in the last place per MMA step.  The row's outputs are scaled back to
 // its input norm (in2 = its squared input norm): the factor is 1 up to that
 // bias, and without it the bias would add up over the bands of every update.
-// 16 outputs of this thread's row from column c of the tile: the two
-// accumulators added in FP32 (round to nearest)
-__device__ __forceinline__ void out16(uint32_t dcol, int c, float (&y)[16]) {
-  uint32_t v[16], w[16];
-  tmem_ld16(dcol + c, v);
-  tmem_ld16(dcol + (kColDC - kColD) + c, w);
-  tc_wait_ld();
-#pragma unroll
-  for (int q = 0; q < 16; q++) y[q] = __uint_as_float(v[q]) + __uint_as_float(w[q]);
-}
-
 template <int NB>
 __device__ __forceinline__ float norm_restore_n(uint32_t dcol, float in2) {
   float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-  for (int c = 0; c < NB; c += 16) {
-    float y[16];
-    out16(dcol, c, y);
+  for (int c = 0; c < NB; c += 32) {
+    float y[32];
+    out32(dcol, c, y);
 #pragma unroll
-    for (int qq = 0; qq < 16; qq += 2) {
+    for (int qq = 0; qq < 32; qq += 2) {
       o0 = fmaf(y[qq], y[qq], o0);
       o1 = fmaf(y[qq + 1], y[qq + 1], o1);
     }
@@ -368,19 +367,41 @@ __device__ __forceinline__ float norm_restore_n(uint32_t dcol, float in2) {
 }
 
 template <int NB>
+__host__ __device__ constexpr size_t apply_smem_bytes() {
+  return (size_t)2 * NB * NB * 4 + 2 * (size_t)(NB / 2) * kRows * 4;  // B blob, two new-column buffers
+}
+
+// Row thread r (warps 0-3) <-> panel row r <-> TMEM lane r.  Tensor memory:
+// D (the main accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo
+// at [256, 256 + NB), the correction accumulator at [384, 384 + NB); A's
+// columns [0, K) hold the carry, [K, NB) the tile's W new columns.  Shared
+// memory: the tile's B blob, then two buffers of the panel's W new columns
+// (column-major, 128 rows each), filled by bulk copies one tile ahead when
+// the panel is whole and the leading dimension a multiple of 4 (16-byte
+// aligned columns), else read by the row threads themselves.  Barriers:
+// bar_b (the blob has landed), bar_a (the four row warps have written A),
+// bar_m (the tile's MMAs have completed; also frees the blob's buffer), one
+// phase per tile each; bar_n[2] (a new-column buffer has landed), one phase
+// per use.
+template <int NB>
 __global__ void __launch_bounds__(kApplyThreads, 1)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
                const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2;
   constexpr uint32_t kBlob = 2u * NB * NB * 4u;
+  constexpr uint32_t kNvCol = kRows * 4u;  // bytes of one new column of the panel
   extern __shared__ __align__(1024) unsigned char sB[];
-  __shared__ uint64_t bar_b, bar_a, bar_m;
+  float *nvbuf = reinterpret_cast<float *>(sB + kBlob);  // [2][W][kRows]
+  __shared__ uint64_t bar_b, bar_a, bar_m, bar_n[2];
   __shared__ uint32_t tmem_s;
   __shared__ volatile int dead;
   const int2 rg = ranges[b];
   if (rg.y < rg.x) return;  // no rotation in this band (the same for the whole block)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = rg.y - rg.x + 1;
+  const int row0 = (int)blockIdx.x * kRows;
+  const bool bulk = (ld % 4) == 0 && row0 + kRows <= nrow;  // the same for the whole block
+  const int o = band_offset(b, W);
   if (warp == 0) {
     tmem_alloc(&tmem_s, kTmemCols);
     tmem_relinquish();
@@ -389,6 +410,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     async::mbar_init(&bar_b, 1);
     async::mbar_init(&bar_a, 4);
     async::mbar_init(&bar_m, 1);
+    async::mbar_init(&bar_n[0], 1);
+    async::mbar_init(&bar_n[1], 1);
     async::mbar_init_fence();
     dead = 0;
   }
@@ -398,14 +421,29 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
   const uint32_t tm = tmem_s;
 
   if (warp == 4) {
-    // ---- MMA warp (one thread): per tile, the blob into shared memory, then
-    // 3 x NB/8 MMAs once the row warps have written A
+    // ---- MMA warp (one thread): per tile, the blob into shared memory and
+    // the next tile's new columns into their buffer, then 3 x NB/8 MMAs once
+    // the row warps have written A
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(kRows, NB);
       constexpr uint32_t sbo = (NB / 4) * 128;
       const uint32_t bh = su32(sB), bl = bh + NB * NB * 4;
-      int committed = 0;
+      // new columns of tile q into buffer q & 1 (columns outside X are not copied)
+      auto issue_nv = [&](int q) {
+        const int c0 = (rg.x + q) * W - o;
+        const int lo = max(c0, 0), hi = min(c0 + W, ncol);
+        uint64_t *bar = &bar_n[q & 1];
+        async::mbar_arrive_tx(bar, hi > lo ? (unsigned)(hi - lo) * kNvCol : 0u);
+        float *dst = nvbuf + (size_t)(q & 1) * W * kRows;
+        for (int col = lo; col < hi; col++)
+          async::bulk_g2s(dst + (size_t)(col - c0) * kRows, X + (size_t)col * ld + row0, kNvCol, bar);
+      };
+      int committed = 0, nv_issued = 0;
       bool copy_pending = false;
+      if (bulk) {
+        issue_nv(0);
+        nv_issued = 1;
+      }
       for (int q = 0; q < ntiles && !dead; q++) {
         if (q > 0 && !async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
           atomicOr(status, ERR_APPLY);
@@ -414,9 +452,15 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         }
         async::mbar_arrive_tx(&bar_b, kBlob);
         const unsigned char *src = reinterpret_cast<const unsigned char *>(blobs) + (size_t)q * kBlob;
-        for (uint32_t o = 0; o < kBlob; o += kCopyChunk)
-          async::bulk_g2s(sB + o, src + o, kBlob - o < kCopyChunk ? kBlob - o : kCopyChunk, &bar_b);
+        for (uint32_t off = 0; off < kBlob; off += kCopyChunk)
+          async::bulk_g2s(sB + off, src + off, kBlob - off < kCopyChunk ? kBlob - off : kCopyChunk, &bar_b);
         copy_pending = true;
+        // buffer (q + 1) & 1 was last read for tile q - 1, whose A the row
+        // warps had written (bar_a) before the previous iteration's MMAs
+        if (bulk && q + 1 < ntiles) {
+          issue_nv(q + 1);
+          nv_issued = q + 2;
+        }
         if (!async::mbar_wait(&bar_b, (unsigned)(q & 1))) {
           atomicOr(status, ERR_APPLY);
           dead = 1;
@@ -439,31 +483,27 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         mma_commit(&bar_m);
         committed = q + 1;
       }
-      // nothing of this thread stays in flight: the last copy and MMAs
-      if (copy_pending) async::mbar_wait(&bar_b, (unsigned)((committed) & 1));
-      if (committed > 0 && dead) async::mbar_wait(&bar_m, (unsigned)((committed - 1) & 1));
+      if (dead) {
+        // nothing of this thread stays in flight: its copies and MMAs
+        if (copy_pending) async::mbar_wait(&bar_b, (unsigned)(committed & 1));
+        for (int q = nv_issued - 2 > 0 ? nv_issued - 2 : 0; q < nv_issued; q++)
+          async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1));
+        if (committed > 0) async::mbar_wait(&bar_m, (unsigned)((committed - 1) & 1));
+      }
     }
   } else {
     // ---- row warps
-    const int row = (int)blockIdx.x * kRows + tid;
+    const int row = row0 + tid;
     const bool rv = row < nrow;
     const float *xr = X + (rv ? row : 0);  // read: columns no earlier tile of the band has written
     float *xw = X + (rv ? row : 0);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     const uint32_t dcol = tm + lane_off + kColD;
-    const int o = band_offset(b, W);
     float in2 = 0.f;  // squared norm of this row's inputs to the tile in flight
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
-      float nv[W], cv[K];
-      // the tile's new columns [j W - o, j W - o + W), read before waiting on
-      // the previous tile
-#pragma unroll
-      for (int c = 0; c < W; c++) {
-        const int col = j * W - o + c;
-        nv[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
-      }
+      float cv[K];
       if (q == 0) {
 #pragma unroll
         for (int c = 0; c < K; c++) {
@@ -481,32 +521,71 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         // the previous tile's first W outputs are final: columns [(j-1) W - K - o, ...)
         const int g0 = (j - 1) * W - K - o;
 #pragma unroll
-        for (int c = 0; c < W; c += 16) {
-          float y[16];
-          out16(dcol, c, y);
+        for (int c = 0; c < W; c += 32) {
+          float y[32];
+          out32(dcol, c, y);
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) {
+          for (int qq = 0; qq < 32; qq++) {
             const int col = g0 + c + qq;
             if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
           }
         }
         // its last K outputs are this tile's first K inputs
 #pragma unroll
-        for (int c = 0; c < K; c += 16) {
-          float y[16];
-          out16(dcol, W + c, y);
+        for (int c = 0; c < K; c += 32) {
+          float y[32];
+          out32(dcol, W + c, y);
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) cv[c + qq] = sc * y[qq];
+          for (int qq = 0; qq < 32; qq++) cv[c + qq] = sc * y[qq];
         }
       }
-      float s0 = 0.f, s1 = 0.f;
+      float s0 = 0.f;
 #pragma unroll
       for (int c = 0; c < K; c++) s0 = fmaf(cv[c], cv[c], s0);
-#pragma unroll
-      for (int c = 0; c < W; c++) s1 = fmaf(nv[c], nv[c], s1);
-      in2 = s0 + s1;
       st_split_cols<K>(tm, lane_off, 0, cv);
-      st_split_cols<W>(tm, lane_off, K, nv);
+      // the tile's W new columns [j W - o, j W - o + W)
+      const int c0 = j * W - o;
+      float s1 = 0.f;
+      if (bulk) {
+        if (!async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1))) {
+          if (lane == 0) atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        const float *nb_ = nvbuf + (size_t)(q & 1) * W * kRows + tid;
+#pragma unroll
+        for (int c = 0; c < W; c += 16) {
+          float v[16];
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) {
+            const int col = c0 + c + qq;
+            v[qq] = (col >= 0 && col < ncol) ? nb_[(size_t)(c + qq) * kRows] : 0.f;
+            s1 = fmaf(v[qq], v[qq], s1);
+          }
+          uint32_t h[16], l[16];
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) split_tf32(v[qq], h[qq], l[qq]);
+          tmem_st16(tm + lane_off + kColAH + K + c, h);
+          tmem_st16(tm + lane_off + kColAL + K + c, l);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < W; c += 16) {
+          float v[16];
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) {
+            const int col = c0 + c + qq;
+            v[qq] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
+            s1 = fmaf(v[qq], v[qq], s1);
+          }
+          uint32_t h[16], l[16];
+#pragma unroll
+          for (int qq = 0; qq < 16; qq++) split_tf32(v[qq], h[qq], l[qq]);
+          tmem_st16(tm + lane_off + kColAH + K + c, h);
+          tmem_st16(tm + lane_off + kColAL + K + c, l);
+        }
+      }
+      in2 = s0 + s1;
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
@@ -521,11 +600,11 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         const float sc = norm_restore_n<NB>(dcol, in2);
         const int g0 = rg.y * W - K - o;  // the last tile's columns, all final
 #pragma unroll 1
-        for (int c = 0; c < NB; c += 16) {
-          float y[16];
-          out16(dcol, c, y);
+        for (int c = 0; c < NB; c += 32) {
+          float y[32];
+          out32(dcol, c, y);
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) {
+          for (int qq = 0; qq < 32; qq++) {
             const int col = g0 + c + qq;
             if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
           }
@@ -546,7 +625,7 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   const float2 *Cf = side == 0 ? st.Lf : st.Rf;
   const int4 *desc = side == 0 ? st.Lm : st.Rm;
   const size_t form_smem = form_smem_bytes<NB>();
-  const size_t apply_smem = (size_t)2 * NB * NB * 4;
+  const size_t apply_smem = apply_smem_bytes<NB>();
   cudaError_t e = cudaFuncSetAttribute(k_tc_form<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)form_smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_apply<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
