@@ -54,7 +54,6 @@ namespace bdu {
 namespace {
 
 constexpr int kRows = 128;          // rows of a panel: the MMA's M and the TMEM lanes
-constexpr int kApplyThreads = 160;  // four row warps + the MMA warp
 constexpr uint32_t kTmemCols = 512;
 // TMEM columns: the main accumulator (A_hi B_hi), A hi, A lo, the correction
 // accumulator (A_hi B_lo + A_lo B_hi)
@@ -81,8 +80,15 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
-// tcgen05.st of 16 consecutive 32-bit columns: lane t of the warp <-> TMEM
-// lane (taddr's lane + t)
+// tcgen05.ld / tcgen05.st of 16 consecutive 32-bit columns: lane t of the
+// warp <-> TMEM lane (taddr's lane + t)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
@@ -307,18 +313,6 @@ __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restr
 // ---------------------------------------------------------------------------
 // the products of one band
 // ---------------------------------------------------------------------------
-// 32 lanes x 32 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-
 // v (N columns of this thread's row) into A hi / A lo at column col0
 template <int N>
 __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, int col0, const float (&v)[N]) {
@@ -332,62 +326,37 @@ __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, in
   }
 }
 
-// 32 outputs of this thread's row from column c of the tile: the two
-// accumulators added in FP32 (round to nearest)
-__device__ __forceinline__ void out32(uint32_t dcol, int c, float (&y)[32]) {
-  uint32_t v[32], w[32];
-  tmem_ld32(dcol + c, v);
-  tmem_ld32(dcol + (kColDC - kColD) + c, w);
-  tc_wait_ld();
-#pragma unroll
-  for (int q = 0; q < 32; q++) y[q] = __uint_as_float(v[q]) + __uint_as_float(w[q]);
-}
-
-// Row-norm restoration.  G is orthogonal, so each row's 2-norm over the
-// tile's NB columns is the same before and after the product; the tensor
-// cores' FP32 accumulation truncates toward zero and shrinks it by about one
-// unit in the last place per MMA step.  The row's outputs are scaled back to
-// its input norm (in2 = its squared input norm): the factor is 1 up to that
-// bias, and without it the bias would add up over the bands of every update.
-template <int NB>
-__device__ __forceinline__ float norm_restore_n(uint32_t dcol, float in2) {
-  float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-  for (int c = 0; c < NB; c += 32) {
-    float y[32];
-    out32(dcol, c, y);
-#pragma unroll
-    for (int qq = 0; qq < 32; qq += 2) {
-      o0 = fmaf(y[qq], y[qq], o0);
-      o1 = fmaf(y[qq + 1], y[qq + 1], o1);
-    }
-  }
-  const float o2 = o0 + o1;
-  return (o2 > 0.f && in2 > 0.f) ? sqrtf(in2 / o2) : 1.f;
-}
-
 template <int NB>
 __host__ __device__ constexpr size_t apply_smem_bytes() {
   return (size_t)2 * NB * NB * 4 + 2 * (size_t)(NB / 2) * kRows * 4;  // B blob, two new-column buffers
 }
 
-// Row thread r (warps 0-3) <-> panel row r <-> TMEM lane r.  Tensor memory:
-// D (the main accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo
-// at [256, 256 + NB), the correction accumulator at [384, 384 + NB); A's
-// columns [0, K) hold the carry, [K, NB) the tile's W new columns.  Shared
-// memory: the tile's B blob, then two buffers of the panel's W new columns
-// (column-major, 128 rows each), filled by bulk copies one tile ahead when
-// the panel is whole and the leading dimension a multiple of 4 (16-byte
-// aligned columns), else read by the row threads themselves.  Barriers:
-// bar_b (the blob has landed), bar_a (the four row warps have written A),
-// bar_m (the tile's MMAs have completed; also frees the blob's buffer), one
-// phase per tile each; bar_n[2] (a new-column buffer has landed), one phase
-// per use.
+// Warps 0-7 are row warps: warp w serves TMEM lanes (panel rows)
+// 32 (w % 4) .. + 31, one row per thread, and half h = w / 4 of the tile's
+// columns: h = 0 the first W outputs (final after the tile) and the W new
+// inputs, h = 1 the last K outputs, which are the next tile's first K inputs
+// (the carry).  The two warps of a lane quarter combine their halves' squared
+// norms through shared memory (named barrier 1 + quarter).  Warp 8 issues the
+// copies and MMAs.  Tensor memory: D (the main accumulator) at columns
+// [0, NB), A hi at [128, 128 + NB), A lo at [256, 256 + NB), the correction
+// accumulator at [384, 384 + NB); A's columns [0, K) hold the carry, [K, NB)
+// the new columns.  Shared memory: the tile's B blob, then two buffers of the
+// panel's W new columns (column-major, 128 rows each), filled by bulk copies
+// one tile ahead when the panel is whole and the leading dimension a multiple
+// of 4 (16-byte aligned columns), else read by the row threads themselves.
+// Barriers: bar_b (the blob has landed), bar_a (the eight row warps have
+// written A), bar_m (the tile's MMAs have completed; also frees the blob's
+// buffer), one phase per tile each; bar_n[2] (a new-column buffer has
+// landed), one phase per use.  The final outputs of a tile are stored to X
+// while the next tile's MMAs run.
+constexpr int kRowWarps = 8;
+constexpr int kApplyThreads2 = (kRowWarps + 1) * 32;
+
 template <int NB>
-__global__ void __launch_bounds__(kApplyThreads, 1)
+__global__ void __maxnreg__(224)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
                const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
-  constexpr int K = NB / 2, W = NB / 2;
+  constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: columns of D per row warp
   constexpr uint32_t kBlob = 2u * NB * NB * 4u;
   constexpr uint32_t kNvCol = kRows * 4u;  // bytes of one new column of the panel
   extern __shared__ __align__(1024) unsigned char sB[];
@@ -395,6 +364,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
   __shared__ uint64_t bar_b, bar_a, bar_m, bar_n[2];
   __shared__ uint32_t tmem_s;
   __shared__ volatile int dead;
+  __shared__ float2 xchg[2][kRows];  // per half and row: (squared output norm, squared input norm)
   const int2 rg = ranges[b];
   if (rg.y < rg.x) return;  // no rotation in this band (the same for the whole block)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -408,7 +378,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
   }
   if (tid == 32) {
     async::mbar_init(&bar_b, 1);
-    async::mbar_init(&bar_a, 4);
+    async::mbar_init(&bar_a, kRowWarps);
     async::mbar_init(&bar_m, 1);
     async::mbar_init(&bar_n[0], 1);
     async::mbar_init(&bar_n[1], 1);
@@ -420,7 +390,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
   tc_fence_after();
   const uint32_t tm = tmem_s;
 
-  if (warp == 4) {
+  if (warp == kRowWarps) {
     // ---- MMA warp (one thread): per tile, the blob into shared memory and
     // the next tile's new columns into their buffer, then 3 x NB/8 MMAs once
     // the row warps have written A
@@ -493,90 +463,103 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     }
   } else {
     // ---- row warps
-    const int row = row0 + tid;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;  // panel row <-> TMEM lane
+    const int row = row0 + r;
     const bool rv = row < nrow;
     const float *xr = X + (rv ? row : 0);  // read: columns no earlier tile of the band has written
     float *xw = X + (rv ? row : 0);
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    const uint32_t dcol = tm + lane_off + kColD;
-    float in2 = 0.f;  // squared norm of this row's inputs to the tile in flight
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const uint32_t dcol = tm + lane_off + kColD + half * H;  // this warp's half of the outputs
+    float in2 = 0.f;  // squared norm of this thread's half of the inputs to the tile in flight
+    float keep[H];    // finals (half 0) or carry (half 1) of the previous tile, scaled
+    // Reads this warp's half of the previous tile's outputs (the two
+    // accumulators added in FP32) into keep and scales them to restore the
+    // row's norm.  G is orthogonal, so each row's 2-norm over the tile's NB
+    // columns is the same before and after the product; the tensor cores'
+    // FP32 accumulation truncates toward zero and shrinks it by about one unit
+    // in the last place per MMA step.  The factor (both halves' sums
+    // combined) is 1 up to that bias, which would otherwise add up over the
+    // bands of every update.
+    auto take_outputs = [&]() {
+      float o2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < H; c += 16) {
+        uint32_t v[16], w[16];
+        tmem_ld16(dcol + c, v);
+        tmem_ld16(dcol + (kColDC - kColD) + c, w);
+        tc_wait_ld();
+#pragma unroll
+        for (int qq = 0; qq < 16; qq++) {
+          keep[c + qq] = __uint_as_float(v[qq]) + __uint_as_float(w[qq]);
+          o2 = fmaf(keep[c + qq], keep[c + qq], o2);
+        }
+      }
+      xchg[half][r] = make_float2(o2, in2);
+      async::named_sync(1 + quarter, 64);
+      const float2 other = xchg[half ^ 1][r];
+      const float out2 = o2 + other.x, inp2 = in2 + other.y;
+      const float sc = (out2 > 0.f && inp2 > 0.f) ? sqrtf(inp2 / out2) : 1.f;
+#pragma unroll
+      for (int c = 0; c < H; c++) keep[c] *= sc;
+      // both halves have read xchg before either writes it again: the next
+      // write follows the next tile's MMAs, which wait for both (bar_a)
+    };
+    auto store_keep = [&](int g0) {
+#pragma unroll
+      for (int c = 0; c < H; c++) {
+        const int col = g0 + c;
+        if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = keep[c];
+      }
+    };
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
-      float cv[K];
-      if (q == 0) {
-#pragma unroll
-        for (int c = 0; c < K; c++) {
-          const int col = j * W - K - o + c;
-          cv[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
-        }
-      } else {
+      bool have_finals = false;
+      if (q > 0) {
         if (!async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
           if (lane == 0) atomicOr(status, ERR_APPLY);
           dead = 1;
           break;
         }
         tc_fence_after();
-        const float sc = norm_restore_n<NB>(dcol, in2);
-        // the previous tile's first W outputs are final: columns [(j-1) W - K - o, ...)
-        const int g0 = (j - 1) * W - K - o;
+        take_outputs();
+        have_finals = half == 0;
+      }
+      float s = 0.f;
+      if (half == 1) {
+        // the carry: the previous tile's last K outputs, or X's columns
+        // [j W - K - o, j W - o) for the band's first tile
+        if (q == 0) {
 #pragma unroll
-        for (int c = 0; c < W; c += 32) {
-          float y[32];
-          out32(dcol, c, y);
-#pragma unroll
-          for (int qq = 0; qq < 32; qq++) {
-            const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
+          for (int c = 0; c < K; c++) {
+            const int col = j * W - K - o + c;
+            keep[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
           }
         }
-        // its last K outputs are this tile's first K inputs
 #pragma unroll
-        for (int c = 0; c < K; c += 32) {
-          float y[32];
-          out32(dcol, W + c, y);
-#pragma unroll
-          for (int qq = 0; qq < 32; qq++) cv[c + qq] = sc * y[qq];
-        }
-      }
-      float s0 = 0.f;
-#pragma unroll
-      for (int c = 0; c < K; c++) s0 = fmaf(cv[c], cv[c], s0);
-      st_split_cols<K>(tm, lane_off, 0, cv);
-      // the tile's W new columns [j W - o, j W - o + W)
-      const int c0 = j * W - o;
-      float s1 = 0.f;
-      if (bulk) {
-        if (!async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1))) {
+        for (int c = 0; c < K; c++) s = fmaf(keep[c], keep[c], s);
+        st_split_cols<K>(tm, lane_off, 0, keep);
+      } else {
+        // the W new columns [j W - o, j W - o + W)
+        const int c0 = j * W - o;
+        if (bulk && !async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1))) {
           if (lane == 0) atomicOr(status, ERR_APPLY);
           dead = 1;
           break;
         }
-        const float *nb_ = nvbuf + (size_t)(q & 1) * W * kRows + tid;
+        const float *nb_ = nvbuf + (size_t)(q & 1) * W * kRows + r;
 #pragma unroll
         for (int c = 0; c < W; c += 16) {
           float v[16];
 #pragma unroll
           for (int qq = 0; qq < 16; qq++) {
             const int col = c0 + c + qq;
-            v[qq] = (col >= 0 && col < ncol) ? nb_[(size_t)(c + qq) * kRows] : 0.f;
-            s1 = fmaf(v[qq], v[qq], s1);
-          }
-          uint32_t h[16], l[16];
-#pragma unroll
-          for (int qq = 0; qq < 16; qq++) split_tf32(v[qq], h[qq], l[qq]);
-          tmem_st16(tm + lane_off + kColAH + K + c, h);
-          tmem_st16(tm + lane_off + kColAL + K + c, l);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < W; c += 16) {
-          float v[16];
-#pragma unroll
-          for (int qq = 0; qq < 16; qq++) {
-            const int col = c0 + c + qq;
-            v[qq] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
-            s1 = fmaf(v[qq], v[qq], s1);
+            v[qq] = (col < 0 || col >= ncol) ? 0.f
+                    : bulk                   ? nb_[(size_t)(c + qq) * kRows]
+                    : rv                     ? xr[(size_t)col * ld]
+                                             : 0.f;
+            s = fmaf(v[qq], v[qq], s);
           }
           uint32_t h[16], l[16];
 #pragma unroll
@@ -585,11 +568,13 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
           tmem_st16(tm + lane_off + kColAL + K + c, l);
         }
       }
-      in2 = s0 + s1;
+      in2 = s;
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) async::mbar_arrive(&bar_a);
+      // the previous tile's finals, while this tile's MMAs run
+      if (have_finals) store_keep((j - 1) * W - K - o);
     }
     if (!dead) {
       if (!async::mbar_wait(&bar_m, (unsigned)((ntiles - 1) & 1))) {
@@ -597,18 +582,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         dead = 1;
       } else {
         tc_fence_after();
-        const float sc = norm_restore_n<NB>(dcol, in2);
-        const int g0 = rg.y * W - K - o;  // the last tile's columns, all final
-#pragma unroll 1
-        for (int c = 0; c < NB; c += 32) {
-          float y[32];
-          out32(dcol, c, y);
-#pragma unroll
-          for (int qq = 0; qq < 32; qq++) {
-            const int col = g0 + c + qq;
-            if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = sc * y[qq];
-          }
-        }
+        take_outputs();
+        store_keep(rg.y * W - K - o + half * H);  // the last tile's columns, all final
       }
     }
   }
@@ -633,7 +608,7 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   const int panels = (nrow + kRows - 1) / kRows;
   for (int b = 0; b < nbands; b++) {
     k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
-    k_tc_apply<NB><<<panels, kApplyThreads, apply_smem, s>>>(X, ld, nrow, ncol, blobs, ranges, b, status);
+    k_tc_apply<NB><<<panels, kApplyThreads2, apply_smem, s>>>(X, ld, nrow, ncol, blobs, ranges, b, status);
   }
   return cudaGetLastError();
 }
