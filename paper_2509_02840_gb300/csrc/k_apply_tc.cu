@@ -347,13 +347,13 @@ __host__ __device__ constexpr size_t apply_smem_bytes() {
 // Barriers: bar_b (the blob has landed), bar_a (the eight row warps have
 // written A), bar_m (the tile's MMAs have completed; also frees the blob's
 // buffer), one phase per tile each; bar_n[2] (a new-column buffer has
-// landed), one phase per use.  The final outputs of a tile are stored to X
-// while the next tile's MMAs run.
+// landed), one phase per use.  (Nine warps: a sub-partition of the SM holds
+// three, which bounds the kernel at 168 registers a thread.)
 constexpr int kRowWarps = 8;
 constexpr int kApplyThreads2 = (kRowWarps + 1) * 32;
 
 template <int NB>
-__global__ void __maxnreg__(224)
+__global__ void __launch_bounds__(kApplyThreads2, 1)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
                const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: columns of D per row warp
@@ -506,16 +506,16 @@ __global__ void __maxnreg__(224)
       // write follows the next tile's MMAs, which wait for both (bar_a)
     };
     auto store_keep = [&](int g0) {
+      float *p = xw + (int64_t)g0 * ld;  // walks the columns (an address, dereferenced only inside X)
 #pragma unroll
-      for (int c = 0; c < H; c++) {
+      for (int c = 0; c < H; c++, p += ld) {
         const int col = g0 + c;
-        if (rv && col >= 0 && col < ncol) xw[(size_t)col * ld] = keep[c];
+        if (rv && col >= 0 && col < ncol) *p = keep[c];
       }
     };
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
-      bool have_finals = false;
       if (q > 0) {
         if (!async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
           if (lane == 0) atomicOr(status, ERR_APPLY);
@@ -524,17 +524,20 @@ __global__ void __maxnreg__(224)
         }
         tc_fence_after();
         take_outputs();
-        have_finals = half == 0;
+        // the previous tile's finals (stores issued, not waited for)
+        if (half == 0) store_keep((j - 1) * W - K - o);
       }
       float s = 0.f;
       if (half == 1) {
         // the carry: the previous tile's last K outputs, or X's columns
         // [j W - K - o, j W - o) for the band's first tile
         if (q == 0) {
+          const int g0 = j * W - K - o;
+          const float *p = xr + (int64_t)g0 * ld;
 #pragma unroll
-          for (int c = 0; c < K; c++) {
-            const int col = j * W - K - o + c;
-            keep[c] = (rv && col >= 0 && col < ncol) ? xr[(size_t)col * ld] : 0.f;
+          for (int c = 0; c < K; c++, p += ld) {
+            const int col = g0 + c;
+            keep[c] = (rv && col >= 0 && col < ncol) ? *p : 0.f;
           }
         }
 #pragma unroll
@@ -549,16 +552,15 @@ __global__ void __maxnreg__(224)
           break;
         }
         const float *nb_ = nvbuf + (size_t)(q & 1) * W * kRows + r;
+        const float *p = xr + (int64_t)c0 * ld;
 #pragma unroll
         for (int c = 0; c < W; c += 16) {
           float v[16];
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) {
+          for (int qq = 0; qq < 16; qq++, p += ld) {
             const int col = c0 + c + qq;
-            v[qq] = (col < 0 || col >= ncol) ? 0.f
-                    : bulk                   ? nb_[(size_t)(c + qq) * kRows]
-                    : rv                     ? xr[(size_t)col * ld]
-                                             : 0.f;
+            const bool in = col >= 0 && col < ncol;
+            v[qq] = bulk ? (in ? nb_[(c + qq) * kRows] : 0.f) : ((rv && in) ? *p : 0.f);
             s = fmaf(v[qq], v[qq], s);
           }
           uint32_t h[16], l[16];
@@ -573,8 +575,6 @@ __global__ void __maxnreg__(224)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) async::mbar_arrive(&bar_a);
-      // the previous tile's finals, while this tile's MMAs run
-      if (have_finals) store_keep((j - 1) * W - K - o);
     }
     if (!dead) {
       if (!async::mbar_wait(&bar_m, (unsigned)((ntiles - 1) & 1))) {
