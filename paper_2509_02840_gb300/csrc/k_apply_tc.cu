@@ -178,6 +178,52 @@ __global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, in
 }
 
 // ---------------------------------------------------------------------------
+// the structure of a block
+// ---------------------------------------------------------------------------
+// In tile coordinates, local chase i may rotate pairs starting at columns
+// [K - 1 - i, K - 2 - i + W]: a value moves at most one column per chase,
+// and only inside that window, which slides one column to the left per
+// chase.  So G(k, c) = 0 unless output column c is reachable from input
+// column k, whatever the rotations are; the reachable range of each k is an
+// interval, computed here by following its ends through the K chases.  The
+// B operand keeps, for each 8-row k-step s of the MMA, only the output
+// columns [n0[s], n1[s]) reachable from its rows (rounded out to 16, the
+// MMA's N granularity): about 62% of the block at NB = 128.  Layout of one
+// part (hi or lo) of a blob: step s at byte off[s], K-major without swizzle,
+// its two 4-column K chunks one after the other, each (n1 - n0) / 8 core
+// matrices of 8 rows x 16 bytes (leading-dimension offset (n1 - n0) / 8 *
+// 128 bytes, stride-dimension offset 128).
+template <int NB>
+struct Cone {
+  static constexpr int K = NB / 2, W = NB / 2, S = NB / 8;
+  int n0[S], n1[S], off[S + 1];
+  __host__ __device__ constexpr Cone() : n0(), n1(), off() {
+    for (int s = 0; s < S; s++) {
+      int lo = NB, hi = -1;
+      for (int k = 8 * s; k < 8 * s + 8; k++) {
+        int a = k, b = k;  // the reachable interval
+        for (int i = 0; i < K; i++) {
+          const int ps0 = K - 1 - i, ps1 = K - 2 - i + W;
+          const int r = b < ps1 ? b : ps1;  // rightmost position that can move right
+          if (r >= (a > ps0 ? a : ps0) && r + 1 > b) b = r + 1;
+          const int l = a > ps0 + 1 ? a : ps0 + 1;  // leftmost position that can move left
+          if (l <= (b < ps1 + 1 ? b : ps1 + 1) && l - 1 < a) a = l - 1;
+        }
+        if (b > NB - 1) b = NB - 1;
+        if (a < lo) lo = a;
+        if (b > hi) hi = b;
+      }
+      n0[s] = lo / 16 * 16;
+      n1[s] = (hi / 16 + 1) * 16;
+    }
+    off[0] = 0;
+    for (int s = 0; s < S; s++) off[s + 1] = off[s] + 2 * (n1[s] - n0[s]) * 16;
+  }
+};
+template <int NB>
+__host__ __device__ constexpr uint32_t blob_part_bytes() { return (uint32_t)Cone<NB>().off[NB / 8]; }
+
+// ---------------------------------------------------------------------------
 // the blocks of one band
 // ---------------------------------------------------------------------------
 // Block x forms tile j = first + x of band b with kFormThreads threads: thread
@@ -187,11 +233,9 @@ __global__ void k_tc_band_ranges(const int4 *__restrict__ desc, int T, int K, in
 // shared memory, chase by chase (rec = (column of the pair in the tile,
 // c, s)); then the chases are applied in order, separated by barriers, each
 // chase's rotations -- disjoint pairs -- dealt to the kFormGroups groups of
-// threads.  Output: blob x = [hi | lo], each the NB x NB block as the MMA's B
-// operand (K = the row index of G, N = its column index), K-major without
-// swizzle: core matrix (n / 8, k / 4) of 8 rows (n) x 16 bytes (4 k) at byte
-// ((n / 8) * (NB / 4) + k / 4) * 128, so the 16-byte chunks are written in
-// order.
+// threads.  Output: blob x = [hi | lo], each the block as the MMA's B operand
+// (K = the row index of G, N = its column index) in the compact layout of
+// Cone, written in order of its 16-byte chunks.
 constexpr int kFormThreads = 512;
 
 struct FormRec {
@@ -295,18 +339,25 @@ __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restr
     }
     __syncthreads();
   }
-  uint4 *oh = reinterpret_cast<uint4 *>(blobs + (size_t)blockIdx.x * 2 * NB * NB);
-  uint4 *ol = oh + NB * NB / 4;
-  for (int idx = tid; idx < NB * NB / 4; idx += kFormThreads) {
-    const int r8 = idx & 7, kc = (idx >> 3) % (NB / 4), ng = (idx >> 3) / (NB / 4);
-    const float4 v = *reinterpret_cast<const float4 *>(Gs + (ng * 8 + r8) * S + 4 * kc);
-    uint4 h, l;
-    split_tf32(v.x, h.x, l.x);
-    split_tf32(v.y, h.y, l.y);
-    split_tf32(v.z, h.z, l.z);
-    split_tf32(v.w, h.w, l.w);
-    oh[idx] = h;
-    ol[idx] = l;
+  constexpr Cone<NB> cone{};
+  constexpr uint32_t part = blob_part_bytes<NB>();
+  unsigned char *oh = reinterpret_cast<unsigned char *>(blobs) + (size_t)blockIdx.x * 2 * part;
+  unsigned char *ol = oh + part;
+#pragma unroll
+  for (int s = 0; s < NB / 8; s++) {
+    const int ngn = (cone.n1[s] - cone.n0[s]) / 8, ng0 = cone.n0[s] / 8;
+    // 16-byte chunks of step s in order: (K chunk, core, row of the core)
+    for (int idx = tid; idx < 2 * ngn * 8; idx += kFormThreads) {
+      const int r8 = idx & 7, core = (idx >> 3) % ngn, kc = 2 * s + (idx >> 3) / ngn;
+      const float4 v = *reinterpret_cast<const float4 *>(Gs + ((ng0 + core) * 8 + r8) * S + 4 * kc);
+      uint4 h, l;
+      split_tf32(v.x, h.x, l.x);
+      split_tf32(v.y, h.y, l.y);
+      split_tf32(v.z, h.z, l.z);
+      split_tf32(v.w, h.w, l.w);
+      *reinterpret_cast<uint4 *>(oh + cone.off[s] + (size_t)idx * 16) = h;
+      *reinterpret_cast<uint4 *>(ol + cone.off[s] + (size_t)idx * 16) = l;
+    }
   }
 }
 
@@ -328,40 +379,55 @@ __device__ __forceinline__ void st_split_cols(uint32_t tm, uint32_t lane_off, in
 
 template <int NB>
 __host__ __device__ constexpr size_t apply_smem_bytes() {
-  return (size_t)2 * NB * NB * 4 + 2 * (size_t)(NB / 2) * kRows * 4;  // B blob, two new-column buffers
+  // two B blobs, one buffer of the panel's new columns
+  return (size_t)2 * 2 * blob_part_bytes<NB>() + (size_t)(NB / 2) * 128 * 4;
 }
 
 // Warps 0-7 are row warps: warp w serves TMEM lanes (panel rows)
-// 32 (w % 4) .. + 31, one row per thread, and half h = w / 4 of the tile's
-// columns: h = 0 the first W outputs (final after the tile) and the W new
-// inputs, h = 1 the last K outputs, which are the next tile's first K inputs
-// (the carry).  The two warps of a lane quarter combine their halves' squared
-// norms through shared memory (named barrier 1 + quarter).  Warp 8 issues the
-// copies and MMAs.  Tensor memory: D (the main accumulator) at columns
-// [0, NB), A hi at [128, 128 + NB), A lo at [256, 256 + NB), the correction
-// accumulator at [384, 384 + NB); A's columns [0, K) hold the carry, [K, NB)
-// the new columns.  Shared memory: the tile's B blob, then two buffers of the
-// panel's W new columns (column-major, 128 rows each), filled by bulk copies
-// one tile ahead when the panel is whole and the leading dimension a multiple
-// of 4 (16-byte aligned columns), else read by the row threads themselves.
-// Barriers: bar_b (the blob has landed), bar_a (the eight row warps have
-// written A), bar_m (the tile's MMAs have completed; also frees the blob's
-// buffer), one phase per tile each; bar_n[2] (a new-column buffer has
-// landed), one phase per use.  (Nine warps: a sub-partition of the SM holds
-// three, which bounds the kernel at 168 registers a thread.)
+// 32 (w % 4) .. + 31, one row per thread, and half h = w / 4 of the work:
+// h = 0 the first W outputs (final after the tile), h = 1 the last K outputs,
+// which are the next tile's first K inputs (the carry); each half also takes
+// half of the W new input columns.  The two warps of a lane quarter combine
+// their squared norms through shared memory (named barrier 1 + quarter).
+// Warp 8 issues the copies and MMAs.  Tensor memory: D (the main
+// accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo at
+// [256, 256 + NB), the correction accumulator at [384, 384 + NB); A's
+// columns [0, K) hold the carry, [K, NB) the new columns.  The MMAs of k-step
+// s cover only the output columns of Cone, so both accumulators are cleared
+// (tcgen05.st of zeros) before a tile's MMAs.  Shared memory: two B blobs
+// (tile q in buffer q & 1, loaded one tile ahead, while the previous tile's
+// MMAs run), then one buffer of the panel's W new columns (column-major, 128
+// rows), loaded by bulk copies while the previous tile's MMAs run when the
+// panel is whole and the leading dimension a multiple of 4 (16-byte aligned
+// columns), else read by the row threads themselves.  Barriers: bar_b[2] (a
+// blob has landed; one phase per use), bar_a (the eight row warps have
+// written A), bar_m (the tile's MMAs have completed: frees A, its blob
+// buffer and the accumulators' contents for reading), bar_n (the new columns
+// have landed), one phase per tile each.  (Nine warps: a sub-partition of the
+// SM holds three, which bounds the kernel at 168 registers a thread.)
 constexpr int kRowWarps = 8;
 constexpr int kApplyThreads2 = (kRowWarps + 1) * 32;
 
+// 16 columns of this thread's row into A hi / A lo at column col
+__device__ __forceinline__ void st_split16(uint32_t tm, uint32_t lane_off, int col, const float (&v)[16]) {
+  uint32_t h[16], l[16];
+#pragma unroll
+  for (int q = 0; q < 16; q++) split_tf32(v[q], h[q], l[q]);
+  tmem_st16(tm + lane_off + kColAH + col, h);
+  tmem_st16(tm + lane_off + kColAL + col, l);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kApplyThreads2, 1)
-    k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const float *__restrict__ blobs,
+    k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const unsigned char *__restrict__ blobs,
                const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
-  constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: columns of D per row warp
-  constexpr uint32_t kBlob = 2u * NB * NB * 4u;
+  constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: outputs per row warp
+  constexpr uint32_t kPart = blob_part_bytes<NB>(), kBlob = 2 * kPart;
   constexpr uint32_t kNvCol = kRows * 4u;  // bytes of one new column of the panel
-  extern __shared__ __align__(1024) unsigned char sB[];
-  float *nvbuf = reinterpret_cast<float *>(sB + kBlob);  // [2][W][kRows]
-  __shared__ uint64_t bar_b, bar_a, bar_m, bar_n[2];
+  constexpr Cone<NB> cone{};
+  extern __shared__ __align__(1024) unsigned char sB[];  // [2][kBlob], then the new columns
+  float *nvbuf = reinterpret_cast<float *>(sB + 2 * kBlob);  // [W][kRows]
+  __shared__ uint64_t bar_b[2], bar_a, bar_m, bar_n;
   __shared__ uint32_t tmem_s;
   __shared__ volatile int dead;
   __shared__ float2 xchg[2][kRows];  // per half and row: (squared output norm, squared input norm)
@@ -377,11 +443,11 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
     tmem_relinquish();
   }
   if (tid == 32) {
-    async::mbar_init(&bar_b, 1);
+    async::mbar_init(&bar_b[0], 1);
+    async::mbar_init(&bar_b[1], 1);
     async::mbar_init(&bar_a, kRowWarps);
     async::mbar_init(&bar_m, 1);
-    async::mbar_init(&bar_n[0], 1);
-    async::mbar_init(&bar_n[1], 1);
+    async::mbar_init(&bar_n, 1);
     async::mbar_init_fence();
     dead = 0;
   }
@@ -391,73 +457,71 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
   const uint32_t tm = tmem_s;
 
   if (warp == kRowWarps) {
-    // ---- MMA warp (one thread): per tile, the blob into shared memory and
-    // the next tile's new columns into their buffer, then 3 x NB/8 MMAs once
-    // the row warps have written A
+    // ---- MMA warp (one thread)
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(kRows, NB);
-      constexpr uint32_t sbo = (NB / 4) * 128;
-      const uint32_t bh = su32(sB), bl = bh + NB * NB * 4;
-      // new columns of tile q into buffer q & 1 (columns outside X are not copied)
+      auto issue_blob = [&](int q) {
+        uint64_t *bar = &bar_b[q & 1];
+        unsigned char *dst = sB + (size_t)(q & 1) * kBlob;
+        const unsigned char *src = blobs + (size_t)q * kBlob;
+        async::mbar_arrive_tx(bar, kBlob);
+        for (uint32_t off = 0; off < kBlob; off += kCopyChunk)
+          async::bulk_g2s(dst + off, src + off, kBlob - off < kCopyChunk ? kBlob - off : kCopyChunk, bar);
+      };
+      // new columns of tile q (columns outside X are not copied)
       auto issue_nv = [&](int q) {
         const int c0 = (rg.x + q) * W - o;
         const int lo = max(c0, 0), hi = min(c0 + W, ncol);
-        uint64_t *bar = &bar_n[q & 1];
-        async::mbar_arrive_tx(bar, hi > lo ? (unsigned)(hi - lo) * kNvCol : 0u);
-        float *dst = nvbuf + (size_t)(q & 1) * W * kRows;
+        async::mbar_arrive_tx(&bar_n, hi > lo ? (unsigned)(hi - lo) * kNvCol : 0u);
         for (int col = lo; col < hi; col++)
-          async::bulk_g2s(dst + (size_t)(col - c0) * kRows, X + (size_t)col * ld + row0, kNvCol, bar);
+          async::bulk_g2s(nvbuf + (size_t)(col - c0) * kRows, X + (size_t)col * ld + row0, kNvCol, &bar_n);
       };
-      int committed = 0, nv_issued = 0;
-      bool copy_pending = false;
+      int committed = 0, blobs_issued = 1, nv_issued = 0;
+      issue_blob(0);
       if (bulk) {
         issue_nv(0);
         nv_issued = 1;
       }
       for (int q = 0; q < ntiles && !dead; q++) {
+        // tile q + 1's blob into the buffer of tile q - 1, free once its MMAs are done
         if (q > 0 && !async::mbar_wait(&bar_m, (unsigned)((q - 1) & 1))) {
           atomicOr(status, ERR_APPLY);
           dead = 1;
           break;
         }
-        async::mbar_arrive_tx(&bar_b, kBlob);
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(blobs) + (size_t)q * kBlob;
-        for (uint32_t off = 0; off < kBlob; off += kCopyChunk)
-          async::bulk_g2s(sB + off, src + off, kBlob - off < kCopyChunk ? kBlob - off : kCopyChunk, &bar_b);
-        copy_pending = true;
-        // buffer (q + 1) & 1 was last read for tile q - 1, whose A the row
-        // warps had written (bar_a) before the previous iteration's MMAs
+        if (q + 1 < ntiles) {
+          issue_blob(q + 1);
+          blobs_issued = q + 2;
+        }
+        if (!async::mbar_wait(&bar_b[q & 1], (unsigned)((q >> 1) & 1)) ||
+            !async::mbar_wait(&bar_a, (unsigned)(q & 1))) {
+          atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+        // the row warps have read the new columns of tile q: the buffer takes tile q + 1's
         if (bulk && q + 1 < ntiles) {
           issue_nv(q + 1);
           nv_issued = q + 2;
         }
-        if (!async::mbar_wait(&bar_b, (unsigned)(q & 1))) {
-          atomicOr(status, ERR_APPLY);
-          dead = 1;
-          break;
-        }
-        copy_pending = false;
-        if (!async::mbar_wait(&bar_a, (unsigned)(q & 1))) {
-          atomicOr(status, ERR_APPLY);
-          dead = 1;
-          break;
-        }
         tc_fence_after();
-#pragma unroll 1
+        const uint32_t bh = su32(sB + (size_t)(q & 1) * kBlob), bl = bh + kPart;
+#pragma unroll
         for (int s = 0; s < NB / 8; s++) {
-          const uint64_t dh = smem_desc(bh + 256u * s, 128u, sbo), dl = smem_desc(bl + 256u * s, 128u, sbo);
-          mma_tf32(tm + kColD, tm + kColAH + 8 * s, dh, idesc, s > 0 ? 1u : 0u);
-          mma_tf32(tm + kColDC, tm + kColAH + 8 * s, dl, idesc, s > 0 ? 1u : 0u);
-          mma_tf32(tm + kColDC, tm + kColAL + 8 * s, dh, idesc, 1u);
+          const uint32_t n = cone.n1[s] - cone.n0[s];
+          const uint32_t idesc = idesc_tf32(kRows, (int)n);
+          const uint64_t dh = smem_desc(bh + cone.off[s], n / 8 * 128, 128u);
+          const uint64_t dl = smem_desc(bl + cone.off[s], n / 8 * 128, 128u);
+          mma_tf32(tm + kColD + cone.n0[s], tm + kColAH + 8 * s, dh, idesc, 1u);
+          mma_tf32(tm + kColDC + cone.n0[s], tm + kColAH + 8 * s, dl, idesc, 1u);
+          mma_tf32(tm + kColDC + cone.n0[s], tm + kColAL + 8 * s, dh, idesc, 1u);
         }
         mma_commit(&bar_m);
         committed = q + 1;
       }
       if (dead) {
         // nothing of this thread stays in flight: its copies and MMAs
-        if (copy_pending) async::mbar_wait(&bar_b, (unsigned)(committed & 1));
-        for (int q = nv_issued - 2 > 0 ? nv_issued - 2 : 0; q < nv_issued; q++)
-          async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1));
+        for (int q = committed; q < blobs_issued; q++) async::mbar_wait(&bar_b[q & 1], (unsigned)((q >> 1) & 1));
+        if (nv_issued > 0) async::mbar_wait(&bar_n, (unsigned)((nv_issued - 1) & 1));
         if (committed > 0) async::mbar_wait(&bar_m, (unsigned)((committed - 1) & 1));
       }
     }
@@ -471,18 +535,19 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
     float *xw = X + (rv ? row : 0);
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const uint32_t dcol = tm + lane_off + kColD + half * H;  // this warp's half of the outputs
-    float in2 = 0.f;  // squared norm of this thread's half of the inputs to the tile in flight
+    const uint32_t zero16[16] = {};
+    float in2 = 0.f;  // squared norm of this thread's share of the inputs to the tile in flight
     float keep[H];    // finals (half 0) or carry (half 1) of the previous tile, scaled
     // Reads this warp's half of the previous tile's outputs (the two
-    // accumulators added in FP32) into keep and scales them to restore the
-    // row's norm.  G is orthogonal, so each row's 2-norm over the tile's NB
-    // columns is the same before and after the product; the tensor cores'
-    // FP32 accumulation truncates toward zero and shrinks it by about one unit
-    // in the last place per MMA step.  The factor (both halves' sums
-    // combined) is 1 up to that bias, which would otherwise add up over the
-    // bands of every update.
+    // accumulators added in FP32) into keep, clears them for the next tile,
+    // and scales keep to restore the row's norm.  G is orthogonal, so each
+    // row's 2-norm over the tile's NB columns is the same before and after
+    // the product; the tensor cores' FP32 accumulation truncates toward zero
+    // and shrinks it by about one unit in the last place per MMA step.  The
+    // factor (both halves' sums combined) is 1 up to that bias, which would
+    // otherwise add up over the bands of every update.
     auto take_outputs = [&]() {
-      float o2 = 0.f;
+      float o2a = 0.f, o2b = 0.f;
 #pragma unroll
       for (int c = 0; c < H; c += 16) {
         uint32_t v[16], w[16];
@@ -490,11 +555,14 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         tmem_ld16(dcol + (kColDC - kColD) + c, w);
         tc_wait_ld();
 #pragma unroll
-        for (int qq = 0; qq < 16; qq++) {
+        for (int qq = 0; qq < 16; qq += 2) {
           keep[c + qq] = __uint_as_float(v[qq]) + __uint_as_float(w[qq]);
-          o2 = fmaf(keep[c + qq], keep[c + qq], o2);
+          keep[c + qq + 1] = __uint_as_float(v[qq + 1]) + __uint_as_float(w[qq + 1]);
+          o2a = fmaf(keep[c + qq], keep[c + qq], o2a);
+          o2b = fmaf(keep[c + qq + 1], keep[c + qq + 1], o2b);
         }
       }
+      const float o2 = o2a + o2b;
       xchg[half][r] = make_float2(o2, in2);
       async::named_sync(1 + quarter, 64);
       const float2 other = xchg[half ^ 1][r];
@@ -504,6 +572,13 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
       for (int c = 0; c < H; c++) keep[c] *= sc;
       // both halves have read xchg before either writes it again: the next
       // write follows the next tile's MMAs, which wait for both (bar_a)
+    };
+    auto clear_outputs = [&]() {
+#pragma unroll
+      for (int c = 0; c < H; c += 16) {
+        tmem_st16(dcol + c, zero16);
+        tmem_st16(dcol + (kColDC - kColD) + c, zero16);
+      }
     };
     auto store_keep = [&](int g0) {
       float *p = xw + (int64_t)g0 * ld;  // walks the columns (an address, dereferenced only inside X)
@@ -524,10 +599,9 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         }
         tc_fence_after();
         take_outputs();
-        // the previous tile's finals (stores issued, not waited for)
-        if (half == 0) store_keep((j - 1) * W - K - o);
       }
-      float s = 0.f;
+      clear_outputs();
+      float sa = 0.f, sb = 0.f;
       if (half == 1) {
         // the carry: the previous tile's last K outputs, or X's columns
         // [j W - K - o, j W - o) for the band's first tile
@@ -541,40 +615,54 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
           }
         }
 #pragma unroll
-        for (int c = 0; c < K; c++) s = fmaf(keep[c], keep[c], s);
-        st_split_cols<K>(tm, lane_off, 0, keep);
-      } else {
-        // the W new columns [j W - o, j W - o + W)
-        const int c0 = j * W - o;
-        if (bulk && !async::mbar_wait(&bar_n[q & 1], (unsigned)((q >> 1) & 1))) {
-          if (lane == 0) atomicOr(status, ERR_APPLY);
-          dead = 1;
-          break;
-        }
-        const float *nb_ = nvbuf + (size_t)(q & 1) * W * kRows + r;
-        const float *p = xr + (int64_t)c0 * ld;
+        for (int c = 0; c < K; c += 16) {
+          float v[16];
 #pragma unroll
-        for (int c = 0; c < W; c += 16) {
+          for (int qq = 0; qq < 16; qq += 2) {
+            v[qq] = keep[c + qq];
+            v[qq + 1] = keep[c + qq + 1];
+            sa = fmaf(v[qq], v[qq], sa);
+            sb = fmaf(v[qq + 1], v[qq + 1], sb);
+          }
+          st_split16(tm, lane_off, c, v);
+        }
+      }
+      // this half's share of the W new columns [j W - o, j W - o + W):
+      // columns [half W / 2, half W / 2 + W / 2) of them
+      const int c0 = j * W - o;
+      if (bulk && !async::mbar_wait(&bar_n, (unsigned)(q & 1))) {
+        if (lane == 0) atomicOr(status, ERR_APPLY);
+        dead = 1;
+        break;
+      }
+      {
+        const int cb = half * (W / 2);
+        const float *nb_ = nvbuf + r;
+        const float *p = xr + (int64_t)(c0 + cb) * ld;
+#pragma unroll
+        for (int c = 0; c < W / 2; c += 16) {
           float v[16];
 #pragma unroll
           for (int qq = 0; qq < 16; qq++, p += ld) {
-            const int col = c0 + c + qq;
+            const int col = c0 + cb + c + qq;
             const bool in = col >= 0 && col < ncol;
-            v[qq] = bulk ? (in ? nb_[(c + qq) * kRows] : 0.f) : ((rv && in) ? *p : 0.f);
-            s = fmaf(v[qq], v[qq], s);
+            v[qq] = bulk ? (in ? nb_[(cb + c + qq) * kRows] : 0.f) : ((rv && in) ? *p : 0.f);
           }
-          uint32_t h[16], l[16];
 #pragma unroll
-          for (int qq = 0; qq < 16; qq++) split_tf32(v[qq], h[qq], l[qq]);
-          tmem_st16(tm + lane_off + kColAH + K + c, h);
-          tmem_st16(tm + lane_off + kColAL + K + c, l);
+          for (int qq = 0; qq < 16; qq += 2) {
+            sa = fmaf(v[qq], v[qq], sa);
+            sb = fmaf(v[qq + 1], v[qq + 1], sb);
+          }
+          st_split16(tm, lane_off, K + cb + c, v);
         }
       }
-      in2 = s;
+      in2 = sa + sb;
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) async::mbar_arrive(&bar_a);
+      // the previous tile's finals, while this tile's MMAs run
+      if (q > 0 && half == 0) store_keep((j - 1) * W - K - o);
     }
     if (!dead) {
       if (!async::mbar_wait(&bar_m, (unsigned)((ntiles - 1) & 1))) {
@@ -608,7 +696,9 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   const int panels = (nrow + kRows - 1) / kRows;
   for (int b = 0; b < nbands; b++) {
     k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
-    k_tc_apply<NB><<<panels, kApplyThreads2, apply_smem, s>>>(X, ld, nrow, ncol, blobs, ranges, b, status);
+    k_tc_apply<NB><<<panels, kApplyThreads2, apply_smem, s>>>(X, ld, nrow, ncol,
+                                                              reinterpret_cast<const unsigned char *>(blobs), ranges,
+                                                              b, status);
   }
   return cudaGetLastError();
 }
@@ -621,11 +711,14 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // A band's tiles j run over floor((a + i + 1 + o) / W) for pair starts a in
 // [0, ncol - 2], i < K and o < W: at most (ncol + K + W) / W + 1 of them.
 static int tc_max_tiles(int ncol, int nb) { return (ncol + nb) / (nb / 2) + 2; }
+static size_t blob_bytes(int nb) {
+  return nb == 64 ? 2 * blob_part_bytes<64>() : nb == 96 ? 2 * blob_part_bytes<96>() : 2 * blob_part_bytes<128>();
+}
 size_t tc_workspace_bytes(int ncol, int T, int nb) {
   const int K = nb / 2;
   const int nbands = (T + K - 1) / K;
   const int max_tiles = tc_max_tiles(ncol, nb);
-  return align256((size_t)(nbands + 1) * sizeof(int2)) + (size_t)max_tiles * 2 * nb * nb * 4;
+  return align256((size_t)(nbands + 1) * sizeof(int2)) + (size_t)max_tiles * blob_bytes(nb);
 }
 
 cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
