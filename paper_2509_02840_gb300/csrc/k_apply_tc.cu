@@ -223,6 +223,23 @@ struct Cone {
 template <int NB>
 __host__ __device__ constexpr uint32_t blob_part_bytes() { return (uint32_t)Cone<NB>().off[NB / 8]; }
 
+// The table as a kernel parameter (filled on the host from Cone<NB>).
+struct ConeTable {
+  int n0[16], n1[16], off[17];
+};
+template <int NB>
+ConeTable cone_table() {
+  constexpr Cone<NB> c{};
+  ConeTable t{};
+  for (int s = 0; s < NB / 8; s++) {
+    t.n0[s] = c.n0[s];
+    t.n1[s] = c.n1[s];
+    t.off[s] = c.off[s];
+  }
+  t.off[NB / 8] = c.off[NB / 8];
+  return t;
+}
+
 // ---------------------------------------------------------------------------
 // the blocks of one band
 // ---------------------------------------------------------------------------
@@ -255,7 +272,7 @@ template <int NB>
 __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restrict__ Ca, const float2 *__restrict__ Cf,
                                                           const int4 *__restrict__ desc, int T, int cap, int b,
                                                           const int2 *__restrict__ ranges, float *__restrict__ blobs,
-                                                          int *__restrict__ status) {
+                                                          const ConeTable cone, int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2, S = NB + 4, G = kFormThreads / NB;
   extern __shared__ __align__(16) float Gs[];
   int *off = reinterpret_cast<int *>(Gs + NB * S);  // K + 1 offsets into rec
@@ -339,7 +356,6 @@ __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restr
     }
     __syncthreads();
   }
-  constexpr Cone<NB> cone{};
   constexpr uint32_t part = blob_part_bytes<NB>();
   unsigned char *oh = reinterpret_cast<unsigned char *>(blobs) + (size_t)blockIdx.x * 2 * part;
   unsigned char *ol = oh + part;
@@ -387,7 +403,7 @@ __host__ __device__ constexpr size_t apply_smem_bytes() {
 // 32 (w % 4) .. + 31, one row per thread, and half h = w / 4 of the work:
 // h = 0 the first W outputs (final after the tile), h = 1 the last K outputs,
 // which are the next tile's first K inputs (the carry); each half also takes
-// half of the W new input columns.  The two warps of a lane quarter combine
+// part of the W new input columns (32 + 32, 32 + 16 or 16 + 16).  The two warps of a lane quarter combine
 // their squared norms through shared memory (named barrier 1 + quarter).
 // Warp 8 issues the copies and MMAs.  Tensor memory: D (the main
 // accumulator) at columns [0, NB), A hi at [128, 128 + NB), A lo at
@@ -420,11 +436,14 @@ __device__ __forceinline__ void st_split16(uint32_t tm, uint32_t lane_off, int c
 template <int NB>
 __global__ void __launch_bounds__(kApplyThreads2, 1)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const unsigned char *__restrict__ blobs,
-               const int2 *__restrict__ ranges, int b, int *__restrict__ status) {
+               const int2 *__restrict__ ranges, int b, const ConeTable cone, int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: outputs per row warp
+  // the W new columns are split between the two halves in multiples of 16
+  // (the width of a tcgen05.st): half 0 takes kNw0, half 1 the rest
+  constexpr int kNw0 = (W / 2 + 15) / 16 * 16, kNw1 = W - kNw0;
+  static_assert(K % 16 == 0 && H % 16 == 0 && kNw0 % 16 == 0 && kNw1 % 16 == 0 && kNw1 > 0, "16-column groups");
   constexpr uint32_t kPart = blob_part_bytes<NB>(), kBlob = 2 * kPart;
   constexpr uint32_t kNvCol = kRows * 4u;  // bytes of one new column of the panel
-  constexpr Cone<NB> cone{};
   extern __shared__ __align__(1024) unsigned char sB[];  // [2][kBlob], then the new columns
   float *nvbuf = reinterpret_cast<float *>(sB + 2 * kBlob);  // [W][kRows]
   __shared__ uint64_t bar_b[2], bar_a, bar_m, bar_n;
@@ -628,7 +647,7 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         }
       }
       // this half's share of the W new columns [j W - o, j W - o + W):
-      // columns [half W / 2, half W / 2 + W / 2) of them
+      // columns [cb, cb + nw) of them
       const int c0 = j * W - o;
       if (bulk && !async::mbar_wait(&bar_n, (unsigned)(q & 1))) {
         if (lane == 0) atomicOr(status, ERR_APPLY);
@@ -636,11 +655,12 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         break;
       }
       {
-        const int cb = half * (W / 2);
+        const int cb = half ? kNw0 : 0, nw = half ? kNw1 : kNw0;
         const float *nb_ = nvbuf + r;
         const float *p = xr + (int64_t)(c0 + cb) * ld;
 #pragma unroll
-        for (int c = 0; c < W / 2; c += 16) {
+        for (int c = 0; c < kNw0; c += 16) {
+          if (c >= nw) break;  // (uniform per warp)
           float v[16];
 #pragma unroll
           for (int qq = 0; qq < 16; qq++, p += ld) {
@@ -694,11 +714,13 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
     e = cudaFuncSetAttribute(k_tc_apply<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem);
   if (e != cudaSuccess) return e;
   const int panels = (nrow + kRows - 1) / kRows;
+  const ConeTable cone = cone_table<NB>();
   for (int b = 0; b < nbands; b++) {
-    k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, status);
+    k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, cone,
+                                                             status);
     k_tc_apply<NB><<<panels, kApplyThreads2, apply_smem, s>>>(X, ld, nrow, ncol,
                                                               reinterpret_cast<const unsigned char *>(blobs), ranges,
-                                                              b, status);
+                                                              b, cone, status);
   }
   return cudaGetLastError();
 }
