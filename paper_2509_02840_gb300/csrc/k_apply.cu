@@ -290,7 +290,7 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
     if (cost <= best_cost) { best_cost = cost; best_R = R; best_csw = csw; }
   }
   if (fixed && best_R != variant) return cudaErrorNotSupported;
-  if (best_R == 0) return cudaErrorInvalidValue;  // a single vector column does not fit
+  if (best_R == 0) return cudaErrorNotSupported;  // a single vector column does not fit
   const size_t smem = (size_t)esz * best_csw * ncol;
   const int blocks = (nrow + best_R - 1) / best_R;
   cudaError_t e;
