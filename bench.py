@@ -29,7 +29,7 @@ reads the updated bidiagonal back every step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
   python bench.py --thin KR [--thin-fp64] [--size M] [--steps K] [--warmup W]
-    rank-KR tracking (bdu_thin_*, Sec. 5; mixed form unless --thin-fp64) on the network edge stream at
+    rank-KR tracking (bdu_thin_*, Sec. 4; mixed form unless --thin-fp64) on the network edge stream at
     m = n = M: each step is one symmetric edge insertion, i.e. two rank-1
     tracking steps; wall clock (every tracking step completes before it
     returns), with the CPU oracle timed on one tracking step beside it.
@@ -537,7 +537,7 @@ def run_gpu(args):
 
 
 def run_thin(args):
-    """Rank-k tracking on the network edge stream (Sec. 5 applied to the
+    """Rank-k tracking on the network edge stream (Sec. 4 applied to the
     Chung-Lu edge insertions): wall-clock rank-1 tracking steps per second."""
     import numpy as np
     import torch
@@ -568,7 +568,7 @@ def run_thin(args):
     ortho = max(float(np.linalg.norm(Qg.T @ Qg - np.eye(k), 2)), float(np.linalg.norm(Pg.T @ Pg - np.eye(k), 2)))
     steps = 2 * K
     form = "FP64" if args.thin_fp64 else "mixed: FP32 factors, FP64 middle band"
-    line = {"metric": f"rank-{k} tracking steps/s at m=n={m} (Sec. 5, {form})", "value": steps / dt,
+    line = {"metric": f"rank-{k} tracking steps/s at m=n={m} (Sec. 4, {form})", "value": steps / dt,
             "unit": "rank-1 tracking steps/s", "n_gpus": 1, "steps": steps, "warmup": 2 * W,
             "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "dtype": "f64" if args.thin_fp64 else "f32+f64",
             "data": "synthetic",

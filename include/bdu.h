@@ -316,7 +316,7 @@ void bdu_set_allocator(bdu_alloc_fn alloc, bdu_free_fn release, void *ctx);
 bdu_status bdu_update_rank1_noalloc(int64_t m, int64_t n, double *Q, double *d, double *e,
                                     double *P, const double *b, const double *c, void *stream);
 
-/* ---- Rank-k subspace tracking (Sec. 5, Eqs. lrup, defup, qrlr, equivlrup,
+/* ---- Rank-k subspace tracking (Sec. 4, Eqs. lrup, defup, qrlr, equivlrup,
  * bdlrup) --------------------------------------------------------------------
  * A thin factorization A ~ Q1 B P1^T with Q1 (m x k) and P1 (n x k) of
  * orthonormal columns and B k x k upper bidiagonal (diagonal d, superdiagonal

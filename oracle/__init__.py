@@ -305,7 +305,7 @@ def singular_values(d, e):
 
 
 # ---------------------------------------------------------------------------
-# Thin (rank-k) tracking, Sec. 5 (Eqs. lrup, defup, qrlr, equivlrup, bdlrup)
+# Thin (rank-k) tracking, Sec. 4 (Eqs. lrup, defup, qrlr, equivlrup, bdlrup)
 # ---------------------------------------------------------------------------
 THIN_TAU = 2.0 ** -40          # b is taken to lie in span(Q1) when ||b_perp|| <= THIN_TAU ||b||
 GOLDEN = 0.6180339887498949    # the FP64 value nearest (sqrt(5) - 1) / 2
@@ -339,7 +339,7 @@ def _augment(X, b):
 
 
 def thin_update(Q1, d, e, P1, b, c, full=False):
-    """One step of rank-k tracking (Sec. 5): A+ = Q1 B P1^T + b c^T with Q1 (m x k),
+    """One step of rank-k tracking (Sec. 4): A+ = Q1 B P1^T + b c^T with Q1 (m x k),
     P1 (n x k) orthonormal and B = diag-band(d, e) k x k upper bidiagonal.
 
     b+ = Q1^T b, b_perp = b - Q1 b+, delta = ||b_perp|| (Eq. defup; the

@@ -342,7 +342,7 @@ class Factorization:
 class ThinTracker:
     """Rank-k subspace tracking A ~ Q1 B P1^T under rank-1 updates, truncated
     back to rank k after each (bdu_thin_create / bdu_thin_update / bdu_thin_read;
-    Sec. 5).  precision FP64, or MIXED (FP32 thin factors, FP64 middle band)."""
+    Sec. 4).  precision FP64, or MIXED (FP32 thin factors, FP64 middle band)."""
 
     def __init__(self, Q1, d, e, P1, precision=FP64, stream=None, device=0, engine=0, graphs=True):
         L = load()

@@ -1876,7 +1876,7 @@ bdu_status bdu_set_timing(bdu_handle h, int on) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Rank-k tracking (Sec. 5, Eqs. lrup, defup, qrlr, equivlrup, bdlrup).  The
+// Rank-k tracking (Sec. 4, Eqs. lrup, defup, qrlr, equivlrup, bdlrup).  The
 // thin factors [Q1, new column] and [P1, new column] live in device buffers of
 // k+1 columns (FP64, or FP32 in the mixed form); the (k+1)-order middle matrix
 // is reduced by an internal handle of the same form (the chase and application

@@ -1,4 +1,4 @@
-"""Rank-k tracking on the GPU (bdu_thin_*; Sec. 5, Eqs. lrup - bdlrup) against
+"""Rank-k tracking on the GPU (bdu_thin_*; Sec. 4, Eqs. lrup - bdlrup) against
 the oracle's thin_update.  The projections and products are library BLAS
 calls whose summation order differs from numpy's, so the FP64 comparison is
 within FP64 rounding: the same removed index at every step, d, e and the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's rank-k tracking step (Sec. 5, Eqs. lrup - bdlrup),
+"""Pins of the oracle's rank-k tracking step (Sec. 4, Eqs. lrup - bdlrup),
 each checked against what the mathematics fixes rather than against the
 oracle's own formulas: the untruncated factorization reproduces A + b c^T,
 the truncation error it reports is the true Frobenius error, the factors stay
