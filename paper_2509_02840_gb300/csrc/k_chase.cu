@@ -472,13 +472,14 @@ struct Chaser {
     }
   }
 
-  // Runs one op of task k: the geometry of its next rotation (integer logic),
-  // the rotation itself (one shared code path), then the chase's next state.
-  // Left rotations go to recL, right ones to recR.
-  __device__ __forceinline__ void run_op(Task &k, Rec &recL, Rec &recR, int &nl, int &nr) {
-    // ---- plan
-    bool isrows = false, withv = false, doit = true;
-    int a = 0, lo = 0, w = 4, src = 0;
+  // Geometry of the next op of task k (integer logic): the pair (a, a+1) it
+  // rotates, its first row or column lo, width w, source and whether v
+  // rotates too; doit is false when the op does not exist (the state then
+  // only advances).
+  __device__ __forceinline__ void op_geometry(const Task &k, bool &isrows, int &a, int &lo, int &w, int &src,
+                                              bool &withv, bool &doit) const {
+    isrows = false; withv = false; doit = true;
+    a = 0; lo = 0; w = 4; src = 0;
     switch (k.st) {
       case S_L0: isrows = true; a = k.p - 1; lo = a; w = 3; src = 1; break;                    // left (j-1, j) on u
       case S_R1: a = k.ii + 1; lo = k.ii; w = 4; withv = true; break;                            // right (i+1, i+2)
@@ -490,7 +491,15 @@ struct Chaser {
       case S_CL: isrows = true; a = k.ii + 1; lo = k.ii; w = 5; break;                           // left (k+1, k+2)
       case S_CR: a = k.ii + 3; lo = k.ii + 1; w = 5; break;                                      // right (k+3, k+4)
     }
-    // ---- rotate
+  }
+
+  // Runs one op of task k: the geometry of its next rotation (integer logic),
+  // the rotation itself, then the chase's next state.  Left rotations go to
+  // recL, right ones to recR.
+  __device__ __forceinline__ void run_op(Task &k, Rec &recL, Rec &recR, int &nl, int &nr) {
+    bool isrows, withv, doit;
+    int a, lo, w, src;
+    op_geometry(k, isrows, a, lo, w, src, withv, doit);
     double b = 0.0;
     bool ok = false;
     if (doit) {
@@ -515,7 +524,11 @@ struct Chaser {
     // scheduled into the rotation above (measured: ~15% of the step time).
     asm volatile("" ::: "memory");
     if (ok) { if (isrows) nl++; else nr++; }
-    // ---- advance
+    advance(k, ok, b);
+  }
+
+  // The chase's next state after an op that rotated (ok) and left the bulge b.
+  __device__ __forceinline__ void advance(Task &k, bool ok, double b) {
     switch (k.st) {
       case S_L0: {
         const int i = k.p - 1;
@@ -567,6 +580,111 @@ struct Chaser {
         chase_start(k, k.ii + 3, b);
         return;
     }
+  }
+
+  // ---- one instruction sequence for the interior ops of every kind
+  //
+  // An interior op (the exec_st cases) is the pair (f, g) that defines the
+  // rotation plus three or four pairs rotated with it: the band pairs after
+  // the first when the first is the source, all w band pairs otherwise, then
+  // v(a), v(a+1) when v rotates.  The plan holds their offsets in the band
+  // buffer (six diagonals, then row 1, v and u, contiguous), so that the
+  // lanes of a warp whose chases are in different states run one sequence of
+  // FP64 instructions (which on GB300 cost the same for 1 or 32 lanes) instead
+  // of one per state.  Same operations on the same values as exec_st.
+  enum : unsigned char { kNoOp = 0, kUniform = 1, kGeneric = 2 };
+  struct Plan {
+    int xs, ys;        // the pair (f, g); becomes (r, 0)
+    int xo[4], yo[4];  // the rotated pairs
+    int a, lo, w, src;
+    unsigned char kind, nrot, inmask;  // inmask bit q: rotated pair q lies inside the matrix
+    bool rows, withv;
+  };
+  __device__ __forceinline__ void make_plan(const Task &k, Plan &P) const {
+    P.kind = kNoOp;
+    P.nrot = 0;
+    P.inmask = 0;
+    if (k.done) return;
+    bool doit;
+    op_geometry(k, P.rows, P.a, P.lo, P.w, P.src, P.withv, doit);
+    if (!doit) return;
+    const int a = P.a, lo = P.lo;
+    if (!(P.rows ? (a >= 2 && a + 1 <= N) : (lo >= 2 && a + 1 <= n))) { P.kind = kGeneric; return; }
+    P.kind = kUniform;
+    int c;  // diagonal of the first pair's first cell: geo_of(st).c
+    switch (k.st) {
+      case S_L1: case S_CL: c = 1; break;
+      case S_L0: case S_A: c = 2; break;
+      case S_R1: case S_P2: case S_C: c = 3; break;
+      default: c = 4; break;  // S_B, S_CR
+    }
+    const int ld = S.ld;
+    const int lim = (P.rows ? n : N) - lo;  // band pair q lies inside iff q <= lim
+    const int A0 = c * ld + (P.rows ? a : lo);
+    const int dA = P.rows ? ld : 1 - ld;  // first cell of the next pair
+    const int dB = P.rows ? 1 - ld : ld;  // second cell of a pair from its first
+    const int q0 = P.src == 0 ? 1 : 0;
+    const int nb = P.w - q0;
+    if (P.src == 0) {
+      P.xs = A0; P.ys = A0 + dB;
+    } else {
+      const int e0 = P.src == 1 ? (int)(S.uptr(0) - S.dg0) : (int)(S.cell(1, 0) - S.dg0);
+      P.xs = e0 + a; P.ys = e0 + a + 1;
+    }
+    const int v0 = (int)(S.vptr(0) - S.dg0);
+    unsigned mask = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int qq = q0 + q;
+      int xo = A0 + qq * dA, yo = xo + dB;
+      bool in = q < nb && qq <= lim;
+      if (P.withv && q == nb) { xo = v0 + a; yo = xo + 1; in = true; }
+      P.xo[q] = xo; P.yo[q] = yo;
+      mask |= in ? (1u << q) : 0u;
+    }
+    P.inmask = (unsigned char)mask;
+    P.nrot = (unsigned char)(nb + (P.withv ? 1 : 0));
+  }
+  // The loads of a uniform op (zeros for lanes without one), issued together.
+  __device__ __forceinline__ void load_plan(const Plan &P, double &f, double &g, double (&x)[4], double (&y)[4]) const {
+    const bool u = P.kind == kUniform;
+    f = u ? Store::load(S.dg0 + P.xs) : 0.0;
+    g = u ? Store::load(S.dg0 + P.ys) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const bool in = u && ((P.inmask >> q) & 1);
+      x[q] = in ? Store::load(S.dg0 + P.xo[q]) : 0.0;
+      y[q] = in ? Store::load(S.dg0 + P.yo[q]) : 0.0;
+    }
+  }
+  // Every lane of the warp calls this (the fourth pair is skipped when no
+  // active lane has one); lanes with act store.  Returns act && rotated.
+  __device__ __forceinline__ bool exec_uniform(const Plan &P, bool act, double f, double g, double (&x)[4],
+                                               double (&y)[4], double &c, double &s, double &last) {
+    f = act ? f : 0.0;
+    g = act ? g : 0.0;
+    double r;
+    const bool ok = A::rot(f, g, c, s, r) && act;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const double nx = A::px(c, s, x[q], y[q]), ny = A::py(c, s, x[q], y[q]);
+      x[q] = nx; y[q] = ny;
+    }
+    if (__any_sync(0xffffffffu, act && P.nrot == 4)) {
+      const double nx = A::px(c, s, x[3], y[3]), ny = A::py(c, s, x[3], y[3]);
+      x[3] = nx; y[3] = ny;
+    }
+    if (ok) {
+      S.dg0[P.xs] = r;
+      S.dg0[P.ys] = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if ((P.inmask >> q) & 1) { S.dg0[P.xo[q]] = x[q]; S.dg0[P.yo[q]] = y[q]; }
+      }
+      if (rx) rotate_extra(P.rows ? Ux : Vx, P.rows ? m : n, P.a, c, s);
+    }
+    last = (P.nrot == 4 && !P.withv) ? x[3] : x[2];
+    return ok;
   }
 };
 
@@ -794,26 +912,56 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase_batch(const ChaseArgs *__
 // engine 2: a thread-block cluster
 // ----------------------------------------------------------------------------
 // The band stays in global memory (L2); chase t runs on CTA t % CS, logical
-// slot (t / CS) % S.  Step protocol: a cluster barrier opens every step, so
-// all band writes and status words of the previous step are visible.  At the
-// end of a step every CTA pushes (asynchronous remote stores) its status words
-// into the next CTA's mirror -- chase t-1 always lives on the CTA before chase
-// t's -- and its counters (chases done, phase-1 chases done, lowest
-// unfinished chase) into every CTA's inbox, so that the reads on a step's
-// critical path are local.  Totals are one step old, which is conservative.
+// slot (t / CS) % S.  Steps are separated by the cluster barrier, split into
+// its arrive (release) and wait (acquire) halves:
+//
+//   wait      every band write and status word of the previous step is
+//             visible cluster-wide;
+//   loads     the status word of chase t-1 and the counters (shared memory)
+//             are read first, then the planned op's band loads are issued at
+//             once (speculatively: a lane whose chase may not run discards
+//             them), so that the look-back overlaps their latency;
+//   look-back may the chase run (lags behind the nearest earlier unfinished
+//             chase, as in the one-CTA engine);
+//   op        the rotation and its pairs, then their stores;
+//   then      the chase's next state, its rotation record, a finished
+//             chase's bookkeeping and the next task, the plan (cell offsets)
+//             of the next op: work that lets the band stores drain before
+//             the barrier's release has to wait for them;
+//   publish   status words into this CTA's table and the next CTA's mirror
+//             (chase t-1 always lives on the CTA before chase t's), each
+//             warp's counters (chases done, phase-1 chases done, lowest
+//             unfinished chase) into every CTA's inbox;
+//   arrive.
+//
+// Status words and inbox slots alternate with the step's parity: a slot
+// written in step s is read in step s+1 and rewritten in step s+2, after
+// every reader of step s+1 has arrived.  So every CTA reads the same totals
+// in a step and leaves the loop in the same step.  Totals are one step old,
+// which is conservative.
+__device__ __forceinline__ void cluster_arrive() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+constexpr int kMaxWarps = kMaxThreads / 32;
+
 template <bool FAST>
 __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   __shared__ int2 st[2][kMaxThreads];    // this CTA's chase status words
   __shared__ int2 pred[2][kMaxThreads];  // mirror of the previous CTA's status words
-  __shared__ int inbox[2][kMaxCluster][4];  // every CTA's counters: done, p1done, min unfinished
-  __shared__ int my_done, my_p1, my_min[2];
+  __shared__ int4 inbox[2][kMaxCluster * kMaxWarps];  // every warp's counters (CTA-major): done, p1 done, min unfinished
   __shared__ unsigned long long cnt[9];
 
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int cta = (int)cl.block_rank();
   const int m = Ar.m, n = Ar.n, N = (m > n) ? n + 1 : n;
-  const int S = blockDim.x, me = threadIdx.x;
+  const int S = blockDim.x, me = threadIdx.x, lane = me & 31, wid = me >> 5;
+  const int NW = (S + 31) / 32;
   const int T = Ar.st.T;
   const int p1 = N - 1, p2 = n > 2 ? n - 2 : 0;
   const int next = (cta + 1) % CS;
@@ -823,7 +971,8 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   if (cta == 0 && me == 0) run_spike<FAST>(Ar, &cnt[0]);
   cl.sync();  // spike done (global u)
 
-  Chaser<GlobalStore, FAST> K;
+  using Ch = Chaser<GlobalStore, FAST>;
+  Ch K;
   K.zero = &g_zero_sink[0];
   K.S.dg0 = Ar.band.dg[0]; K.S.ld = N + 2;
   K.S.r1 = Ar.band.r1; K.S.u = Ar.band.u; K.S.v = Ar.band.v;
@@ -847,32 +996,35 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   bind_rec(Ar, k, recL, recR);
   st[0][myslot] = enc(k);
   pred_next[myslot] = enc(k);  // slot 0 of the next CTA's mirror
-  if (me == 0) {
-    my_done = 0; my_p1 = 0; my_min[0] = INT_MAX; my_min[1] = INT_MAX;
-    for (int c = 0; c < CS; c++) {
-      int *ib = cl.map_shared_rank(&inbox[1][cta][0], c);
-      ib[0] = 0; ib[1] = 0; ib[2] = cta;
+  int ndone = 0, np1 = 0;      // this thread's finished chases (all, phase 1)
+  {
+    const int mn = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);
+    if (lane < CS) {
+      int4 *ib = cl.map_shared_rank(&inbox[1][cta * NW + wid], lane);
+      *ib = make_int4(0, 0, mn, 0);
     }
   }
+  typename Ch::Plan P;
+  K.make_plan(k, P);
   bool fold_done = false;
   const long long max_steps = Ar.step_budget > 0 ? Ar.step_budget : 64LL * (n + 16) + 4096;
   long long step = 0;
+  cluster_arrive();
   for (;; step++) {
-    cl.sync();  // every write of the previous step is visible cluster-wide
+    cluster_wait();  // every write of the previous step is visible cluster-wide
     const int rd = step & 1, wr = rd ^ 1;
-    // this step's lowest-unfinished slot is my_min[rd]; my_min[wr] was read by
-    // the previous step's pushes, all done before the barrier above
-    if (me == 0) my_min[wr] = INT_MAX;
-    // cluster totals at the end of the previous step (inbox slot wr): lane c
-    // reads CTA c's counters, then warp reductions
-    int sd, sp1, fr;
-    {
-      const int lane = me & 31;
-      const bool has = lane < CS;
-      sd = __reduce_add_sync(0xffffffffu, has ? inbox[wr][lane][0] : 0);
-      sp1 = __reduce_add_sync(0xffffffffu, has ? inbox[wr][lane][1] : 0);
-      fr = __reduce_min_sync(0xffffffffu, has ? inbox[wr][lane][2] : INT_MAX);
+    const int2 wpred = pred[rd][pslot];  // chase t-1 (local mirror of the previous CTA)
+    // cluster totals at the end of the previous step (inbox slot wr)
+    int sd = 0, sp1 = 0, fr = INT_MAX;
+    for (int e = lane; e < CS * NW; e += 32) {
+      const int4 v = inbox[wr][e];
+      sd += v.x; sp1 += v.y; fr = v.z < fr ? v.z : fr;
     }
+    double f, g, x[4], y[4];
+    K.load_plan(P, f, g, x, y);
+    sd = __reduce_add_sync(0xffffffffu, sd);
+    sp1 = __reduce_add_sync(0xffffffffu, sp1);
+    fr = __reduce_min_sync(0xffffffffu, fr);
     if (fr == INT_MAX) fr = T;
     if (!fold_done && sp1 == p1) {
       // fold: row 1 += u(1) v^T, the columns split over the cluster's threads
@@ -881,14 +1033,16 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
         K.S.r1[j] = Arith<FAST>::px(1.0, u1, __ldcg(K.S.r1 + j), __ldcg(K.S.v + j));
       cl.sync();
       fold_done = true;
+      K.load_plan(P, f, g, x, y);  // row 1 has changed
     }
     if (fold_done && sd == T) break;
     if (step >= max_steps) {
       if (me == 0) atomicOr(Ar.status, ERR_STEPS);
       break;
     }
+    bool run = false;
+    const int t = k.t;
     if (!k.done) {
-      const int t = k.t;
       bool ok = !(t >= p1 && !fold_done);
       int reach = INT_MAX;  // last position this chase may reach in this step
       if (ok) {
@@ -898,7 +1052,7 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
         for (int u = t - 1; u >= stop; u--) {
           int2 w;
           if (u == t - 1) {
-            w = pred[rd][pslot];  // local mirror of the previous CTA
+            w = wpred;
           } else {
             const int2 *su = cl.map_shared_rank(&st[0][0], u % CS);
             w = su[rd * kMaxThreads + (u / CS) % S];
@@ -910,48 +1064,62 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
           break;
         }
       }
-      // Keeps the op's band loads from being scheduled into the look-back
-      // above (measured: about a quarter of the step time at n = 4096).
-      asm volatile("" ::: "memory");
-      for (int rep = 0; rep < kOpsPerStep && ok && k.pos <= reach; rep++) {
-        K.run_op(k, recL, recR, nl, nr);
-        k.started = true;
-        if (k.done) {
-          Ar.st.Ln[t] = nl;
-          Ar.st.Rn[t] = nr;
-          atomicAdd(&cnt[k.phase], (unsigned long long)nl);
-          atomicAdd(&cnt[4 + k.phase], (unsigned long long)nr);
-          if (t < p1) atomicAdd(&my_p1, 1);
-          atomicAdd(&my_done, 1);
-          task_init(k, t + stride, T, N, n);
-          nl = nr = 0;
-          bind_rec(Ar, k, recL, recR);
-          break;
-        }
+      run = ok && k.pos <= reach;
+    }
+    // the op: one FP64 instruction sequence for the warp's interior ops, the
+    // general form (ops touching row 1) apart
+    bool rot = false, pend = false;
+    double c = 0.0, sn = 0.0, b = 0.0;
+    if (__any_sync(0xffffffffu, run && P.kind == Ch::kUniform)) {
+      rot = K.exec_uniform(P, run && P.kind == Ch::kUniform, f, g, x, y, c, sn, b);
+      pend = rot;
+    }
+    if (run && P.kind == Ch::kGeneric) rot = K.exec(P.rows, P.a, P.lo, P.w, P.src, P.withv, recL, recR, b);
+    bool fin = false;
+    if (run) {
+      if (rot) { if (P.rows) nl++; else nr++; }
+      K.advance(k, rot, b);
+      k.started = true;
+      if (k.done) {
+        fin = true;
+        ndone++;
+        if (t < p1) np1++;
       }
     }
+    if (pend) (P.rows ? recL : recR).push(c, sn, P.a);
+    if (fin) {
+      Ar.st.Ln[t] = nl;
+      Ar.st.Rn[t] = nr;
+      atomicAdd(&cnt[k.phase], (unsigned long long)nl);
+      atomicAdd(&cnt[4 + k.phase], (unsigned long long)nr);
+      task_init(k, t + stride, T, N, n);  // the slot moves on: chase t reads as finished
+      nl = nr = 0;
+      bind_rec(Ar, k, recL, recR);
+    }
+    K.make_plan(k, P);
+    // publish
+    const int2 sw = enc(k);
+    st[wr][myslot] = sw;
+    pred_next[wr * kMaxThreads + myslot] = sw;  // push to the next CTA's mirror
     {
-      const int mn = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);
-      if ((me & 31) == 0 && mn != INT_MAX) atomicMin(&my_min[rd], mn);
+      const int wd = __reduce_add_sync(0xffffffffu, ndone);
+      const int wp = __reduce_add_sync(0xffffffffu, np1);
+      const int wm = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);  // lowest unfinished chase
+      if (lane < CS) {
+        int4 *ib = cl.map_shared_rank(&inbox[rd][cta * NW + wid], lane);
+        *ib = make_int4(wd, wp, wm, 0);
+      }
     }
-    const int2 w = enc(k);
-    st[wr][myslot] = w;
-    pred_next[wr * kMaxThreads + myslot] = w;  // push to the next CTA's mirror
-    __syncthreads();
-    if (me < CS) {
-      // push this CTA's counters into every CTA's inbox (slot rd)
-      int *ib = cl.map_shared_rank(&inbox[rd][cta][0], me);
-      ib[0] = my_done;
-      ib[1] = my_p1;
-      ib[2] = my_min[rd];
-    }
+    cluster_arrive();
   }
   if (me == 0) {
     if (cta == 0) cnt[8] = step;
+  }
+  cl.sync();  // every CTA has left the loop; the phase counters are complete
+  if (me == 0) {
     for (int q = 0; q < 9; q++)
       if (cnt[q]) atomicAdd(&Ar.counters[q], cnt[q]);
   }
-  cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 template <bool FAST>
@@ -1086,3 +1254,4 @@ cudaError_t launch_chase(const ChaseArgs &a0, cudaStream_t s) {
 }
 
 }  // namespace bdu
+
