@@ -923,22 +923,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase_batch(const ChaseArgs *__
 //             them), so that the look-back overlaps their latency;
 //   look-back may the chase run (lags behind the nearest earlier unfinished
 //             chase, as in the one-CTA engine);
-//   op        the rotation and its pairs, then their stores;
-//   then      the chase's next state, its rotation record, a finished
-//             chase's bookkeeping and the next task, the plan (cell offsets)
-//             of the next op: work that lets the band stores drain before
-//             the barrier's release has to wait for them;
+//   op        the rotation and its pairs, their stores, the chase's next
+//             state;
 //   publish   status words into this CTA's table and the next CTA's mirror
 //             (chase t-1 always lives on the CTA before chase t's), each
 //             warp's counters (chases done, phase-1 chases done, lowest
 //             unfinished chase) into every CTA's inbox;
-//   arrive.
+//   arrive    (release: waits for the band stores to be performed);
+//   deferred  the rotation record, a finished chase's bookkeeping and the
+//             next task, the plan (cell offsets) of the next op: nothing any
+//             CTA reads before the next barrier.  (Measured at n = 4096: 146
+//             ms per column against 158 with this work before the arrive.)
 //
 // Status words and inbox slots alternate with the step's parity: a slot
-// written in step s is read in step s+1 and rewritten in step s+2, after
-// every reader of step s+1 has arrived.  So every CTA reads the same totals
-// in a step and leaves the loop in the same step.  Totals are one step old,
-// which is conservative.
+// written in step s is read in step s+1 and rewritten in step s+2 or later,
+// after every reader of step s+1 has arrived.  So every CTA reads the same
+// totals in a step and leaves the loop in the same step.  Totals are at least
+// one step old, which is conservative.
 __device__ __forceinline__ void cluster_arrive() {
   __syncwarp();
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -948,6 +949,11 @@ __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 constexpr int kMaxWarps = kMaxThreads / 32;
+// The cluster totals (chases done, phase-1 chases done, lowest unfinished
+// chase) are exchanged every kTotalsEvery steps; between exchanges the last
+// values stand, which only delays the fold and the exit by a few steps and
+// makes the look-back scan a few finished chases more.
+constexpr int kTotalsEvery = 8;
 
 template <bool FAST>
 __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
@@ -957,11 +963,11 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   __shared__ unsigned long long cnt[9];
 
   cg::cluster_group cl = cg::this_cluster();
-  const int CS = (int)cl.num_blocks();
+  constexpr int CS = kMaxCluster;  // the launch's cluster size; chase t runs on CTA t % CS
   const int cta = (int)cl.block_rank();
   const int m = Ar.m, n = Ar.n, N = (m > n) ? n + 1 : n;
-  const int S = blockDim.x, me = threadIdx.x, lane = me & 31, wid = me >> 5;
-  const int NW = (S + 31) / 32;
+  const int S = blockDim.x, me = threadIdx.x, lane = me & 31, wid = me >> 5;  // S: a power of two
+  const int NW = S / 32;
   const int T = Ar.st.T;
   const int p1 = N - 1, p2 = n > 2 ? n - 2 : 0;
   const int next = (cta + 1) % CS;
@@ -1007,35 +1013,47 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   typename Ch::Plan P;
   K.make_plan(k, P);
   bool fold_done = false;
+  int sd = 0, sp1 = 0, fr = 0;  // cluster totals, read every kTotalsEvery steps
   const long long max_steps = Ar.step_budget > 0 ? Ar.step_budget : 64LL * (n + 16) + 4096;
   long long step = 0;
   cluster_arrive();
   for (;; step++) {
     cluster_wait();  // every write of the previous step is visible cluster-wide
     const int rd = step & 1, wr = rd ^ 1;
+    const bool totals = (step & (kTotalsEvery - 1)) == 0;
     const int2 wpred = pred[rd][pslot];  // chase t-1 (local mirror of the previous CTA)
-    // cluster totals at the end of the previous step (inbox slot wr)
-    int sd = 0, sp1 = 0, fr = INT_MAX;
-    for (int e = lane; e < CS * NW; e += 32) {
-      const int4 v = inbox[wr][e];
-      sd += v.x; sp1 += v.y; fr = v.z < fr ? v.z : fr;
+    int4 iv[kMaxCluster * kMaxWarps / 32];
+    if (totals) {
+      // cluster totals at the end of the previous step (inbox slot wr)
+#pragma unroll
+      for (int q = 0; q < kMaxCluster * kMaxWarps / 32; q++) {
+        const int e = lane + 32 * q;
+        iv[q] = e < CS * NW ? inbox[wr][e] : make_int4(0, 0, INT_MAX, 0);
+      }
     }
     double f, g, x[4], y[4];
     K.load_plan(P, f, g, x, y);
-    sd = __reduce_add_sync(0xffffffffu, sd);
-    sp1 = __reduce_add_sync(0xffffffffu, sp1);
-    fr = __reduce_min_sync(0xffffffffu, fr);
-    if (fr == INT_MAX) fr = T;
-    if (!fold_done && sp1 == p1) {
-      // fold: row 1 += u(1) v^T, the columns split over the cluster's threads
-      const double u1 = __ldcg(K.S.u + 1);
-      for (int j = cta * S + me + 1; j <= n; j += CS * S)
-        K.S.r1[j] = Arith<FAST>::px(1.0, u1, __ldcg(K.S.r1 + j), __ldcg(K.S.v + j));
-      cl.sync();
-      fold_done = true;
-      K.load_plan(P, f, g, x, y);  // row 1 has changed
+    if (totals) {
+      int a0 = 0, a1 = 0, a2 = INT_MAX;
+#pragma unroll
+      for (int q = 0; q < kMaxCluster * kMaxWarps / 32; q++) {
+        a0 += iv[q].x; a1 += iv[q].y; a2 = iv[q].z < a2 ? iv[q].z : a2;
+      }
+      sd = __reduce_add_sync(0xffffffffu, a0);
+      sp1 = __reduce_add_sync(0xffffffffu, a1);
+      fr = __reduce_min_sync(0xffffffffu, a2);
+      if (fr == INT_MAX) fr = T;
+      if (!fold_done && sp1 == p1) {
+        // fold: row 1 += u(1) v^T, the columns split over the cluster's threads
+        const double u1 = __ldcg(K.S.u + 1);
+        for (int j = cta * S + me + 1; j <= n; j += CS * S)
+          K.S.r1[j] = Arith<FAST>::px(1.0, u1, __ldcg(K.S.r1 + j), __ldcg(K.S.v + j));
+        cl.sync();
+        fold_done = true;
+        K.load_plan(P, f, g, x, y);  // row 1 has changed
+      }
+      if (fold_done && sd == T) break;
     }
-    if (fold_done && sd == T) break;
     if (step >= max_steps) {
       if (me == 0) atomicOr(Ar.status, ERR_STEPS);
       break;
@@ -1054,8 +1072,8 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
           if (u == t - 1) {
             w = wpred;
           } else {
-            const int2 *su = cl.map_shared_rank(&st[0][0], u % CS);
-            w = su[rd * kMaxThreads + (u / CS) % S];
+            const int2 *su = cl.map_shared_rank(&st[0][0], u & (CS - 1));
+            w = su[rd * kMaxThreads + ((u / CS) & (S - 1))];
           }
           if (w.x < u) { ok = false; break; }
           if (w.x > u || (w.y & 1)) continue;
@@ -1086,6 +1104,23 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
         if (t < p1) np1++;
       }
     }
+    // publish
+    const int2 sw = enc(k);  // a finished chase reads as finished
+    st[wr][myslot] = sw;
+    pred_next[wr * kMaxThreads + myslot] = sw;  // push to the next CTA's mirror
+    if (((step + 1) & (kTotalsEvery - 1)) == 0) {  // read in the next step
+      const int wd = __reduce_add_sync(0xffffffffu, ndone);
+      const int wp = __reduce_add_sync(0xffffffffu, np1);
+      // lowest unfinished chase of the warp (a finished chase's slot moves on
+      // to chase t + stride)
+      const int wm = __reduce_min_sync(0xffffffffu, !k.done ? k.t : (fin && t + stride < T ? t + stride : INT_MAX));
+      if (lane < CS) {
+        int4 *ib = cl.map_shared_rank(&inbox[rd][cta * NW + wid], lane);
+        *ib = make_int4(wd, wp, wm, 0);
+      }
+    }
+    cluster_arrive();
+    // deferred
     if (pend) (P.rows ? recL : recR).push(c, sn, P.a);
     if (fin) {
       Ar.st.Ln[t] = nl;
@@ -1097,20 +1132,6 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
       bind_rec(Ar, k, recL, recR);
     }
     K.make_plan(k, P);
-    // publish
-    const int2 sw = enc(k);
-    st[wr][myslot] = sw;
-    pred_next[wr * kMaxThreads + myslot] = sw;  // push to the next CTA's mirror
-    {
-      const int wd = __reduce_add_sync(0xffffffffu, ndone);
-      const int wp = __reduce_add_sync(0xffffffffu, np1);
-      const int wm = __reduce_min_sync(0xffffffffu, k.done ? INT_MAX : k.t);  // lowest unfinished chase
-      if (lane < CS) {
-        int4 *ib = cl.map_shared_rank(&inbox[rd][cta * NW + wid], lane);
-        *ib = make_int4(wd, wp, wm, 0);
-      }
-    }
-    cluster_arrive();
   }
   if (me == 0) {
     if (cta == 0) cnt[8] = step;
@@ -1135,6 +1156,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_chase_cluster_batch(const Chase
   engine_cluster<FAST>(Ar);
 }
 
+// Threads per CTA of the cluster engine: a slot for each of the ~n/3 chases in
+// flight, a power of two (64..kMaxThreads) so that slot arithmetic is shifts.
+int cluster_threads(int n) {
+  const int need = (n / 3 + 16) / kMaxCluster;
+  int t = 64;
+  while (t < need && t < kMaxThreads) t *= 2;
+  return t;
+}
+
 template <bool FAST>
 cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
   const int n = a.n, m = a.m;
@@ -1149,9 +1179,7 @@ cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
     // cluster engine
     const int CS = kMaxCluster;
     const size_t dyn = 0;
-    int threads = ((n / 3 + 16) / CS + 31) / 32 * 32;
-    if (threads < 64) threads = 64;
-    if (threads > kMaxThreads) threads = kMaxThreads;
+    const int threads = cluster_threads(n);
     cudaError_t e = cudaFuncSetAttribute(k_chase_cluster<FAST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -1192,9 +1220,7 @@ cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int 
                                        cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const int CS = kMaxCluster;
-  int threads = ((max_n / 3 + 16) / CS + 31) / 32 * 32;
-  if (threads < 64) threads = 64;
-  if (threads > kMaxThreads) threads = kMaxThreads;
+  const int threads = cluster_threads(max_n);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS * count);
   cfg.blockDim = dim3(threads);
