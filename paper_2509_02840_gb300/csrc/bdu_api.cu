@@ -1452,7 +1452,7 @@ static bdu_status update_batch_held(bdu_handle *hs, int count, const double *con
       a.st = h->st; a.status = h->status; a.counters = h->counters;
       a.fast = precision == BDU_MIXED ? 1 : 0;
       a.step_budget = h->opt.step_budget;
-      if (n >= kClusterBatchMinN) {
+      if (n >= kClusterBatchMinN && chase_cluster_fits(m, n)) {
         a.engine = 2;
         chase_l.push_back(a);
         ucol_l.push_back(h->U + k * m);

@@ -115,6 +115,9 @@ struct ProjItem {
 
 // Launchers (return the launch error, if any).
 cudaError_t launch_chase(const ChaseArgs &a, cudaStream_t s);
+// The cluster chase engine keeps the band in its CTAs' shared memory; false
+// when (m, n) is too large for that (n above about 48000).
+bool chase_cluster_fits(int m, int n);
 
 cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, int ncol,
                            const double *B, int64_t ldb, int r, double *U, int64_t ldu,

@@ -189,23 +189,62 @@ struct LocalStore {
   static __device__ __forceinline__ double load(const double *p) { return *p; }
   __device__ __forceinline__ double *uptr(int i) const { return u + i; }
   __device__ __forceinline__ double *vptr(int j) const { return v + j; }
+  // cell handles of the uniform op: offsets from dg0 (one contiguous buffer)
+  using H = int;
+  __device__ __forceinline__ H h_band(int diag, int i) const { return diag * ld + i; }
+  __device__ __forceinline__ H h_r1(int j) const { return (int)(r1 - dg0) + j; }
+  __device__ __forceinline__ H h_v(int j) const { return (int)(v - dg0) + j; }
+  __device__ __forceinline__ H h_u(int i) const { return (int)(u - dg0) + i; }
+  __device__ __forceinline__ double ld_h(H h) const { return dg0[h]; }
+  __device__ __forceinline__ void st_h(H h, double x) const { dg0[h] = x; }
 };
 
-// The band in global memory, shared by the CTAs of a cluster.  The ~3 MB of
-// band, row 1, u and v stay in L2; loads bypass L1 (ld.global.cg) so that each
-// step sees the writes other SMs made in earlier steps, which the cluster
-// barrier between steps orders.
-struct GlobalStore {
-  double *dg0;  // diagonal o starts at dg0 + (o+2) * ld
-  int ld;
-  double *r1, *u, *v;
-  __device__ __forceinline__ double *cell(int i, int j) const {
-    return (i == 1) ? r1 + j : dg0 + (size_t)(j - i + 2) * ld + i;
+// The band of a thread-block cluster, in distributed shared memory: nine
+// arrays indexed 0..N+1 (the six diagonals by row, row 1 and v by column, u by
+// row), index i of every array held by CTA i % 16 at slot i / 16 of its slice
+// (the same shared-memory offset in every CTA; interleaved, so that the rows
+// the chases are working on are spread over all the CTAs).  An op's cells are
+// reached by their shared::cluster addresses (mapa), the general path's by
+// generic pointers into the cluster's shared-memory window; the cluster
+// barrier between steps orders every CTA's stores before the next step's
+// loads.
+struct DsmStore {
+  double *loc;    // this CTA's slice (generic address)
+  uint32_t base;  // this CTA's slice (shared::cta address)
+  int B;          // indices per array and CTA
+  using H = uint32_t;  // a cell's shared::cluster address
+  // (plans also form handles of cells they never touch -- pairs past the
+  // matrix edge, unused slots -- so both coordinates are clamped into range)
+  __device__ __forceinline__ H h_at(int arr, int idx) const {
+    arr = arr < 0 ? 0 : (arr > 8 ? 8 : arr);
+    idx = idx < 0 ? 0 : (idx < kMaxCluster * B ? idx : kMaxCluster * B - 1);
+    const uint32_t a = base + (uint32_t)(arr * B + (idx >> 4)) * 8u;
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(idx & (kMaxCluster - 1)));
+    return r;
   }
-  __device__ __forceinline__ double *uptr(int i) const { return u + i; }
-  __device__ __forceinline__ double *vptr(int j) const { return v + j; }
-  static __device__ __forceinline__ double load(const double *p) { return __ldcg(p); }
+  __device__ __forceinline__ H h_band(int diag, int i) const { return h_at(diag, i); }
+  __device__ __forceinline__ H h_r1(int j) const { return h_at(6, j); }
+  __device__ __forceinline__ H h_v(int j) const { return h_at(7, j); }
+  __device__ __forceinline__ H h_u(int i) const { return h_at(8, i); }
+  __device__ __forceinline__ double ld_h(H h) const {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];\n" : "=d"(v) : "r"(h) : "memory");
+    return v;
+  }
+  __device__ __forceinline__ void st_h(H h, double v) const {
+    asm volatile("st.shared::cluster.f64 [%0], %1;\n" ::"r"(h), "d"(v) : "memory");
+  }
+  __device__ __forceinline__ double *gp(int arr, int idx) const {
+    return static_cast<double *>(__cluster_map_shared_rank(loc + arr * B + (idx >> 4), (unsigned)(idx & (kMaxCluster - 1))));
+  }
+  __device__ __forceinline__ double *cell(int i, int j) const { return (i == 1) ? gp(6, j) : gp(j - i + 2, i); }
+  __device__ __forceinline__ double *uptr(int i) const { return gp(8, i); }
+  __device__ __forceinline__ double *vptr(int j) const { return gp(7, j); }
+  static __device__ __forceinline__ double load(const double *p) { return *p; }
 };
+// Slice of the cluster band per CTA: B indices of each array, 16 B >= N + 2.
+__host__ __device__ inline int dsm_slice(int N) { return (N + 2 + kMaxCluster - 1) / kMaxCluster; }
 
 struct Rec {
   double *c, *s;
@@ -587,15 +626,16 @@ struct Chaser {
   // An interior op (the exec_st cases) is the pair (f, g) that defines the
   // rotation plus three or four pairs rotated with it: the band pairs after
   // the first when the first is the source, all w band pairs otherwise, then
-  // v(a), v(a+1) when v rotates.  The plan holds their offsets in the band
-  // buffer (six diagonals, then row 1, v and u, contiguous), so that the
-  // lanes of a warp whose chases are in different states run one sequence of
-  // FP64 instructions (which on GB300 cost the same for 1 or 32 lanes) instead
-  // of one per state.  Same operations on the same values as exec_st.
+  // v(a), v(a+1) when v rotates.  The plan holds their addresses (the
+  // store's cell handles), so that the lanes of a warp whose chases are in
+  // different states run one sequence of FP64 instructions (which on GB300
+  // cost the same for 1 or 32 lanes) instead of one per state.  Same
+  // operations on the same values as exec_st.
   enum : unsigned char { kNoOp = 0, kUniform = 1, kGeneric = 2 };
+  using H = typename Store::H;
   struct Plan {
-    int xs, ys;        // the pair (f, g); becomes (r, 0)
-    int xo[4], yo[4];  // the rotated pairs
+    H xs, ys;        // the pair (f, g); becomes (r, 0)
+    H xo[4], yo[4];  // the rotated pairs
     int a, lo, w, src;
     unsigned char kind, nrot, inmask;  // inmask bit q: rotated pair q lies inside the matrix
     bool rows, withv;
@@ -611,34 +651,27 @@ struct Chaser {
     const int a = P.a, lo = P.lo;
     if (!(P.rows ? (a >= 2 && a + 1 <= N) : (lo >= 2 && a + 1 <= n))) { P.kind = kGeneric; return; }
     P.kind = kUniform;
-    int c;  // diagonal of the first pair's first cell: geo_of(st).c
-    switch (k.st) {
-      case S_L1: case S_CL: c = 1; break;
-      case S_L0: case S_A: c = 2; break;
-      case S_R1: case S_P2: case S_C: c = 3; break;
-      default: c = 4; break;  // S_B, S_CR
-    }
-    const int ld = S.ld;
+    // band pair q: rows (a, a+1) at column lo+q, diagonals c+q and c+q-1; or
+    // columns (a, a+1) at row lo+q, diagonals c-q and c-q+1 (geo_of(st).c)
+    const int c = P.rows ? lo - a + 2 : a - lo + 2;
     const int lim = (P.rows ? n : N) - lo;  // band pair q lies inside iff q <= lim
-    const int A0 = c * ld + (P.rows ? a : lo);
-    const int dA = P.rows ? ld : 1 - ld;  // first cell of the next pair
-    const int dB = P.rows ? 1 - ld : ld;  // second cell of a pair from its first
     const int q0 = P.src == 0 ? 1 : 0;
     const int nb = P.w - q0;
     if (P.src == 0) {
-      P.xs = A0; P.ys = A0 + dB;
+      P.xs = P.rows ? S.h_band(c, a) : S.h_band(c, lo);
+      P.ys = P.rows ? S.h_band(c - 1, a + 1) : S.h_band(c + 1, lo);
     } else {
-      const int e0 = P.src == 1 ? (int)(S.uptr(0) - S.dg0) : (int)(S.cell(1, 0) - S.dg0);
-      P.xs = e0 + a; P.ys = e0 + a + 1;
+      P.xs = P.src == 1 ? S.h_u(a) : S.h_r1(a);
+      P.ys = P.src == 1 ? S.h_u(a + 1) : S.h_r1(a + 1);
     }
-    const int v0 = (int)(S.vptr(0) - S.dg0);
     unsigned mask = 0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int qq = q0 + q;
-      int xo = A0 + qq * dA, yo = xo + dB;
+      H xo = P.rows ? S.h_band(c + qq, a) : S.h_band(c - qq, lo + qq);
+      H yo = P.rows ? S.h_band(c + qq - 1, a + 1) : S.h_band(c - qq + 1, lo + qq);
       bool in = q < nb && qq <= lim;
-      if (P.withv && q == nb) { xo = v0 + a; yo = xo + 1; in = true; }
+      if (P.withv && q == nb) { xo = S.h_v(a); yo = S.h_v(a + 1); in = true; }
       P.xo[q] = xo; P.yo[q] = yo;
       mask |= in ? (1u << q) : 0u;
     }
@@ -648,13 +681,13 @@ struct Chaser {
   // The loads of a uniform op (zeros for lanes without one), issued together.
   __device__ __forceinline__ void load_plan(const Plan &P, double &f, double &g, double (&x)[4], double (&y)[4]) const {
     const bool u = P.kind == kUniform;
-    f = u ? Store::load(S.dg0 + P.xs) : 0.0;
-    g = u ? Store::load(S.dg0 + P.ys) : 0.0;
+    f = u ? S.ld_h(P.xs) : 0.0;
+    g = u ? S.ld_h(P.ys) : 0.0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const bool in = u && ((P.inmask >> q) & 1);
-      x[q] = in ? Store::load(S.dg0 + P.xo[q]) : 0.0;
-      y[q] = in ? Store::load(S.dg0 + P.yo[q]) : 0.0;
+      x[q] = in ? S.ld_h(P.xo[q]) : 0.0;
+      y[q] = in ? S.ld_h(P.yo[q]) : 0.0;
     }
   }
   // Every lane of the warp calls this (the fourth pair is skipped when no
@@ -675,11 +708,11 @@ struct Chaser {
       x[3] = nx; y[3] = ny;
     }
     if (ok) {
-      S.dg0[P.xs] = r;
-      S.dg0[P.ys] = 0.0;
+      S.st_h(P.xs, r);
+      S.st_h(P.ys, 0.0);
 #pragma unroll
       for (int q = 0; q < 4; q++) {
-        if ((P.inmask >> q) & 1) { S.dg0[P.xo[q]] = x[q]; S.dg0[P.yo[q]] = y[q]; }
+        if ((P.inmask >> q) & 1) { S.st_h(P.xo[q], x[q]); S.st_h(P.yo[q], y[q]); }
       }
       if (rx) rotate_extra(P.rows ? Ux : Vx, P.rows ? m : n, P.a, c, s);
     }
@@ -957,6 +990,7 @@ constexpr int kTotalsEvery = 8;
 
 template <bool FAST>
 __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
+  extern __shared__ double bslice[];     // this CTA's slice of the band (DsmStore)
   __shared__ int2 st[2][kMaxThreads];    // this CTA's chase status words
   __shared__ int2 pred[2][kMaxThreads];  // mirror of the previous CTA's status words
   __shared__ int4 inbox[2][kMaxCluster * kMaxWarps];  // every warp's counters (CTA-major): done, p1 done, min unfinished
@@ -977,12 +1011,23 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   if (cta == 0 && me == 0) run_spike<FAST>(Ar, &cnt[0]);
   cl.sync();  // spike done (global u)
 
-  using Ch = Chaser<GlobalStore, FAST>;
+  using Ch = Chaser<DsmStore, FAST>;
   Ch K;
   K.zero = &g_zero_sink[0];
-  K.S.dg0 = Ar.band.dg[0]; K.S.ld = N + 2;
-  K.S.r1 = Ar.band.r1; K.S.u = Ar.band.u; K.S.v = Ar.band.v;
+  static_assert(kMaxCluster == 16, "the slice layout takes index i to CTA i % 16, slot i / 16");
+  const int B = dsm_slice(N);
+  K.S.loc = bslice; K.S.base = (uint32_t)__cvta_generic_to_shared(bslice);
+  K.S.B = B;
   K.N = N; K.n = n; K.m = m; K.err = Ar.status;
+  // this CTA's slice of the nine arrays: indices cta * B .. cta * B + B - 1
+  const double *gsrc[9] = {Ar.band.dg[0], Ar.band.dg[1], Ar.band.dg[2], Ar.band.dg[3], Ar.band.dg[4],
+                           Ar.band.dg[5], Ar.band.r1, Ar.band.v, Ar.band.u};
+  const int glen[9] = {N + 2, N + 2, N + 2, N + 2, N + 2, N + 2, n + 2, n + 2, N + 2};
+  for (int arr = 0; arr < 9; arr++)
+    for (int q = me; q < B; q += S) {
+      const int idx = q * CS + cta;
+      bslice[arr * B + q] = idx < glen[arr] ? __ldcg(gsrc[arr] + idx) : 0.0;
+    }
   K.Ux = Ar.Ux; K.Vx = Ar.Vx; K.rx = Ar.rx;
 
   int2 *pred_next = cl.map_shared_rank(&pred[0][0], next);
@@ -1044,10 +1089,12 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
       fr = __reduce_min_sync(0xffffffffu, a2);
       if (fr == INT_MAX) fr = T;
       if (!fold_done && sp1 == p1) {
-        // fold: row 1 += u(1) v^T, the columns split over the cluster's threads
-        const double u1 = __ldcg(K.S.u + 1);
-        for (int j = cta * S + me + 1; j <= n; j += CS * S)
-          K.S.r1[j] = Arith<FAST>::px(1.0, u1, __ldcg(K.S.r1 + j), __ldcg(K.S.v + j));
+        // fold: row 1 += u(1) v^T, each CTA over the columns of its slice
+        const double u1 = DsmStore::load(K.S.uptr(1));
+        for (int q = me; q < B; q += S) {
+          const int j = q * CS + cta;
+          if (j >= 1 && j <= n) bslice[6 * B + q] = Arith<FAST>::px(1.0, u1, bslice[6 * B + q], bslice[7 * B + q]);
+        }
         cl.sync();
         fold_done = true;
         K.load_plan(P, f, g, x, y);  // row 1 has changed
@@ -1136,7 +1183,16 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   if (me == 0) {
     if (cta == 0) cnt[8] = step;
   }
-  cl.sync();  // every CTA has left the loop; the phase counters are complete
+  cl.sync();  // every CTA has left the loop; the slices and phase counters are final
+  {
+    double *gdst[9] = {Ar.band.dg[0], Ar.band.dg[1], Ar.band.dg[2], Ar.band.dg[3], Ar.band.dg[4],
+                       Ar.band.dg[5], Ar.band.r1, Ar.band.v, Ar.band.u};
+    for (int arr = 0; arr < 9; arr++)
+      for (int q = me; q < B; q += S) {
+        const int idx = q * CS + cta;
+        if (idx < glen[arr]) gdst[arr][idx] = bslice[arr * B + q];
+      }
+  }
   if (me == 0) {
     for (int q = 0; q < 9; q++)
       if (cnt[q]) atomicAdd(&Ar.counters[q], cnt[q]);
@@ -1154,6 +1210,14 @@ template <bool FAST>
 __global__ void __launch_bounds__(kMaxThreads) k_chase_cluster_batch(const ChaseArgs *__restrict__ items) {
   const ChaseArgs Ar = items[blockIdx.x / kMaxCluster];
   engine_cluster<FAST>(Ar);
+}
+
+// Static shared memory of the cluster engine (status words, mirrors, inbox)
+// with some margin, and its dynamic shared memory: the band slice of each CTA.
+constexpr size_t kClusterStaticSmem = 16384;
+size_t cluster_slice_bytes(int n, int m) {
+  const int N = (m > n) ? n + 1 : n;
+  return (size_t)9 * sizeof(double) * dsm_slice(N);
 }
 
 // Threads per CTA of the cluster engine: a slot for each of the ~n/3 chases in
@@ -1175,12 +1239,17 @@ cudaError_t launch_engine(const ChaseArgs &a, cudaStream_t s) {
   // by size: one CTA up to the measured crossover (n = 512: 17.2 vs 20.0 ms
   // per mixed column, 26.2 vs 28.0 FP64; n = 1024: 42.9 vs 40.9, 69.4 vs 56.9)
   const int cluster_from = FAST ? 896 : 640;
-  if (a.engine != 1 && (a.engine == 2 || n >= cluster_from)) {
+  // the cluster engine holds the band in its CTAs' shared memory (about
+  // 9 (n + 2) / 16 doubles each: n < 48000)
+  const bool fits = cluster_slice_bytes(n, m) + kClusterStaticSmem <= (size_t)optin;
+  if (fits && a.engine != 1 && (a.engine == 2 || n >= cluster_from)) {
     // cluster engine
     const int CS = kMaxCluster;
-    const size_t dyn = 0;
     const int threads = cluster_threads(n);
     cudaError_t e = cudaFuncSetAttribute(k_chase_cluster<FAST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = cluster_slice_bytes(n, m);
+    e = cudaFuncSetAttribute(k_chase_cluster<FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS);
@@ -1221,10 +1290,11 @@ cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int 
   if (count <= 0) return cudaSuccess;
   const int CS = kMaxCluster;
   const int threads = cluster_threads(max_n);
+  const size_t dyn = cluster_slice_bytes(max_n, max_n + 1);  // N <= max_n + 1
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS * count);
   cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1236,9 +1306,13 @@ cudaError_t launch_chase_cluster_batch(const ChaseArgs *d_items, int count, int 
   cudaError_t e;
   if (fast) {
     e = cudaFuncSetAttribute(k_chase_cluster_batch<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_chase_cluster_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_chase_cluster_batch<true>, d_items);
   } else {
     e = cudaFuncSetAttribute(k_chase_cluster_batch<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_chase_cluster_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_chase_cluster_batch<false>, d_items);
   }
   if (e != cudaSuccess) return e;
@@ -1268,6 +1342,13 @@ cudaError_t launch_chase_batch(const ChaseArgs *d_items, int count, int max_n, i
     k_chase_batch<false><<<count, threads, dyn, s>>>(d_items, dyn);
   }
   return cudaGetLastError();
+}
+
+bool chase_cluster_fits(int m, int n) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return cluster_slice_bytes(n, m) + kClusterStaticSmem <= (size_t)optin;
 }
 
 // Failure injection (BDU_INJECT_STEP_BUDGET) sets the step budget of a
