@@ -95,7 +95,7 @@ struct bdu_ctx {
   // orthogonality control (mixed form)
   void *cublas;           // created on first use
   double *ortho_ws;       // 3*m+1 doubles
-  double *rx_E, *rx_W;    // m*m doubles each, allocated on the first re-orthogonalization
+  double *rx_E, *rx_W;    // re-orthogonalization workspace (floats; reorth32_workspace), allocated on first use
   int64_t since_check;
   int64_t cols_since_reorth[2];  // rank-1 columns since the last unconditional step (Q, P)
   double ortho[2];        // last estimates for Q, P (-1 = none)
@@ -277,6 +277,7 @@ bdu_status check_device_status(bdu_ctx *h) {
   if (st & ERR_STEPS) return fail(h, BDU_ETIMEOUT, "the bulge-chase engine exceeded its step budget");
   if (st & ERR_APPLY) return fail(h, BDU_ETIMEOUT, "a bounded wait of the rotation apply ran out");
   if (st & ERR_ROTVEC) return fail(h, BDU_ETIMEOUT, "a bounded wait of the vector rotation ran out");
+  if (st & ERR_GEMM) return fail(h, BDU_ETIMEOUT, "a bounded wait of the re-orthogonalization GEMM ran out");
   if (st & ERR_RANGE) return fail(h, BDU_EINTERNAL, "a rotation record named a pair outside the vector");
   if (st) return fail(h, BDU_EINTERNAL, "device invariant check failed (status bits 0x%x)", st);
   return BDU_OK;
@@ -387,14 +388,11 @@ bdu_status probe_factor(bdu_ctx *h, int which, double *est) {
 // One Newton-Schulz step on Q (which = 0) or P, enqueued on stream s.
 bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s) {
   const int64_t k = which == 0 ? h->m : h->n;
-  if (!h->cublas) {
-    cublasHandle_t hb;
-    if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, BDU_ENOMEM, "cublasCreate failed");
-    h->cublas = hb;
-  }
   if (!h->rx_E) {
-    h->rx_E = (double *)dev_alloc(h, sizeof(float) * h->m * h->m);
-    h->rx_W = (double *)dev_alloc(h, sizeof(float) * h->m * h->m);
+    size_t ef = 0, wf = 0;
+    reorth32_workspace(h->m, (int)h->m, &ef, &wf);  // Q's order is the larger
+    h->rx_E = (double *)dev_alloc(h, sizeof(float) * ef);
+    h->rx_W = (double *)dev_alloc(h, sizeof(float) * wf);
     if (!h->rx_E || !h->rx_W) {
       dev_free(h, h->rx_E); dev_free(h, h->rx_W);
       h->rx_E = h->rx_W = nullptr;
@@ -402,7 +400,7 @@ bdu_status reorth_factor(bdu_ctx *h, int which, cudaStream_t s) {
     }
   }
   cudaError_t e = launch_reorth32((float *)(which == 0 ? h->Q : h->P), k, (int)k, (float *)h->rx_E, (float *)h->rx_W,
-                                  h->cublas, s);
+                                  h->status, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "re-orthogonalization");
   h->reorth[which]++;
   return BDU_OK;
@@ -2097,8 +2095,8 @@ bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
   std::swap(t->Pb, t->Pn);
   if (sizeof(T) == 4) {
     // FP32 factors: one Newton-Schulz step each, X <- X - X (X^T X - I) / 2
-    ce = launch_reorth32((float *)t->Qb, m, (int)k, t->E, t->W, h->cublas, s);
-    if (ce == cudaSuccess) ce = launch_reorth32((float *)t->Pb, n, (int)k, t->E, t->W, h->cublas, s);
+    ce = launch_reorth32((float *)t->Qb, m, (int)k, t->E, t->W, h->status, s);
+    if (ce == cudaSuccess) ce = launch_reorth32((float *)t->Pb, n, (int)k, t->E, t->W, h->status, s);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: re-orthogonalization");
   }
   // B+ = Bbar+(kept, kept): the superdiagonal entry across the removed index is zero
@@ -2207,8 +2205,10 @@ bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k
     t->wq = dev_alloc(h, es * N);
     t->wp = dev_alloc(h, es * N);
     t->xd = (double *)dev_alloc(h, sizeof(double) * (L * k > m + n ? L * k : m + n));  // b and c, or a factor
-    t->E = (float *)dev_alloc(h, sizeof(float) * k * k);
-    t->W = (float *)dev_alloc(h, sizeof(float) * L * k);
+    size_t ef = 0, wf = 0;
+    reorth32_workspace(L, (int)k, &ef, &wf);
+    t->E = (float *)dev_alloc(h, sizeof(float) * ef);
+    t->W = (float *)dev_alloc(h, sizeof(float) * wf);
     ok = ok && t->wq && t->wp && t->xd && t->E && t->W;
   } else {
     t->wq = t->u;

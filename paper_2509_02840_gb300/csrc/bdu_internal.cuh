@@ -16,6 +16,7 @@ enum : int {
   ERR_APPLY = 16,    // a bounded wait of the register-resident apply ran out
   ERR_ROTVEC = 32,   // a bounded wait of the vector rotation ran out
   ERR_RANGE = 64,    // a record named a pair outside the vector (skipped)
+  ERR_GEMM = 128,    // a bounded wait of the tensor-core GEMM ran out
 };
 
 // Failure injection for tests of the bounded waits (bdu_set_fault_injection):
@@ -189,10 +190,24 @@ cudaError_t launch_stage_batch(const ChaseArgs *d_items, const double *const *d_
 cudaError_t launch_ortho_probe(int precision, const void *X, int k, double *ws, int iters, cudaStream_t s);
 // One Newton-Schulz step with FP32 products and an FP64 diagonal of X^T X
 // (E, W: k*k floats of workspace).
-cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, void *cublas_handle, cudaStream_t s);
-cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, void *cublas_handle,
-                          cudaStream_t s);
+// One Newton-Schulz step X <- X - X E / 2, E = X^T X - I, on X (rows x k,
+// FP32, column-major, leading dimension rows); E and W: workspace of the
+// sizes reorth32_workspace gives (floats); status: the device error word
+// (ERR_GEMM).
+cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, int *status, cudaStream_t s);
+void reorth32_workspace(int64_t rows, int k, size_t *e_floats, size_t *w_floats);
 
+// D = alpha A B + beta D (beta 0 or 1) for FP32 operands on the tensor cores
+// (tcgen05, kind::tf32): passes = 3 is 3xTF32 (about FP32 accuracy), 1 plain
+// TF32.  K-contiguous operands: A(m, k) at A[m * a_sr + k], B(k, n) at
+// B[n * b_sr + k], row strides multiples of 4 and bases 16-byte aligned
+// (cudaErrorInvalidValue otherwise); D(m, n) at D[m * d_sm + n * d_sn].
+cudaError_t launch_gemm_tc(int passes, const float *A, int64_t a_sr, const float *B, int64_t b_sr, int M, int N,
+                           int K, float *D, int64_t d_sm, int64_t d_sn, float alpha, int beta, int *status,
+                           cudaStream_t s);
+// XT[i + r * ldt] = X[r + i * rows] (X rows x k); Y[r + i * ldy] = X[r + i * rows]
+cudaError_t launch_transpose32(const float *X, int64_t rows, int k, float *XT, int64_t ldt, cudaStream_t s);
+cudaError_t launch_pad_copy32(const float *X, int64_t rows, int k, float *Y, int64_t ldy, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, int64_t count,
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, int64_t count,

@@ -12,13 +12,12 @@
 // represented A by O(||E||) relative, and shrinks ||E|| to O(||E||^2).  E is
 // small (~1e-5), so it only needs to be right in absolute terms: its
 // off-diagonal entries are sums of products of nearly orthogonal columns whose
-// partial sums stay ~1/sqrt(k), and an FP32 GEMM (two plain cuBLAS SGEMMs, no
-// tensor-core rounding) gets them to ~1e-7; the diagonal, where the partial
-// sums grow to 1, is formed in FP64.  X E / 2 is a correction of relative size
-// ||E||, so its FP32 rounding is negligible.  (FP64 GEMMs would cost ~0.25 s at
-// k = 4096 on GB300's FP64 rate; these take a few ms.)
-#include <cublas_v2.h>
-
+// partial sums stay ~1/sqrt(k), and a 3xTF32 tensor-core GEMM (FP32 accuracy,
+// launch_gemm_tc) gets them to ~1e-7; the diagonal, where the partial sums
+// grow to 1, is formed in FP64.  X E / 2 is a correction of relative size
+// ||E||, so plain TF32 (relative error ~5e-4 of a value ~1e-5 |X|) stays far
+// below X's FP32 rounding.  (FP64 GEMMs would cost ~0.25 s at k = 4096 on
+// GB300's FP64 rate.)
 #include "bdu_internal.cuh"
 
 namespace bdu {
@@ -76,12 +75,9 @@ __global__ void k_start_vector(double *__restrict__ x, int k) {
   }
 }
 
-__global__ void k_minus_identity(double *__restrict__ E, int64_t ld, int k) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) E[(size_t)i * ld + i] -= 1.0;
-}
-
-// E(i, i) = sum_r X(r, i)^2 - 1 in FP64 (X rows x k, one warp per column)
-__global__ void k_diag_gram(const float *__restrict__ X, int64_t rows, int k, float *__restrict__ E) {
+// E(i, i) = sum_r X(r, i)^2 - 1 in FP64 (X rows x k, E with leading
+// dimension lde; one warp per column)
+__global__ void k_diag_gram(const float *__restrict__ X, int64_t rows, int k, float *__restrict__ E, int64_t lde) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= k) return;
   const float *col = X + (size_t)warp * rows;
@@ -91,28 +87,7 @@ __global__ void k_diag_gram(const float *__restrict__ X, int64_t rows, int k, fl
     s = fma(v, v, s);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) E[(size_t)warp * k + warp] = (float)(s - 1.0);
-}
-
-// X = X - W / 2 (FP32 entries, the difference formed in FP64 and rounded once)
-__global__ void k_finish_reorth32(const float *__restrict__ W, float *__restrict__ X, int64_t count) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
-       q += (int64_t)gridDim.x * blockDim.x)
-    X[q] = (float)((double)X[q] - 0.5 * (double)W[q]);
-}
-
-// X = (float)(Xd - W / 2)
-__global__ void k_finish_reorth(const double *__restrict__ Xd, const double *__restrict__ W,
-                                float *__restrict__ X, int64_t count) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
-       q += (int64_t)gridDim.x * blockDim.x)
-    X[q] = (float)(Xd[q] - 0.5 * W[q]);
-}
-
-__global__ void k_widen(const float *__restrict__ s, double *__restrict__ d, int64_t count) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
-       q += (int64_t)gridDim.x * blockDim.x)
-    d[q] = (double)s[q];
+  if (lane == 0) E[(size_t)warp * lde + warp] = (float)(s - 1.0);
 }
 
 }  // namespace
@@ -139,40 +114,30 @@ cudaError_t launch_ortho_probe(int precision, const void *X, int k, double *ws, 
   return probe<float>((const float *)X, k, ws, iters, s);
 }
 
-// One Newton-Schulz step on X (k x k, FP32) using three k*k FP64 buffers.
-cudaError_t launch_reorth(float *X, int k, double *Xd, double *E, double *W, void *cublas_handle,
-                          cudaStream_t s) {
-  cublasHandle_t hb = (cublasHandle_t)cublas_handle;
-  if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-  const int64_t cnt = (int64_t)k * k;
-  k_widen<<<1216, 256, 0, s>>>(X, Xd, cnt);
-  const double one = 1.0, zero = 0.0;
-  if (cublasDgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, k, k, &one, Xd, k, Xd, k, &zero, E, k) != CUBLAS_STATUS_SUCCESS)
-    return cudaErrorUnknown;
-  k_minus_identity<<<(k + 255) / 256, 256, 0, s>>>(E, k, k);
-  if (cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, Xd, k, E, k, &zero, W, k) != CUBLAS_STATUS_SUCCESS)
-    return cudaErrorUnknown;
-  k_finish_reorth<<<1216, 256, 0, s>>>(Xd, W, X, cnt);
-  return cudaGetLastError();
-}
-
 // One Newton-Schulz step on X (rows x k, FP32, leading dimension rows; a
-// square factor or the thin factor of rank-k tracking), E: k*k and W: rows*k
-// floats of workspace.
-cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, void *cublas_handle,
-                            cudaStream_t s) {
-  cublasHandle_t hb = (cublasHandle_t)cublas_handle;
-  if (cublasSetStream(hb, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-  if (cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-  const float one = 1.0f, zero = 0.0f;
-  const int r = (int)rows;
-  // E = X^T X (FP32; its diagonal is replaced by the FP64 one minus 1)
-  if (cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, k, k, r, &one, X, r, X, r, &zero, E, k) != CUBLAS_STATUS_SUCCESS)
-    return cudaErrorUnknown;
-  k_diag_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(X, rows, k, E);
-  if (cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, r, k, k, &one, X, r, E, k, &zero, W, r) != CUBLAS_STATUS_SUCCESS)
-    return cudaErrorUnknown;
-  k_finish_reorth32<<<1216, 256, 0, s>>>(W, X, rows * k);
+// square factor or the thin factor of rank-k tracking), with the workspace
+// reorth32_workspace gives: E (k x k, leading dimension kp = k rounded up to
+// a multiple of 4) and W (a padded copy of X when rows is not a multiple of
+// 4, then X^T with leading dimension kp).
+cudaError_t launch_reorth32(float *X, int64_t rows, int k, float *E, float *W, int *status, cudaStream_t s) {
+  const int64_t kp = (k + 3) / 4 * 4, rp = (rows + 3) / 4 * 4;
+  // E = X^T X (3xTF32): X's columns, k-contiguous rows of the product
+  const float *A1 = X;
+  int64_t s1 = rows;
+  cudaError_t e = cudaSuccess;
+  if (rows % 4 != 0 || (uintptr_t)X % 16 != 0) {
+    e = launch_pad_copy32(X, rows, k, W, rp, s);
+    A1 = W;
+    s1 = rp;
+  }
+  if (e == cudaSuccess) e = launch_gemm_tc(3, A1, s1, A1, s1, k, k, (int)rows, E, 1, kp, 1.0f, 0, status, s);
+  if (e != cudaSuccess) return e;
+  // its diagonal in FP64, minus 1
+  k_diag_gram<<<(k * 32 + 255) / 256, 256, 0, s>>>(X, rows, k, E, kp);
+  // X <- X - X E / 2 (TF32), from X^T so that the contracted index is contiguous
+  e = launch_transpose32(X, rows, k, W, kp, s);
+  if (e == cudaSuccess) e = launch_gemm_tc(1, W, kp, E, kp, (int)rows, k, k, X, 1, rows, -0.5f, 1, status, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

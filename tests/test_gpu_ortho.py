@@ -107,3 +107,30 @@ def test_default_policy_keeps_the_tolerance_after_every_update(overlap):
         st = F.stats()
     assert worst <= 1e-5
     assert st["reorth_q"] >= 3 and st["reorth_p"] >= 3
+
+
+@pytest.mark.parametrize("m,n", [(300, 200), (1024, 1024)])
+def test_newton_schulz_step_matches_fp64(m, n):
+    """One re-orthogonalization step on the GPU (X^T X in 3xTF32 with the
+    diagonal in FP64, X E in TF32, both on the tensor cores) against the same
+    step in FP64 on the host, X - X (X^T X - I) / 2 (Sec. 4.2), from the same
+    FP32 factor: two handles take the same update, one re-orthogonalizes Q
+    after it, the other does not."""
+    Q, d, e, P = I.factorization(m, n, config=0, which=11)
+    g = np.random.default_rng(3)
+    Qp = Q + 3e-5 * g.standard_normal((m, m)) / np.sqrt(m)
+    B, C = I.dense_update(m, n, 1, config=0)
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_every=0, check_every=0) as F:
+        F.update(B, C)
+        X, _, _, _ = F.read()
+    with bdu.Factorization(Qp, d, e, P, precision=bdu.MIXED, reorth_tol=1e-9, check_every=1, reorth_every=0) as F:
+        F.update(B, C)
+        Qg, _, _, _ = F.read()
+        st = F.stats()
+    assert st["reorth_q"] == 1
+    E = X.T @ X - np.eye(m)
+    want = X - 0.5 * (X @ E)
+    # the result is rounded to FP32 (entries up to ~1: half an ulp is 6e-8)
+    # and E carries FP32-level error in absolute terms
+    assert np.max(np.abs(Qg - want)) <= 2e-7
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(m), 2) <= 2e-6
