@@ -1958,11 +1958,6 @@ inline cublasStatus_t bl_gemm(cublasHandle_t h, int m, int n, int k, const doubl
   const double one = 1.0, zero = 0.0;
   return cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
 }
-inline cublasStatus_t bl_gemm(cublasHandle_t h, int m, int n, int k, const float *A, int lda, const float *B, int ldb,
-                              float *C, int ldc) {
-  const float one = 1.0f, zero = 0.0f;
-  return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc);
-}
 
 // The middle matrix's factorization starts from Q = P = I and Bd = [B 0; 0 0]
 // (beta_k = 0 between B and the zero block).
@@ -2088,8 +2083,21 @@ bdu_status thin_step(bdu_thin_ctx *t, int64_t *dropped, double *err2) {
     if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: gathering the kept columns");
     const int64_t len = side == 0 ? m : n;
     T *Xb = (T *)(side == 0 ? t->Qb : t->Pb), *Xn = (T *)(side == 0 ? t->Qn : t->Pn);
-    if (bl_gemm(cb, (int)len, (int)k, (int)N, Xb, (int)len, K2, (int)N, Xn, (int)len) != CUBLAS_STATUS_SUCCESS)
-      return fail(h, BDU_ECUDA, "rank-k step: cuBLAS GEMM failed");
+    if constexpr (sizeof(T) == 4) {
+      // mixed form: 3xTF32 on the tensor cores from K-contiguous copies, X^T
+      // (leading dimension Np = N rounded up to a multiple of 4) in W and the
+      // kept columns in E
+      const int64_t Np = (N + 3) / 4 * 4;
+      ce = launch_transpose32((const float *)Xb, len, (int)N, t->W, Np, s);
+      if (ce == cudaSuccess) ce = launch_pad_copy32((const float *)K2, N, (int)k, t->E, Np, s);
+      if (ce == cudaSuccess)
+        ce = launch_gemm_tc(3, t->W, Np, t->E, Np, (int)len, (int)k, (int)N, (float *)Xn, 1, len, 1.0f, 0, h->status,
+                            s);
+      if (ce != cudaSuccess) return cuda_fail(h, ce, "rank-k step: the product with the kept columns");
+    } else {
+      if (bl_gemm(cb, (int)len, (int)k, (int)N, Xb, (int)len, K2, (int)N, Xn, (int)len) != CUBLAS_STATUS_SUCCESS)
+        return fail(h, BDU_ECUDA, "rank-k step: cuBLAS GEMM failed");
+    }
   }
   std::swap(t->Qb, t->Qn);
   std::swap(t->Pb, t->Pn);
@@ -2206,7 +2214,7 @@ bdu_status bdu_thin_create(bdu_thin_handle *out, int64_t m, int64_t n, int64_t k
     t->wp = dev_alloc(h, es * N);
     t->xd = (double *)dev_alloc(h, sizeof(double) * (L * k > m + n ? L * k : m + n));  // b and c, or a factor
     size_t ef = 0, wf = 0;
-    reorth32_workspace(L, (int)k, &ef, &wf);
+    reorth32_workspace(L, (int)(k + 1), &ef, &wf);  // also the products' operand copies (k + 1 columns)
     t->E = (float *)dev_alloc(h, sizeof(float) * ef);
     t->W = (float *)dev_alloc(h, sizeof(float) * wf);
     ok = ok && t->wq && t->wp && t->xd && t->E && t->W;
