@@ -78,9 +78,12 @@ def parse():
     ap.add_argument("--thin", type=int, default=0,
                     help="rank of the thin (rank-k tracking) benchmark instead of the headline")
     ap.add_argument("--thin-fp64", action="store_true", help="the FP64 form of rank-k tracking (default: mixed)")
+    ap.add_argument("--network", action="store_true",
+                    help="full factors on the network edge stream (rank-2 symmetric edge insertions), mixed form, "
+                         "at m = n = --size (16384 for this mode unless given)")
     a = ap.parse_args()
     global M, N
-    M = N = a.size
+    M = N = a.size if (not a.network or any(x.startswith("--size") for x in sys.argv[1:])) else 16384
     return a
 
 
@@ -586,10 +589,71 @@ def run_thin(args):
     print(json.dumps(line), flush=True)
 
 
+def run_network(args):
+    """Full factors on the network edge stream (Sec. 4.1: rank-2 symmetric
+    edge insertions between Chung-Lu nodes), mixed form: rank-2 updates per
+    second, device-timed with B, C resident, the last update's work included."""
+    import numpy as np
+    import torch
+
+    from paper_2509_02840_gb300 import bdu, inputs as I
+
+    n = M
+    K, W = args.steps, max(args.warmup, 1)
+    Q0, d0, e0, P0 = I.factorization(n, n, config=3)
+    ups = [I.network_update(n, h, config=3) for h in range(W + K)]
+    stream = torch.cuda.Stream()
+    dev = []
+    with torch.cuda.stream(stream):
+        for B, C in ups:
+            dev.append((torch.from_numpy(np.asfortranarray(B).reshape(-1, order="F")).cuda(),
+                        torch.from_numpy(np.asfortranarray(C).reshape(-1, order="F")).cuda()))
+    stream.synchronize()
+    with bdu.Factorization(Q0, d0, e0, P0, precision=bdu.MIXED, stream=stream.cuda_stream) as F:
+        del Q0, P0
+        for Bd, Cd in dev[:W]:
+            F.update_dev(Bd.data_ptr(), Cd.data_ptr(), 2)
+        F.sync()
+        st0 = F.stats()
+        F.set_timing(True)
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        with torch.cuda.stream(stream):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for Bd, Cd in dev[W:]:
+                F.update_dev(Bd.data_ptr(), Cd.data_ptr(), 2)
+            F.flush()
+            ev1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        st = F.stats()
+        q, p = F.check_orthogonality()
+    tu = max(st["timed_updates"], 1)
+    line = {"metric": f"rank-2 network updates/s at m=n={n} (mixed form)", "value": 1e3 * K / ms,
+            "unit": "updates/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
+            "higher_is_better": True, "dtype": "f32 (Q, P) + f64 (projection, rotations, Bd)", "data": "synthetic",
+            "config": {"workload": f"network edge stream (Chung-Lu, exponent 2.1), m=n={n}, rank-2 symmetric "
+                                   "edge insertions, full factors", "m": n, "n": n, "rank": 2, "form": "mixed",
+                       "l2": "not flushed: each update streams > 10 GB"},
+            "apply_variant": st["apply_variant"], "orthogonality": {"q": q, "p": p, "tolerance": 1e-5},
+            "kernel_ms_per_update": {k: st["ms_" + k] / tu for k in ("project", "chase", "apply_q", "apply_p")},
+            "chase_steps_per_update": (st["chase_steps"] - st0["chase_steps"]) / K,
+            "clocks": clk, "cpu_baseline": None,
+            "note": "no CPU baseline: the oracle does not finish an update at this size in minutes"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.thin:
         run_thin(args)
+        return
+    if args.network:
+        run_network(args)
         return
     if args.impl == "reference":
         run_reference(args)
