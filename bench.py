@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--thin", type=int, default=0,
                     help="rank of the thin (rank-k tracking) benchmark instead of the headline")
     ap.add_argument("--thin-fp64", action="store_true", help="the FP64 form of rank-k tracking (default: mixed)")
+    ap.add_argument("--nb", type=int, default=0,
+                    help="apply variant of the mixed form (0: the autotuner's choice; 64/96/128: the blocked "
+                         "tensor-core apply; for profiling runs)")
     ap.add_argument("--network", action="store_true",
                     help="full factors on the network edge stream (rank-2 symmetric edge insertions), mixed form, "
                          "at m = n = --size (16384 for this mode unless given)")
@@ -417,7 +420,7 @@ def run_gpu(args):
 
     # ---- mixed form (headline), overlapped -------------------------------
     Fm = bdu.Factorization(Q, d, e, P, precision=bdu.MIXED, stream=stream.cuda_stream, device=local,
-                           overlap=True)
+                           overlap=True, nb=args.nb)
     timed_block(Fm, dev_ups[:W])
     st0 = Fm.stats()
     Fm.set_timing(True)
