@@ -205,16 +205,19 @@ __host__ __device__ constexpr size_t form_smem_bytes() {
 
 template <int NB>
 __global__ void __launch_bounds__(kFormThreads) k_tc_form(const int32_t *__restrict__ Ca, const float2 *__restrict__ Cf,
-                                                          const int4 *__restrict__ desc, int T, int cap, int b,
-                                                          const int2 *__restrict__ ranges, float *__restrict__ blobs,
-                                                          const ConeTable cone, int *__restrict__ status) {
+                                                          const int4 *__restrict__ desc, int T, int cap, int b0,
+                                                          int max_tiles, const int2 *__restrict__ ranges,
+                                                          float *__restrict__ blobs, const ConeTable cone,
+                                                          int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2, S = NB + 4, G = kFormThreads / NB;
   extern __shared__ __align__(16) float Gs[];
   int *off = reinterpret_cast<int *>(Gs + NB * S);  // K + 1 offsets into rec
   FormRec *rec = reinterpret_cast<FormRec *>(reinterpret_cast<unsigned char *>(off) + 16 * ((4 * (K + 1) + 15) / 16));
   __shared__ int cnt_s[K], e0_s[K];
+  // block (band b0 + i, tile t) at i * max_tiles + t; its blob at the same index
+  const int b = b0 + (int)blockIdx.x / max_tiles;
   const int2 rg = ranges[b];
-  const int j = rg.x + (int)blockIdx.x;
+  const int j = rg.x + (int)blockIdx.x % max_tiles;
   if (j > rg.y) return;
   const int tid = threadIdx.x, r = tid % NB, g = tid / NB;
   const int o = band_offset(b, W);
@@ -359,6 +362,45 @@ __host__ __device__ constexpr size_t apply_smem_bytes() {
 constexpr int kRowWarps = 8;
 constexpr int kApplyThreads2 = (kRowWarps + 1) * 32;
 
+// Bands in flight.  One launch applies a chunk of bands: the block of band
+// b0 + i and panel p (index i * panels + p) runs beside the blocks of the
+// bands before it, a couple of tiles behind band b - 1's block of the same
+// panel.  Each row warp of a block publishes a progress word, a column bound
+// (offset by kBias, INT_MAX when the block is done) below which X's columns
+// of its rows are final for its band: the four warps that store finals
+// during the band (half 0) publish the minimum of what they have stored and
+// of band b - 1's words, so that the least of a block's eight words holds for
+// every earlier band too; the carry warps (half 1) store only at the end.  A
+// block reads a column of X only once band b - 1's eight words have passed
+// it.  It waits only on a block of a lower index, which starts no later than
+// itself.
+constexpr int kBias = 1 << 24;
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+// the least of band b - 1's eight progress words (INT_MAX without one)
+__device__ __forceinline__ int pred_bound(const int *pred) {
+  if (!pred) return INT_MAX;
+  int mn = INT_MAX;
+#pragma unroll
+  for (int w = 0; w < kRowWarps; w++) mn = min(mn, ld_acquire(pred + w));
+  return mn;
+}
+// waits (bounded) until band b - 1's columns below `need` (biased) are final
+__device__ __forceinline__ bool wait_pred(const int *pred, int need) {
+  if (!pred) return true;
+  for (int it = 0; it < async::kSpin; it++) {
+    if (pred_bound(pred) >= need) return true;
+    __nanosleep(100);
+  }
+  return false;
+}
+
 // 16 columns of this thread's row into A hi / A lo at column col
 __device__ __forceinline__ void st_split16(uint32_t tm, uint32_t lane_off, int col, const float (&v)[16]) {
   uint32_t h[16], l[16];
@@ -371,7 +413,8 @@ __device__ __forceinline__ void st_split16(uint32_t tm, uint32_t lane_off, int c
 template <int NB>
 __global__ void __launch_bounds__(kApplyThreads2, 1)
     k_tc_apply(float *__restrict__ X, int64_t ld, int nrow, int ncol, const unsigned char *__restrict__ blobs,
-               const int2 *__restrict__ ranges, int b, const ConeTable cone, int *__restrict__ status) {
+               const int2 *__restrict__ ranges, int b0, int panels, int max_tiles, int *__restrict__ progress,
+               const ConeTable cone, int *__restrict__ status) {
   constexpr int K = NB / 2, W = NB / 2, H = NB / 2;  // H: outputs per row warp
   // the W new columns are split between the two halves in multiples of 16
   // (the width of a tcgen05.st): half 0 takes kNw0, half 1 the rest
@@ -385,11 +428,22 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
   __shared__ uint32_t tmem_s;
   __shared__ volatile int dead;
   __shared__ float2 xchg[2][kRows];  // per half and row: (squared output norm, squared input norm)
+  const int bi = (int)blockIdx.x / panels, panel = (int)blockIdx.x % panels, b = b0 + bi;
   const int2 rg = ranges[b];
-  if (rg.y < rg.x) return;  // no rotation in this band (the same for the whole block)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int *prog = progress + ((size_t)bi * panels + panel) * kRowWarps;  // this block's words
+  const int *pred = bi > 0 ? progress + ((size_t)(bi - 1) * panels + panel) * kRowWarps : nullptr;
+  if (rg.y < rg.x) {
+    // no rotation in this band (the same for the whole block): done once band b - 1 is
+    if (tid < kRowWarps) {
+      if (!wait_pred(pred, INT_MAX)) atomicOr(status, ERR_APPLY);
+      st_release(prog + tid, INT_MAX);
+    }
+    return;
+  }
+  blobs += (size_t)bi * max_tiles * (2 * blob_part_bytes<NB>());
   const int ntiles = rg.y - rg.x + 1;
-  const int row0 = (int)blockIdx.x * kRows;
+  const int row0 = panel * kRows;
   const bool bulk = (ld % 4) == 0 && row0 + kRows <= nrow;  // the same for the whole block
   const int o = band_offset(b, W);
   if (warp == 0) {
@@ -421,9 +475,15 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         for (uint32_t off = 0; off < kBlob; off += kCopyChunk)
           async::bulk_g2s(dst + off, src + off, kBlob - off < kCopyChunk ? kBlob - off : kCopyChunk, bar);
       };
-      // new columns of tile q (columns outside X are not copied)
+      // new columns of tile q (columns outside X are not copied), once band
+      // b - 1 is done with them
       auto issue_nv = [&](int q) {
         const int c0 = (rg.x + q) * W - o;
+        if (!wait_pred(pred, c0 + W + kBias)) {
+          atomicOr(status, ERR_APPLY);
+          dead = 1;
+        }
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");  // the copies read what band b - 1 stored
         const int lo = max(c0, 0), hi = min(c0 + W, ncol);
         async::mbar_arrive_tx(&bar_n, hi > lo ? (unsigned)(hi - lo) * kNvCol : 0u);
         for (int col = lo; col < hi; col++)
@@ -542,6 +602,18 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         if (rv && col >= 0 && col < ncol) *p = keep[c];
       }
     };
+    // this warp's progress word: its rows' columns below `bound` (unbiased)
+    // are final for this band and band b - 1 (the warp's stores ordered
+    // before the word by the warp barrier and lane 0's release)
+    auto publish = [&](int bound) {
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        st_release(prog + warp, min(bound + kBias, pred_bound(pred)));
+      }
+    };
+    // half 1 writes X only at the end, the columns from the last tile's carry on
+    if (half == 1 && lane == 0) st_release(prog + warp, rg.y * W - o + kBias);
     for (int q = 0; q < ntiles; q++) {
       if (dead) break;
       const int j = rg.x + q;
@@ -556,6 +628,20 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
       }
       clear_outputs();
       float sa = 0.f, sb = 0.f;
+      // columns of X this tile reads directly: the band's first carry (half 1)
+      // and, without bulk copies, the new columns
+      if ((q == 0 && half == 1) || !bulk) {
+        const int need = bulk ? j * W - o : j * W + W - o;
+        bool ok = true;
+        if (lane == 0) ok = wait_pred(pred, need + kBias);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        __syncwarp();  // the warp's reads of X follow lane 0's acquire
+        if (!ok) {
+          if (lane == 0) atomicOr(status, ERR_APPLY);
+          dead = 1;
+          break;
+        }
+      }
       if (half == 1) {
         // the carry: the previous tile's last K outputs, or X's columns
         // [j W - K - o, j W - o) for the band's first tile
@@ -618,6 +704,7 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
       if (lane == 0) async::mbar_arrive(&bar_a);
       // the previous tile's finals, while this tile's MMAs run
       if (q > 0 && half == 0) store_keep((j - 1) * W - K - o);
+      if (half == 0) publish(q > 0 ? (j - 1) * W - o : rg.x * W - K - o);
     }
     if (!dead) {
       if (!async::mbar_wait(&bar_m, (unsigned)((ntiles - 1) & 1))) {
@@ -629,6 +716,13 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
         store_keep(rg.y * W - K - o + half * H);  // the last tile's columns, all final
       }
     }
+    // done: once band b - 1 is (also after a failure, so that later bands end)
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      if (!wait_pred(pred, INT_MAX)) atomicOr(status, ERR_APPLY);
+      st_release(prog + warp, INT_MAX);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -636,9 +730,11 @@ __global__ void __launch_bounds__(kApplyThreads2, 1)
   if (warp == 0) tmem_dealloc(tm, kTmemCols);
 }
 
+constexpr int kChunkBands = 16;  // bands per launch pair (form, apply)
+
 template <int NB>
 cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side, int *status,
-                      int2 *ranges, float *blobs, int nbands, int max_tiles, cudaStream_t s) {
+                      int2 *ranges, float *blobs, int *progress, int nbands, int max_tiles, cudaStream_t s) {
   const int32_t *Ca = side == 0 ? st.La : st.Ra;
   const float2 *Cf = side == 0 ? st.Lf : st.Rf;
   const int4 *desc = side == 0 ? st.Lm : st.Rm;
@@ -650,12 +746,15 @@ cudaError_t run_bands(float *X, int64_t ld, int nrow, int ncol, const RotStream 
   if (e != cudaSuccess) return e;
   const int panels = (nrow + kRows - 1) / kRows;
   const ConeTable cone = cone_table<NB>();
-  for (int b = 0; b < nbands; b++) {
-    k_tc_form<NB><<<max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b, ranges, blobs, cone,
-                                                             status);
-    k_tc_apply<NB><<<panels, kApplyThreads2, apply_smem, s>>>(X, ld, nrow, ncol,
-                                                              reinterpret_cast<const unsigned char *>(blobs), ranges,
-                                                              b, cone, status);
+  for (int b0 = 0; b0 < nbands; b0 += kChunkBands) {
+    const int nb = min(kChunkBands, nbands - b0);
+    e = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nb * panels * kRowWarps, s);
+    if (e != cudaSuccess) return e;
+    k_tc_form<NB><<<nb * max_tiles, kFormThreads, form_smem, s>>>(Ca, Cf, desc, st.T, st.cap, b0, max_tiles, ranges,
+                                                                  blobs, cone, status);
+    k_tc_apply<NB><<<nb * panels, kApplyThreads2, apply_smem, s>>>(
+        X, ld, nrow, ncol, reinterpret_cast<const unsigned char *>(blobs), ranges, b0, panels, max_tiles, progress,
+        cone, status);
   }
   return cudaGetLastError();
 }
@@ -664,18 +763,24 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-// Workspace of the blocked apply: the band ranges, then one band's blobs.
+// Workspace of the blocked apply: the band ranges, the progress words of a
+// chunk of bands, then the chunk's blobs.
 // A band's tiles j run over floor((a + i + 1 + o) / W) for pair starts a in
 // [0, ncol - 2], i < K and o < W: at most (ncol + K + W) / W + 1 of them.
 static int tc_max_tiles(int ncol, int nb) { return (ncol + nb) / (nb / 2) + 2; }
 static size_t blob_bytes(int nb) {
   return nb == 64 ? 2 * blob_part_bytes<64>() : nb == 96 ? 2 * blob_part_bytes<96>() : 2 * blob_part_bytes<128>();
 }
+static size_t tc_progress_bytes(int nrow) {
+  return align256(sizeof(int) * (size_t)kChunkBands * ((nrow + kRows - 1) / kRows) * kRowWarps);
+}
 size_t tc_workspace_bytes(int ncol, int T, int nb) {
   const int K = nb / 2;
   const int nbands = (T + K - 1) / K;
   const int max_tiles = tc_max_tiles(ncol, nb);
-  return align256((size_t)(nbands + 1) * sizeof(int2)) + (size_t)max_tiles * blob_bytes(nb);
+  // (nrow <= ncol + 1 for every factor the apply serves: Q is m x m, P n x n)
+  return align256((size_t)(nbands + 1) * sizeof(int2)) + tc_progress_bytes(ncol + 1) +
+         (size_t)kChunkBands * max_tiles * blob_bytes(nb);
 }
 
 cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotStream &st, int side,
@@ -694,14 +799,16 @@ cudaError_t launch_apply_tc(float *X, int64_t ld, int nrow, int ncol, const RotS
   const int nbands = (st.T + K - 1) / K;
   const int max_tiles = tc_max_tiles(ncol, nb);
   int2 *ranges = reinterpret_cast<int2 *>(ws);
-  float *blobs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ws) +
-                                           align256((size_t)(nbands + 1) * sizeof(int2)));
+  int *progress = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(ws) +
+                                          align256((size_t)(nbands + 1) * sizeof(int2)));
+  float *blobs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(progress) + tc_progress_bytes(nrow));
+  if (nrow > ncol + 1) return cudaErrorNotSupported;  // the workspace is sized for nrow <= ncol + 1
   k_tc_band_ranges<<<(nbands + 127) / 128, 128, 0, s>>>(desc, st.T, K, W, nbands, max_tiles, ranges, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (nb == 64) return run_bands<64>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
-  if (nb == 96) return run_bands<96>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
-  return run_bands<128>(X, ld, nrow, ncol, st, side, status, ranges, blobs, nbands, max_tiles, s);
+  if (nb == 64) return run_bands<64>(X, ld, nrow, ncol, st, side, status, ranges, blobs, progress, nbands, max_tiles, s);
+  if (nb == 96) return run_bands<96>(X, ld, nrow, ncol, st, side, status, ranges, blobs, progress, nbands, max_tiles, s);
+  return run_bands<128>(X, ld, nrow, ncol, st, side, status, ranges, blobs, progress, nbands, max_tiles, s);
 }
 
 }  // namespace bdu
