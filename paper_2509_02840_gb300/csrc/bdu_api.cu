@@ -321,9 +321,11 @@ bdu_status reorth_after_column(bdu_ctx *h, cudaStream_t s) {
     // times as fast as rotation-by-rotation FP32 application (the tensor
     // cores' accumulation truncates toward zero); the step removes exactly
     // that symmetric part of the error, so it follows every column there.
-    const int every = h->opt.reorth_every > 0            ? h->opt.reorth_every
-                      : is_tc_variant(h->apply_var[which]) ? 1
-                                                          : auto_cadence(which == 0 ? h->m : h->n);
+    const int64_t dim = which == 0 ? h->m : h->n;
+    // (the blocked apply: the variant chosen, or the library's rule for the order)
+    const bool blocked = is_tc_variant(h->apply_var[which]) ||
+                         (h->apply_var[which] == 0 && dim >= kBlockedFrom && h->st.tc_ws);
+    const int every = h->opt.reorth_every > 0 ? h->opt.reorth_every : blocked ? 1 : auto_cadence(dim);
     if (++h->cols_since_reorth[which] < every && h->reorth[which] > 0) continue;
     h->cols_since_reorth[which] = 0;
     const bdu_status st = reorth_factor(h, which, s);
@@ -567,23 +569,29 @@ void save() {
 // yet applied, or applied: only a scratch copy of the factor is touched.
 bdu_status tune_side(bdu_ctx *h, int side, int sm_reserve) {
   const int m = (int)h->m, n = (int)h->n, dim = side == 0 ? m : n;
+  const bool mixed = h->opt.precision == BDU_MIXED;
+  if (mixed && dim >= kBlockedFrom && h->st.tc_ws) {
+    h->apply_var[side] = 128;  // the fixed rule, not a timing (see kBlockedFrom)
+    return BDU_OK;
+  }
   const std::string k = tune::key(h, dim, sm_reserve);
   {
     std::lock_guard<std::mutex> lk(tune::mu);
     tune::load();
     auto it = tune::table.find(k);
-    if (it != tune::table.end()) {
+    if (it != tune::table.end() && !(mixed && is_tc_variant(it->second))) {
       h->apply_var[side] = it->second;
       return BDU_OK;
     }
   }
+  // candidates that round alike (FP64: slab heights; mixed: the FP32 register
+  // layouts and the FP32 slab), so that the choice changes no result
   std::vector<int> cand;
-  if (h->opt.precision == BDU_FP64) {
+  if (!mixed) {
     for (int R : {2, 4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64}) cand.push_back(R);
   } else {
     for (int v = 1; v <= 4; v++) cand.push_back(v);
     cand.push_back(kSlabVariant);
-    for (int v : {64, 96, 128}) cand.push_back(v);
   }
   const size_t bytes = esize(h) * (size_t)dim * dim;
   void *scratch = dev_alloc(h, bytes);
@@ -1200,8 +1208,9 @@ bdu_status bdu_create(bdu_handle *out, int64_t m, int64_t n, const double *Q, co
   h->band = (double *)dev_alloc(h, sizeof(double) * band_doubles(m, n));
   const bool mixed = o.precision == BDU_MIXED;
   bool rec_ok = alloc_records(h, h->st, T, cap, m, mixed);
-  if (mixed) {
-    // the blocked tensor-core apply's workspace, for every block order and both factors
+  if (mixed && (m >= kBlockedFrom || is_tc_variant(o.nb))) {
+    // the blocked tensor-core apply's workspace, for every block order and both
+    // factors (factors below kBlockedFrom take it only when asked for: nb)
     size_t tcb = 0;
     for (int nb : {64, 96, 128}) tcb = std::max(tcb, tc_workspace_bytes((int)m, T, nb));
     h->st.tc_ws = dev_alloc(h, tcb);
@@ -1434,6 +1443,7 @@ static bdu_status update_batch_held(bdu_handle *hs, int count, const double *con
     std::vector<ChaseArgs> chase_s, chase_l;
     std::vector<const double *> ucol_s, ucol_l, vcol_s, vcol_l;
     std::vector<ApplyItem> apply;
+    std::vector<std::pair<bdu_ctx *, int>> tc_items;  // (handle, side) applied by the blocked apply
     std::vector<int> first;
     int max_n = 0, max_n_l = 0, max_band = 0, slabs = 0;
     size_t smem = 0;
@@ -1465,6 +1475,11 @@ static bdu_status update_batch_held(bdu_handle *hs, int count, const double *con
         if ((int)band_doubles(m, n) > max_band) max_band = (int)band_doubles(m, n);
       }
       for (int side = 0; side < 2; side++) {
+        const int dim = side == 0 ? m : n;
+        if (precision == BDU_MIXED && dim >= kBlockedFrom && h->st.tc_ws) {
+          tc_items.push_back({h, side});  // the blocked apply, as a single update takes it
+          continue;
+        }
         ApplyItem it{};
         it.X = side == 0 ? h->Q : h->P;
         it.ld = side == 0 ? m : n;
@@ -1525,6 +1540,12 @@ static bdu_status update_batch_held(bdu_handle *hs, int count, const double *con
       h0->launches += 3;
     }
     if (ce == cudaSuccess) ce = launch_apply_batch(precision, d_apply, d_first, (int)apply.size(), slabs, smem, s);
+    for (size_t q = 0; q < tc_items.size() && ce == cudaSuccess; q++) {
+      bdu_ctx *h = tc_items[q].first;
+      const int side = tc_items[q].second, dim = side == 0 ? (int)h->m : (int)h->n;
+      ce = launch_apply_tc((float *)(side == 0 ? h->Q : h->P), dim, dim, dim, h->st, side,
+                           side == 0 && h->m > h->n, h->status, false, 128, h->st.tc_ws, h->st.tc_ws_bytes, s);
+    }
     if (ce != cudaSuccess) return cuda_fail(h0, ce, "batched update round");
     h0->launches += 3;
     for (int i = 0; i < count; i++)

@@ -138,6 +138,12 @@ cudaError_t launch_project(int precision, const void *X, int64_t ld, int nrow, i
 // of that order (st.tc_ws must be set); variant 0 uses it (order 128) when no
 // register layout covers the shape.
 constexpr int kSlabVariant = 5;
+// Mixed form: factors of order >= kBlockedFrom take the blocked tensor-core
+// apply with blocks of order 128 whenever the variant is left to the library
+// (single updates before and after tuning, batches alike), smaller ones a
+// tuned FP32 variant; the two round differently, and a fixed rule keeps every
+// path of one shape bit-identical.
+constexpr int kBlockedFrom = 1024;
 inline bool is_tc_variant(int v) { return v == 64 || v == 96 || v == 128; }
 cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s,

@@ -252,6 +252,7 @@ cudaError_t launch_apply(int precision, void *X, int64_t ld, int nrow, int ncol,
                          const RotStream &st, int side, bool with_spike, cudaStream_t s, int *status,
                          int sm_reserve, bool desc_ready, int variant, const int *gate) {
   if (precision == BDU_MIXED && (st.Lf == nullptr || st.Rf == nullptr)) return cudaErrorInvalidValue;
+  if (precision == BDU_MIXED && variant == 0 && ncol >= kBlockedFrom && st.tc_ws) variant = 128;
   if (precision == BDU_MIXED && is_tc_variant(variant))
     return launch_apply_tc((float *)X, ld, nrow, ncol, st, side, with_spike, status, desc_ready, variant, st.tc_ws,
                            st.tc_ws_bytes, s);

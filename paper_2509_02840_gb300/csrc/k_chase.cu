@@ -209,19 +209,15 @@ struct LocalStore {
 // barrier between steps orders every CTA's stores before the next step's
 // loads.
 struct DsmStore {
-  double *loc;    // this CTA's slice (generic address)
-  uint32_t base;  // this CTA's slice (shared::cta address)
-  int B;          // indices per array and CTA
-  using H = uint32_t;  // a cell's shared::cluster address
+  double *loc;          // this CTA's slice (generic address)
+  const uint32_t *rb;   // shared::cluster address of every CTA's slice (rb[r] for rank r; in shared memory)
+  int B;                // indices per array and CTA
+  using H = uint32_t;   // a cell's shared::cluster address
   // (plans also form handles of cells they never touch -- pairs past the
-  // matrix edge, unused slots -- so both coordinates are clamped into range)
+  // matrix edge, unused slots: harmless, the rank is masked into range and
+  // such a handle is never dereferenced)
   __device__ __forceinline__ H h_at(int arr, int idx) const {
-    arr = arr < 0 ? 0 : (arr > 8 ? 8 : arr);
-    idx = idx < 0 ? 0 : (idx < kMaxCluster * B ? idx : kMaxCluster * B - 1);
-    const uint32_t a = base + (uint32_t)(arr * B + (idx >> 4)) * 8u;
-    uint32_t r;
-    asm("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(idx & (kMaxCluster - 1)));
-    return r;
+    return rb[idx & (kMaxCluster - 1)] + (uint32_t)(arr * B + (idx >> 4)) * 8u;
   }
   __device__ __forceinline__ H h_band(int diag, int i) const { return h_at(diag, i); }
   __device__ __forceinline__ H h_r1(int j) const { return h_at(6, j); }
@@ -621,6 +617,25 @@ struct Chaser {
     }
   }
 
+  // Geometry of an interior op by state, for the plan: bit 0 rows, bits 1-3
+  // w, bits 4-5 src, bit 6 withv, bit 7 a counts from ii (else p), bits 8-10
+  // a's offset + 1, bits 11-12 lo's distance below a, bits 13-14 the op's
+  // existence test (1: p + 1 <= N, 2: p + 2 <= n).  The same values as
+  // op_geometry (which the general path keeps).
+  static __device__ __forceinline__ unsigned geo_word(int st) {
+    switch (st) {  // (the compiler turns the constant table into selects)
+      case S_L0: return 1u | 3u << 1 | 1u << 4 | 0u << 8 | 0u << 11;
+      case S_R1: return 0u | 4u << 1 | 1u << 6 | 1u << 7 | 2u << 8 | 1u << 11;
+      case S_L1: return 1u | 4u << 1 | 1u << 7 | 3u << 8 | 1u << 11;
+      case S_A: return 1u | 4u << 1 | 1u << 8 | 0u << 11 | 1u << 13;
+      case S_B: return 0u | 5u << 1 | 3u << 8 | 2u << 11;
+      case S_C: return 0u | 4u << 1 | 2u << 8 | 1u << 11 | 2u << 13;
+      case S_CL: return 1u | 5u << 1 | 1u << 7 | 2u << 8 | 1u << 11;
+      case S_CR: return 0u | 5u << 1 | 1u << 7 | 4u << 8 | 2u << 11;
+      default: return 0u | 4u << 1 | 2u << 4 | 0u << 8 | 1u << 11;  // S_P2
+    }
+  }
+
   // ---- one instruction sequence for the interior ops of every kind
   //
   // An interior op (the exec_st cases) is the pair (f, g) that defines the
@@ -645,11 +660,22 @@ struct Chaser {
     P.nrot = 0;
     P.inmask = 0;
     if (k.done) return;
-    bool doit;
-    op_geometry(k, P.rows, P.a, P.lo, P.w, P.src, P.withv, doit);
-    if (!doit) return;
+    const unsigned gw = geo_word(k.st);
+    const unsigned chk = (gw >> 13) & 3;
+    if ((chk == 1 && k.p + 1 > N) || (chk == 2 && k.p + 2 > n)) return;  // the op does not exist
+    P.rows = gw & 1;
+    P.w = (gw >> 1) & 7;
+    P.src = (gw >> 4) & 3;
+    P.withv = (gw >> 6) & 1;
+    P.a = ((gw >> 7) & 1 ? k.ii : k.p) + (int)((gw >> 8) & 7) - 1;
+    P.lo = P.a - (int)((gw >> 11) & 3);
     const int a = P.a, lo = P.lo;
-    if (!(P.rows ? (a >= 2 && a + 1 <= N) : (lo >= 2 && a + 1 <= n))) { P.kind = kGeneric; return; }
+    if (!(P.rows ? (a >= 2 && a + 1 <= N) : (lo >= 2 && a + 1 <= n))) {
+      bool doit;
+      op_geometry(k, P.rows, P.a, P.lo, P.w, P.src, P.withv, doit);  // the general path's exact geometry
+      P.kind = kGeneric;
+      return;
+    }
     P.kind = kUniform;
     // band pair q: rows (a, a+1) at column lo+q, diagonals c+q and c+q-1; or
     // columns (a, a+1) at row lo+q, diagonals c-q and c-q+1 (geo_of(st).c)
@@ -1016,7 +1042,14 @@ __device__ __forceinline__ void engine_cluster(const ChaseArgs &Ar) {
   K.zero = &g_zero_sink[0];
   static_assert(kMaxCluster == 16, "the slice layout takes index i to CTA i % 16, slot i / 16");
   const int B = dsm_slice(N);
-  K.S.loc = bslice; K.S.base = (uint32_t)__cvta_generic_to_shared(bslice);
+  __shared__ uint32_t rbase[kMaxCluster];
+  if (me < CS) {
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(bslice)), "r"(me));
+    rbase[me] = r;
+  }
+  __syncthreads();
+  K.S.loc = bslice; K.S.rb = rbase;
   K.S.B = B;
   K.N = N; K.n = n; K.m = m; K.err = Ar.status;
   // this CTA's slice of the nine arrays: indices cta * B .. cta * B + B - 1

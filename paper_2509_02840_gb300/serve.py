@@ -65,8 +65,17 @@ def reserve_bytes(m, n, precision, max_rank=4):
     if precision == bdu.MIXED:
         b += 8 * m * m + 8 * (m + 1) + 32 * (T + 1)       # FP64 scratch, spike copies, chase descriptors
         b += 16 * m * m                                   # re-orthogonalization workspace
-        b += ((m + 64) // 64 + 2) * 2 * 128 * 128 * 4 + 8 * (T // 32 + 2) + 512  # blocked-apply workspace
+        if m >= BLOCKED_FROM:
+            # the blocked apply's workspace: a chunk of 16 bands of blocks (the
+            # largest over the block orders), band ranges, progress words
+            blobs = max(((m + nb) // (nb // 2) + 2) * part for nb, part in ((64, 23552), (96, 48128), (128, 81920)))
+            b += 16 * blobs + 8 * (T // 32 + 2) + 16 * ((m + 128) // 128) * 8 * 4 + 1024
     return b
+
+
+# factor orders from which the library's mixed form keeps the blocked
+# tensor-core apply's workspace (and applies with it)
+BLOCKED_FROM = 1024
 
 
 class Session:
@@ -135,6 +144,9 @@ class Server:
             if self.resident_bytes + s.bytes > self.budget:
                 return False
         s.admit()
+        if s.bytes > self.budget:
+            raise RuntimeError(f"session {s.sid} ({s.m} x {s.n}) holds {s.bytes} device bytes, more than the "
+                               f"budget of {self.budget}")
         self.resident_bytes += s.bytes
         self.peak_resident = max(self.peak_resident, self.resident_bytes)
         s.last_used = now

@@ -92,14 +92,28 @@ def test_overlapped_form_with_the_blocked_apply(nb):
     _check_invariants(Q, d, e, P, ups, a[-1], 3e-5)
 
 
-def test_autotuner_may_pick_the_blocked_apply_and_results_stay_within_tolerance():
-    # an order no other test uses, so that this handle's first update tunes
-    # (choices are cached per order in the process)
-    m = n = 1056
+def test_library_choice_of_the_apply():
+    """With nb = 0 the mixed form takes the blocked apply (order 128) for
+    factors of order >= 1024, by rule rather than by timing, so that every
+    path of a shape rounds alike; below that the autotuner picks among the
+    FP32 variants, which all round alike: the tuned result equals the one of
+    the chosen variant asked for explicitly, bit for bit."""
+    m = n = 1056  # (orders no other test uses: the tuner's choices are cached per order)
     Q, d, e, P = I.factorization(m, n, config=1, which=3)
     ups = [I.recommender_update(m, n, h, config=1) for h in range(3)]
     outs, st = _run(Q, d, e, P, ups, 0)
-    assert st["tunings"] >= 1
+    assert st["apply_variant"] == [128, 128] and st["tunings"] == 0
     Qg, dg, eg, Pg = outs[-1]
     for X in (Qg, Pg):
         assert np.linalg.norm(X.T @ X - np.eye(X.shape[0]), 2) <= 1e-5
+    m = n = 656
+    Q, d, e, P = I.factorization(m, n, config=1, which=4)
+    ups = [I.recommender_update(m, n, h, config=1) for h in range(3)]
+    outs, st = _run(Q, d, e, P, ups, 0)
+    assert st["tunings"] >= 1
+    v = st["apply_variant"]
+    assert all(1 <= x <= 5 for x in v), v
+    if v[0] == v[1]:
+        ref, _ = _run(Q, d, e, P, ups, v[0])
+        for a, b in zip(outs[-1], ref[-1]):
+            assert np.array_equal(a, b)
