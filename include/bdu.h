@@ -190,6 +190,59 @@ bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int6
 bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,
                             const int64_t *r, void *stream);
 
+/* ---- BHU: the bidiagonal Householder update (Sec. 3.3, Algorithm 1, Theorem 1)
+ *
+ * Algorithm 1 bidiagonalizes B + u v^T (B upper bidiagonal m x n, m >= n;
+ * u = Q^T b, v = P^T c, Eq. rk1) with Householder reflectors applied
+ * alternately from the left and the right (Sec. 2.1, Eq. house), keeping the
+ * transformed matrix in the factored form of Theorem 1 (Eq. comp): nothing
+ * dense of size m x n is formed.  Left reflector k zeroes column k below the
+ * diagonal (k = 1..n-1, and k = n when m > n); right reflector k+1 zeroes row
+ * k right of the superdiagonal (k = 1..n-2), so P's first column is kept.  The
+ * products of the reflectors are Q_k = I - Y SL Y^T and P_k = I - W SR W^T
+ * (Eq. QP with SL = 2 T^{-1}, SR = 2 R^{-1} of Eq. TR). */
+
+/* Sizes after `steps` iterations of Algorithm 1 (0 <= steps <= n): *kl left
+ * and *kr right reflectors, kl = min(steps, n if m > n else n-1),
+ * kr = min(steps, n-2), and the bytes of device workspace bdu_bhu_factor
+ * needs.  Any output pointer may be NULL.  Errors: BDU_EINVAL (m < n, n < 1,
+ * steps out of range). */
+bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64_t *kr,
+                         int64_t *workspace_bytes);
+
+/* Algorithm 1 on B + u v^T, FP64, every pointer in device memory,
+ * column-major:
+ *   in:  d (n), e (n-1; may be NULL when n == 1), u (m), v (n);
+ *   out: alpha (steps), beta (min(steps, n-1); may be NULL when n == 1): the
+ *        first `steps` diagonal and superdiagonal entries of the new
+ *        bidiagonal (a partial factorization when steps < n, Sec. 3.3);
+ *        Y (m x kl, leading dimension m): the normalized vectors y_1..y_kl
+ *        (Eq. YW; zeros above row k); W (n x kr, leading dimension n):
+ *        w_2..w_{kr+1} (zeros in rows 1..k); SL (kl x kl, leading dimension
+ *        kl) and SR (kr x kr, leading dimension kr), upper triangular;
+ *   workspace: bdu_bhu_sizes' bytes of device memory, 16-byte aligned, owned
+ *        by the caller (not kept past the call's work);
+ *   stream: cudaStream_t (NULL = the legacy default stream).
+ * The call returns once the work is queued; the outputs are the caller's.
+ * Results are deterministic (fixed summation orders); they equal the dense
+ * Householder process up to rounding, not bit for bit.
+ * Errors: BDU_EINVAL (sizes, NULL pointers, unaligned workspace), BDU_ECUDA. */
+bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, const double *e,
+                          const double *u, const double *v, double *alpha, double *beta, double *Y,
+                          double *W, double *SL, double *SR, void *workspace, void *stream);
+
+/* A+ = A + B C^T by BHU instead of the Givens update: for each of the r
+ * columns, u = Q^T b, v = P^T c with the current factors, Algorithm 1 to
+ * completion, Q <- Q - (Q Y) SL Y^T, P <- P - (P W) SR W^T (cuBLAS FP64
+ * products) and (d, e) <- (alpha, beta).  FP64 handles only; m < n through the
+ * transposed form as bdu_update.  Host (bdu_update_bhu) or device
+ * (bdu_update_bhu_dev) B, C as in bdu_update / bdu_update_dev.  The new
+ * bidiagonal equals the Givens update's up to the signs of its entries (both
+ * keep P's first column; Eq. bidiagplus), not bit for bit.
+ * Errors: as bdu_update; BDU_EINVAL for a mixed-form handle. */
+bdu_status bdu_update_bhu(bdu_handle h, const double *B, const double *C, int64_t r);
+bdu_status bdu_update_bhu_dev(bdu_handle h, const double *dB, const double *dC, int64_t r);
+
 /* Waits for all queued work and reports device-side failures
  * (BDU_ETIMEOUT, BDU_EINTERNAL, BDU_ECUDA). */
 bdu_status bdu_sync(bdu_handle h);

@@ -123,6 +123,15 @@ def load(build_if_missing: bool = True):
     L.bdu_thin_last_error.restype = ctypes.c_char_p
     L.bdu_thin_destroy.argtypes = [H]
     L.bdu_thin_destroy.restype = None
+    L.bdu_bhu_sizes.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i64p, i64p, i64p]
+    L.bdu_bhu_sizes.restype = ctypes.c_int
+    vp = ctypes.c_void_p
+    L.bdu_bhu_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + [vp] * 12
+    L.bdu_bhu_factor.restype = ctypes.c_int
+    L.bdu_update_bhu.argtypes = [H, dp, dp, ctypes.c_int64]
+    L.bdu_update_bhu.restype = ctypes.c_int
+    L.bdu_update_bhu_dev.argtypes = [H, vp, vp, ctypes.c_int64]
+    L.bdu_update_bhu_dev.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -187,6 +196,26 @@ def use_torch_allocator():
         torch.cuda.caching_allocator_delete(ptr)
 
     set_allocator(alloc, free)
+
+
+def bhu_sizes(m: int, n: int, steps: int):
+    """bdu_bhu_sizes: (kl, kr, workspace bytes) after `steps` iterations of Algorithm 1."""
+    L = load()
+    kl, kr, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    code = L.bdu_bhu_sizes(int(m), int(n), int(steps), ctypes.byref(kl), ctypes.byref(kr), ctypes.byref(wb))
+    if code != 0:
+        raise BduError(code, (L.bdu_last_error(None) or b"").decode())
+    return kl.value, kr.value, wb.value
+
+
+def bhu_factor(m: int, n: int, steps: int, d: int, e: int, u: int, v: int, alpha: int, beta: int, Y: int, W: int,
+               SL: int, SR: int, workspace: int, stream: int = 0):
+    """bdu_bhu_factor with device pointers (ints; 0 for NULL)."""
+    L = load()
+    ptrs = [ctypes.c_void_p(p or None) for p in (d, e, u, v, alpha, beta, Y, W, SL, SR, workspace, stream)]
+    code = L.bdu_bhu_factor(int(m), int(n), int(steps), *ptrs)
+    if code != 0:
+        raise BduError(code, (L.bdu_last_error(None) or b"").decode())
 
 
 def update_batch(factorizations, ptrB, ptrC, ranks, stream=None):
@@ -270,6 +299,19 @@ class Factorization:
     def update_dev(self, ptrB: int, ptrC: int, r: int):
         """B, C as device pointers (FP64, column-major, leading dimensions m and n)."""
         _check(self._L, self._h, self._L.bdu_update_dev(self._h, ctypes.c_void_p(ptrB), ctypes.c_void_p(ptrC), int(r)))
+
+    def update_bhu(self, B, C):
+        """The update by BHU (bdu_update_bhu; FP64 handles)."""
+        B = _f64(np.asarray(B, dtype=np.float64).reshape(self.m, -1))
+        C = _f64(np.asarray(C, dtype=np.float64).reshape(self.n, -1))
+        if B.shape[1] != C.shape[1]:
+            raise ValueError("B and C need the same number of columns")
+        _check(self._L, self._h, self._L.bdu_update_bhu(self._h, _dp(B), _dp(C), B.shape[1]))
+
+    def update_bhu_dev(self, ptrB: int, ptrC: int, r: int):
+        """bdu_update_bhu_dev: B, C as device pointers."""
+        _check(self._L, self._h, self._L.bdu_update_bhu_dev(self._h, ctypes.c_void_p(ptrB), ctypes.c_void_p(ptrC),
+                                                            int(r)))
 
     def sync(self):
         _check(self._L, self._h, self._L.bdu_sync(self._h))

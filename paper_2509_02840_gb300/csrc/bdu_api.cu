@@ -131,6 +131,11 @@ struct bdu_ctx {
   int64_t g_reorth[2];  // re-orthogonalizations one replay performs
   int64_t g_cols[2], g_cols_after[2];  // re-orthogonalization cadence counters before / after
   bool g_off;
+  // BHU (bdu_update_bhu): the compact representation and its workspace,
+  // allocated on first use
+  double *bhu_Y, *bhu_W, *bhu_SL, *bhu_SR, *bhu_ws, *bhu_G1, *bhu_G2, *bhu_vec;
+  unsigned *bhu_cnt;
+  int64_t bhu_updates;
   int64_t graph_replays;
   // apply variant per side (launch_apply), and whether the autotuner is still
   // to run after the next update
@@ -1337,6 +1342,158 @@ bdu_status bdu_update(bdu_handle h, const double *B, const double *C, int64_t r)
 bdu_status bdu_update_dev(bdu_handle h, const double *dB, const double *dC, int64_t r) {
   if (h && h->tr) return update_common(h, dC, dB, r, false);
   return update_common(h, dB, dC, r, false);
+}
+
+// ---------------------------------------------------------------- BHU
+// Sec. 3.3, Algorithm 1: the reflectors come from k_bhu.cu; the factors are
+// updated as Q <- Q Q_k = Q - (Q Y) SL Y^T and P <- P - (P W) SR W^T.
+
+bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64_t *kr, int64_t *workspace_bytes) {
+  if (m < n || n < 1 || steps < 0 || steps > n || m > (int64_t)1 << 30)
+    return fail(nullptr, BDU_EINVAL, "bdu_bhu_sizes: need m >= n >= 1 and 0 <= steps <= n");
+  const BhuSizes z = bhu_sizes(m, n, steps);
+  if (kl) *kl = z.kl;
+  if (kr) *kr = z.kr;
+  if (workspace_bytes) *workspace_bytes = (int64_t)(sizeof(double) * z.ws_doubles + sizeof(unsigned) * z.ws_counters + 16);
+  return BDU_OK;
+}
+
+bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, const double *e, const double *u,
+                          const double *v, double *alpha, double *beta, double *Y, double *W, double *SL,
+                          double *SR, void *workspace, void *stream) {
+  if (m < n || n < 1 || steps < 0 || steps > n || m > (int64_t)1 << 30)
+    return fail(nullptr, BDU_EINVAL, "bdu_bhu_factor: need m >= n >= 1 and 0 <= steps <= n");
+  if (steps == 0) return BDU_OK;
+  const BhuSizes z = bhu_sizes(m, n, steps);
+  if (!d || !u || !v || !alpha || !workspace || (n > 1 && !e) || (steps > 0 && n > 1 && !beta) ||
+      (z.kl > 0 && (!Y || !SL)) || (z.kr > 0 && (!W || !SR)))
+    return fail(nullptr, BDU_EINVAL, "bdu_bhu_factor: NULL argument");
+  if (((uintptr_t)workspace & 15) != 0) return fail(nullptr, BDU_EINVAL, "bdu_bhu_factor: workspace not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *ws = (double *)workspace;
+  unsigned *cnt = (unsigned *)(ws + z.ws_doubles);
+  cudaError_t ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * z.ws_counters, s);
+  if (ce == cudaSuccess)
+    ce = launch_bhu((int)m, (int)n, (int)steps, d, n > 1 ? e : d, u, v, alpha, n > 1 ? beta : alpha, Y, W, SL, SR,
+                    ws, cnt, s, nullptr);
+  if (ce != cudaSuccess) return fail(nullptr, BDU_ECUDA, "bdu_bhu_factor: %s", cudaGetErrorString(ce));
+  return BDU_OK;
+}
+
+static bdu_status bhu_ensure(bdu_ctx *h) {
+  if (h->bhu_ws) return BDU_OK;
+  const int64_t m = h->m, n = h->n;
+  const BhuSizes z = bhu_sizes(m, n, n);
+  const int64_t kl = z.kl > 0 ? z.kl : 1, kr = z.kr > 0 ? z.kr : 1;
+  h->bhu_Y = (double *)dev_alloc(h, sizeof(double) * m * kl);
+  h->bhu_W = (double *)dev_alloc(h, sizeof(double) * n * kr);
+  h->bhu_SL = (double *)dev_alloc(h, sizeof(double) * kl * kl);
+  h->bhu_SR = (double *)dev_alloc(h, sizeof(double) * kr * kr);
+  h->bhu_G1 = (double *)dev_alloc(h, sizeof(double) * m * kl);
+  h->bhu_G2 = (double *)dev_alloc(h, sizeof(double) * m * kl);
+  h->bhu_vec = (double *)dev_alloc(h, sizeof(double) * 4 * (n + 1));
+  h->bhu_cnt = (unsigned *)dev_alloc(h, sizeof(unsigned) * z.ws_counters);
+  h->bhu_ws = (double *)dev_alloc(h, sizeof(double) * z.ws_doubles);
+  if (!h->bhu_Y || !h->bhu_W || !h->bhu_SL || !h->bhu_SR || !h->bhu_G1 || !h->bhu_G2 || !h->bhu_vec ||
+      !h->bhu_cnt || !h->bhu_ws) {
+    for (double *p : {h->bhu_Y, h->bhu_W, h->bhu_SL, h->bhu_SR, h->bhu_G1, h->bhu_G2, h->bhu_vec, h->bhu_ws})
+      dev_free(h, p);
+    dev_free(h, h->bhu_cnt);
+    h->bhu_Y = h->bhu_W = h->bhu_SL = h->bhu_SR = h->bhu_G1 = h->bhu_G2 = h->bhu_vec = h->bhu_ws = nullptr;
+    h->bhu_cnt = nullptr;
+    return fail(h, BDU_ENOMEM, "device allocation for the BHU workspace failed");
+  }
+  cudaError_t ce = cudaMemsetAsync(h->bhu_cnt, 0, sizeof(unsigned) * z.ws_counters, h->stream);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "clearing the BHU counters");
+  if (!h->cublas) {
+    cublasHandle_t cb = nullptr;
+    if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) return fail(h, BDU_ENOMEM, "cublasCreate failed");
+    h->cublas = cb;
+  }
+  return BDU_OK;
+}
+
+// X <- X - (X Yr) S Yr^T for X rows x k reflectors (column-major, ld rows).
+static bool bhu_apply_factor(cublasHandle_t cb, double *X, int64_t rows, const double *Yr, int64_t k,
+                             const double *S, double *G1, double *G2) {
+  const double one = 1.0, zero = 0.0, minus = -1.0;
+  if (k <= 0) return true;
+  return cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, (int)k, (int)rows, &one, X, (int)rows, Yr, (int)rows,
+                     &zero, G1, (int)rows) == CUBLAS_STATUS_SUCCESS &&
+         cublasDtrmm(cb, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, (int)rows,
+                     (int)k, &one, S, (int)k, G1, (int)rows, G2, (int)rows) == CUBLAS_STATUS_SUCCESS &&
+         cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_T, (int)rows, (int)rows, (int)k, &minus, G2, (int)rows, Yr,
+                     (int)rows, &one, X, (int)rows) == CUBLAS_STATUS_SUCCESS;
+}
+
+static bdu_status run_update_bhu(bdu_ctx *h, const double *dB, const double *dC, int64_t r) {
+  bdu_status st = flush_apply(h);
+  if (st != BDU_OK) return st;
+  st = bhu_ensure(h);
+  if (st != BDU_OK) return st;
+  const int64_t m = h->m, n = h->n;
+  const BhuSizes z = bhu_sizes(m, n, n);
+  cudaStream_t s = h->stream;
+  cublasHandle_t cb = (cublasHandle_t)h->cublas;
+  if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS) return fail(h, BDU_EINTERNAL, "cublasSetStream failed");
+  double *d = h->bhu_vec, *e = d + (n + 1), *alpha = e + (n + 1), *beta = alpha + (n + 1);
+  int64_t launches = 0;
+  for (int64_t k = 0; k < r; k++) {
+    // u = Q^T b, v = P^T c with the current factors
+    cudaError_t ce = launch_project_nz(BDU_FP64, h->Q, m, (int)m, (int)m, dB + k * m, m, 1, h->U, m, h->nzB, s);
+    if (ce == cudaSuccess) ce = launch_project_nz(BDU_FP64, h->P, n, (int)n, (int)n, dC + k * n, n, 1, h->V, n, h->nzC, s);
+    if (ce == cudaSuccess) ce = launch_bhu_band_get(h->band, (int)m, (int)n, d, e, s);
+    if (ce == cudaSuccess)
+      ce = launch_bhu((int)m, (int)n, (int)n, d, e, h->U, h->V, alpha, beta, h->bhu_Y, h->bhu_W, h->bhu_SL,
+                      h->bhu_SR, h->bhu_ws, h->bhu_cnt, s, &launches);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "BHU reflectors");
+    if (!bhu_apply_factor(cb, (double *)h->Q, m, h->bhu_Y, z.kl, h->bhu_SL, h->bhu_G1, h->bhu_G2) ||
+        !bhu_apply_factor(cb, (double *)h->P, n, h->bhu_W, z.kr, h->bhu_SR, h->bhu_G1, h->bhu_G2))
+      return fail(h, BDU_ECUDA, "BHU: a cuBLAS product failed");
+    ce = launch_bhu_band_put(h->band, (int)m, (int)n, alpha, beta, s);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "BHU: storing the bidiagonal");
+    launches += 6;
+    h->updates++;
+    h->bhu_updates++;
+  }
+  h->launches += launches;
+  return BDU_OK;
+}
+
+static bdu_status update_bhu_common(bdu_handle h, const double *B, const double *C, int64_t r, bool host) {
+  if (!h) return fail(nullptr, BDU_EINVAL, "NULL handle");
+  Guard g(h);
+  if (!g.ok) return fail(h, BDU_EBUSY, "handle in use by another thread");
+  if (h->poisoned) return fail(h, BDU_EPOISONED, "handle poisoned by an earlier failure: %s", h->err);
+  if (h->opt.precision != BDU_FP64) return fail(h, BDU_EINVAL, "BHU updates need an FP64 handle");
+  if (r < 0) return fail(h, BDU_EINVAL, "negative rank %lld", (long long)r);
+  if (r == 0) return BDU_OK;
+  if (!B || !C) return fail(h, BDU_EINVAL, "NULL update pointer");
+  if (r > 4096) return fail(h, BDU_EINVAL, "rank %lld exceeds 4096", (long long)r);
+  if (host && (!all_finite(B, h->m * r) || !all_finite(C, h->n * r)))
+    return fail(h, BDU_EINVAL, "non-finite value in B or C");
+  cudaError_t ce = cudaSetDevice(h->device);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaSetDevice");
+  bdu_status st = ensure_rank_workspace(h, r);
+  if (st != BDU_OK) return st;
+  const double *dB = B, *dC = C;
+  if (host) {
+    ce = cudaMemcpyAsync(h->dB, B, sizeof(double) * h->m * r, cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->dC, C, sizeof(double) * h->n * r, cudaMemcpyHostToDevice, h->stream);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "copying B, C to the device");
+    dB = h->dB; dC = h->dC;
+  }
+  return run_update_bhu(h, dB, dC, r);
+}
+
+bdu_status bdu_update_bhu(bdu_handle h, const double *B, const double *C, int64_t r) {
+  if (h && h->tr) return update_bhu_common(h, C, B, r, true);
+  return update_bhu_common(h, B, C, r, true);
+}
+
+bdu_status bdu_update_bhu_dev(bdu_handle h, const double *dB, const double *dC, int64_t r) {
+  if (h && h->tr) return update_bhu_common(h, dC, dB, r, false);
+  return update_bhu_common(h, dB, dC, r, false);
 }
 
 static bdu_status update_batch_held(bdu_handle *hs, int count, const double *const *dB, const double *const *dC,

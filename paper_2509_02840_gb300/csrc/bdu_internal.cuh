@@ -219,4 +219,17 @@ cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, int64_t cou
 cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, int64_t count,
                                       cudaStream_t s);
 
+// BHU, the bidiagonal Householder update (k_bhu.cu; Sec. 3.3, Algorithm 1).
+// kl, kr: left and right reflectors after `steps` iterations; the workspace
+// of launch_bhu: ws_doubles doubles and ws_counters zeroed counters.
+struct BhuSizes {
+  int64_t kl, kr, ws_doubles, ws_counters;
+};
+BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps);
+cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e, const double *u, const double *v,
+                       double *alpha, double *beta, double *Y, double *W, double *SL, double *SR, double *ws,
+                       unsigned *cnt, cudaStream_t s, int64_t *launches);
+cudaError_t launch_bhu_band_get(double *band, int m, int n, double *d, double *e, cudaStream_t s);
+cudaError_t launch_bhu_band_put(double *band, int m, int n, const double *d, const double *e, cudaStream_t s);
+
 }  // namespace bdu
