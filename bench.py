@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--oracle-rows", type=int, default=256,
                     help="rows of Q and P the CPU oracle applies in its bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bhu", action="store_true", help="no BHU (Algorithm 1) measurement in the bench line")
     ap.add_argument("--size", type=int, default=4096,
                     help="m = n of the workload (4096 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--quick", action="store_true",
@@ -282,6 +283,59 @@ def serving(args):
     out["config"] = {"sessions": args.serving_sessions, "budget_fraction": 1 / 3,
                      "poisson_seconds": args.serving_seconds, "load": 0.8,
                      "saturation": "one request per session, all present at the start"}
+    return out
+
+
+def bhu_bench(steps=2):
+    """BHU (Sec. 3.3, Algorithm 1) beside the FP64 Givens form on the same
+    rank-1 updates, at m = n = 4096 (the recommender stream) and m = 8192 x
+    n = 2048 (dense b, c: a tall factorization, the case Sec. 3.3 names for
+    BHU).  Device time per update with CUDA events on the handle's stream (B, C
+    already on the device); one untimed update first.  The roofline counts the
+    paper's multiplications for the reflectors, (m + 3n) n^2 - 4/3 n^3 (Eq.
+    housecplx), two flops each, plus the three products a side that update Q
+    and P (4 m^2 k + m k^2 with k reflectors), against the FP64 peak."""
+    import numpy as np
+    import torch
+    from paper_2509_02840_gb300 import bdu, inputs as I
+    peak = 152 * 2 * 2 * 2.07e9
+    out = {}
+    for name, m, n in (("recommender_4096", M, N), ("tall_8192x2048", 8192, 2048)):
+        Q, d, e, P = I.factorization(m, n, config=1 if m == n else 2)
+        if m == n:
+            ups = [I.recommender_update(m, n, h + 500, config=1) for h in range(steps + 1)]
+        else:
+            ups = [I.dense_update(m, n, h + 500, config=2, r=1) for h in range(steps + 1)]
+        dev = [(torch.from_numpy(np.asfortranarray(B)).cuda(), torch.from_numpy(np.asfortranarray(C)).cuda())
+               for B, C in ups]
+        res = {}
+        for method in ("bhu", "givens"):
+            stream = torch.cuda.Stream()
+            with bdu.Factorization(Q, d, e, P, precision=bdu.FP64, stream=stream.cuda_stream) as F:
+                call = F.update_bhu_dev if method == "bhu" else F.update_dev
+                call(dev[0][0].data_ptr(), dev[0][1].data_ptr(), 1)
+                F.sync()
+                with torch.cuda.stream(stream):
+                    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for Bd, Cd in dev[1:]:
+                        call(Bd.data_ptr(), Cd.data_ptr(), 1)
+                    e1.record(stream)
+                F.sync()
+                res[method] = e0.elapsed_time(e1) / steps
+                if method == "bhu":
+                    s_bhu = F.singular_values(16)
+                else:
+                    s_giv = F.singular_values(16)
+        kl, kr = (n if m > n else n - 1), n - 2
+        flops = 2 * ((m + 3 * n) * n * n - 4.0 / 3.0 * n ** 3) + 4 * m * m * kl + m * kl * kl + 4 * n * n * kr + n * kr * kr
+        achieved = flops / (res["bhu"] * 1e-3) / 1e12
+        out[name] = {"m": m, "n": n, "bhu_ms_per_update": res["bhu"], "givens_fp64_ms_per_update": res["givens"],
+                     "bhu_updates_per_s": 1e3 / res["bhu"], "steps": steps,
+                     "top16_singular_values_max_rel_diff": float(np.abs(s_bhu - s_giv).max() / s_giv[0]),
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                                  "frac": achieved * 1e12 / peak, "flops_per_update": flops,
+                                  "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}}
     return out
 
 
@@ -543,6 +597,8 @@ def run_gpu(args):
     line["apply_roofline"] = apply_roofline(st, rot_per_update)
     if rank == 0 and world == 1 and args.serving_seconds > 0:
         line["serving"] = serving(args)
+    if rank == 0 and world == 1 and not args.no_bhu:
+        line["bhu"] = bhu_bench()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.oracle_rows, 1)
     if rank == 0:
