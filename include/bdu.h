@@ -223,10 +223,13 @@ bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64
  *   workspace: bdu_bhu_sizes' bytes of device memory, 16-byte aligned, owned
  *        by the caller (not kept past the call's work);
  *   stream: cudaStream_t (NULL = the legacy default stream).
- * The call returns once the work is queued; the outputs are the caller's.
- * Results are deterministic (fixed summation orders); they equal the dense
- * Householder process up to rounding, not bit for bit.
- * Errors: BDU_EINVAL (sizes, NULL pointers, unaligned workspace), BDU_ECUDA. */
+ * The call returns when the work is done (it synchronizes the stream); the
+ * outputs are the caller's.  Results are deterministic (fixed summation
+ * orders); they equal the dense Householder process up to rounding, not bit
+ * for bit.  One cooperative launch runs the loop; its grid barriers are
+ * bounded waits.
+ * Errors: BDU_EINVAL (sizes, NULL pointers, unaligned workspace), BDU_ECUDA,
+ * BDU_ETIMEOUT (a grid barrier ran out). */
 bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, const double *e,
                           const double *u, const double *v, double *alpha, double *beta, double *Y,
                           double *W, double *SL, double *SR, void *workspace, void *stream);

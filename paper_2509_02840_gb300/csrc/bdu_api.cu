@@ -283,6 +283,7 @@ bdu_status check_device_status(bdu_ctx *h) {
   if (st & ERR_APPLY) return fail(h, BDU_ETIMEOUT, "a bounded wait of the rotation apply ran out");
   if (st & ERR_ROTVEC) return fail(h, BDU_ETIMEOUT, "a bounded wait of the vector rotation ran out");
   if (st & ERR_GEMM) return fail(h, BDU_ETIMEOUT, "a bounded wait of the re-orthogonalization GEMM ran out");
+  if (st & ERR_BHU) return fail(h, BDU_ETIMEOUT, "a grid barrier of the BHU kernel ran out");
   if (st & ERR_RANGE) return fail(h, BDU_EINTERNAL, "a rotation record named a pair outside the vector");
   if (st) return fail(h, BDU_EINTERNAL, "device invariant check failed (status bits 0x%x)", st);
   return BDU_OK;
@@ -1354,7 +1355,8 @@ bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64
   const BhuSizes z = bhu_sizes(m, n, steps);
   if (kl) *kl = z.kl;
   if (kr) *kr = z.kr;
-  if (workspace_bytes) *workspace_bytes = (int64_t)(sizeof(double) * z.ws_doubles + sizeof(unsigned) * z.ws_counters + 16);
+  if (workspace_bytes)
+    *workspace_bytes = (int64_t)(sizeof(double) * z.ws_doubles + sizeof(unsigned) * z.ws_counters + sizeof(int) + 16);
   return BDU_OK;
 }
 
@@ -1372,11 +1374,16 @@ bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, 
   cudaStream_t s = (cudaStream_t)stream;
   double *ws = (double *)workspace;
   unsigned *cnt = (unsigned *)(ws + z.ws_doubles);
-  cudaError_t ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * z.ws_counters, s);
+  int *status = (int *)(cnt + z.ws_counters);
+  cudaError_t ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * z.ws_counters + sizeof(int), s);
   if (ce == cudaSuccess)
     ce = launch_bhu((int)m, (int)n, (int)steps, d, n > 1 ? e : d, u, v, alpha, n > 1 ? beta : alpha, Y, W, SL, SR,
-                    ws, cnt, s, nullptr);
+                    ws, cnt, status, s, nullptr);
+  int hst = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return fail(nullptr, BDU_ECUDA, "bdu_bhu_factor: %s", cudaGetErrorString(ce));
+  if (hst & ERR_BHU) return fail(nullptr, BDU_ETIMEOUT, "bdu_bhu_factor: a grid barrier ran out");
   return BDU_OK;
 }
 
@@ -1445,7 +1452,7 @@ static bdu_status run_update_bhu(bdu_ctx *h, const double *dB, const double *dC,
     if (ce == cudaSuccess) ce = launch_bhu_band_get(h->band, (int)m, (int)n, d, e, s);
     if (ce == cudaSuccess)
       ce = launch_bhu((int)m, (int)n, (int)n, d, e, h->U, h->V, alpha, beta, h->bhu_Y, h->bhu_W, h->bhu_SL,
-                      h->bhu_SR, h->bhu_ws, h->bhu_cnt, s, &launches);
+                      h->bhu_SR, h->bhu_ws, h->bhu_cnt, h->status, s, &launches);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "BHU reflectors");
     if (!bhu_apply_factor(cb, (double *)h->Q, m, h->bhu_Y, z.kl, h->bhu_SL, h->bhu_G1, h->bhu_G2) ||
         !bhu_apply_factor(cb, (double *)h->P, n, h->bhu_W, z.kr, h->bhu_SR, h->bhu_G1, h->bhu_G2))

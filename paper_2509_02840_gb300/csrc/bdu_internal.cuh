@@ -17,6 +17,7 @@ enum : int {
   ERR_ROTVEC = 32,   // a bounded wait of the vector rotation ran out
   ERR_RANGE = 64,    // a record named a pair outside the vector (skipped)
   ERR_GEMM = 128,    // a bounded wait of the tensor-core GEMM ran out
+  ERR_BHU = 256,     // a grid barrier of the BHU kernel ran out
 };
 
 // Failure injection for tests of the bounded waits (bdu_set_fault_injection):
@@ -226,9 +227,10 @@ struct BhuSizes {
   int64_t kl, kr, ws_doubles, ws_counters;
 };
 BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps);
+// status: the device status word (ERR_BHU when a grid barrier runs out).
 cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e, const double *u, const double *v,
                        double *alpha, double *beta, double *Y, double *W, double *SL, double *SR, double *ws,
-                       unsigned *cnt, cudaStream_t s, int64_t *launches);
+                       unsigned *cnt, int *status, cudaStream_t s, int64_t *launches);
 cudaError_t launch_bhu_band_get(double *band, int m, int n, double *d, double *e, cudaStream_t s);
 cudaError_t launch_bhu_band_put(double *band, int m, int n, const double *d, const double *e, cudaStream_t s);
 

@@ -29,13 +29,22 @@
 // m > n, and the last diagonal and superdiagonal entries read off without a
 // reflector when m = n.
 //
-// Kernels: column products (one warp per column, lanes over rows in order,
-// a fixed shuffle tree), row products (tiles of 256 rows x 64 columns, partial
-// sums per column chunk, added in chunk order by the last block of each row
-// tile to finish), the reflector (one block) and small vector kernels.  Every
-// result is deterministic: no atomics on values, fixed summation orders.
-// Entries the structure makes zero (above y_j, in W's rows 1..j, below the
-// diagonal of S, R') are skipped, never read.
+// One cooperative launch runs the whole loop; the blocks meet at a grid
+// barrier (bounded waits) between the phases of a step, 16 at most per step.
+// Column products: one warp per column, lanes over rows in order, a fixed
+// shuffle tree.  Row products: tiles of 512 rows x 64 columns, partial sums per
+// column chunk, added in chunk order by the last block of each row group to
+// finish, which also sums the group's share of the dot product or norm the next
+// phase needs.  The new column of S (R') and the next product with it are one
+// pass over the triangle with two right-hand sides:
+//
+//   Q_j e_j = e_j - Y_j S_j Y_j^T e_j,  S_j Y_j^T e_j = (S yr + eta S(:, j), 2 eta)
+//
+// with yr, eta the entries of row j of Y.  Every result is deterministic: no
+// atomics on values, fixed summation orders.  Entries the structure makes zero
+// (above y_j, in W's rows 1..j, below the diagonal of S, R') are skipped, and
+// everything written inside the launch is read through L2 (ld.global.cg), since
+// L1 is not coherent across SMs.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,9 +53,7 @@
 namespace bdu {
 namespace {
 
-constexpr int kRows = 256;  // rows per tile of a row product (one thread per row)
-constexpr int kCols = 64;   // columns per partial-sum chunk
-constexpr int kHouseThreads = 1024;
+constexpr int kCols = 64;  // columns per partial-sum chunk of a row product
 
 // Structure of a stored matrix M (column-major): which entries are zero.
 enum Shape : int {
@@ -64,28 +71,6 @@ __device__ __forceinline__ int col_hi(int shape, int c, int R) {
   return (shape == kUT && c + 1 < R) ? c + 1 : R;
 }
 
-// out[c] = scale * sum_{r in [lo(c), hi(c))} M(r, c) x[r], c < C.
-__global__ void k_gemv_t(const double *__restrict__ M, int64_t ld, int r0, int R, int C, int shape,
-                         const double *__restrict__ x, double scale, double *__restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
-    const int lo = col_lo(shape, c, r0), hi = col_hi(shape, c, R);
-    const double *col = M + (size_t)c * ld;
-    double s0 = 0.0, s1 = 0.0;
-    int r = lo + lane;
-    for (; r + 32 < hi; r += 64) {
-      s0 = fma(col[r], x[r], s0);
-      s1 = fma(col[r + 32], x[r + 32], s1);
-    }
-    if (r < hi) s0 = fma(col[r], x[r], s0);
-    double s = s0 + s1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[c] = scale * s;
-  }
-}
-
 // The row tiles [ra, rb) x column chunk [ca, cb) that hold only structural zeros.
 __device__ __forceinline__ bool tile_zero(int shape, int ra, int rb, int ca, int cb) {
   if (shape == kY) return rb <= ca;       // every r < c
@@ -94,58 +79,8 @@ __device__ __forceinline__ bool tile_zero(int shape, int ra, int rb, int ca, int
   return false;
 }
 
-// out[r] = base(r) + scale * sum_{c < C} M(r, c) t[c * ts] for r in [r0, R),
-// base(r) = (base ? base[r] : 0) + (r == unit ? 1 : 0).
-// grid (row tiles, column chunks); part: chunks x ldp partial sums; cnt: one
-// counter per row tile, zero on entry and left zero.
-__global__ void __launch_bounds__(kRows) k_gemv_n(const double *__restrict__ M, int64_t ld, int r0, int R, int C,
-                                                  int shape, const double *__restrict__ t, int64_t ts,
-                                                  const double *__restrict__ base, int unit, double scale,
-                                                  double *__restrict__ out, double *part, int64_t ldp,
-                                                  unsigned *cnt) {
-  const int tile = blockIdx.x, chunk = blockIdx.y, chunks = gridDim.y;
-  const int ra = r0 + tile * kRows, rb = min(ra + kRows, R);
-  const int ca = chunk * kCols, cb = min(ca + kCols, C);
-  const int r = ra + threadIdx.x;
-  __shared__ double tc[kCols];
-  __shared__ bool last;
-  if (!tile_zero(shape, ra, rb, ca, cb)) {
-    for (int c = ca + threadIdx.x; c < cb; c += blockDim.x) tc[c - ca] = t[(size_t)c * ts];
-    __syncthreads();
-    if (r < rb) {
-      const double *row = M + r;
-      double s0 = 0.0, s1 = 0.0;
-      int c = ca;
-      for (; c + 1 < cb; c += 2) {
-        s0 = fma(row[(size_t)c * ld], tc[c - ca], s0);
-        s1 = fma(row[(size_t)(c + 1) * ld], tc[c + 1 - ca], s1);
-      }
-      if (c < cb) s0 = fma(row[(size_t)c * ld], tc[c - ca], s0);
-      part[(size_t)chunk * ldp + r] = s0 + s1;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&cnt[tile], 1u);
-    last = prev == (unsigned)chunks - 1;
-    if (last) cnt[tile] = 0;
-  }
-  __syncthreads();
-  if (!last || r >= rb) return;
-  __threadfence();
-  double s = 0.0;
-  for (int k = 0; k < chunks; k++) {
-    const int ka = k * kCols, kb = min(ka + kCols, C);
-    if (tile_zero(shape, ra, rb, ka, kb)) continue;
-    s += __ldcg(part + (size_t)k * ldp + r);
-  }
-  double b = base ? base[r] : 0.0;
-  if (r == unit) b += 1.0;
-  out[r] = fma(scale, s, b);
-}
-
-// Deterministic block sum of v over the block (blockDim.x a multiple of 32).
+// Deterministic block sum of v (every thread of the block calls it; the
+// result is returned to every thread).
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -155,74 +90,392 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   __syncthreads();
   double s = 0.0;
   for (int k = 0; k < nw; k++) s += sh[k];
+  __syncthreads();
   return s;
 }
 
-// out[0] = sum_{r < len} a[r] b[r] (one block).
-__global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int len, double *out) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int r = threadIdx.x; r < len; r += blockDim.x) s = fma(a[r], b[r], s);
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) out[0] = s;
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
-// x = B z + u * dot: x[r] = d[r] z[r] + e[r] z[r+1] + u[r] dot (r < m; B is m x n).
-__global__ void k_bmv(const double *__restrict__ d, const double *__restrict__ e, int m, int n,
-                      const double *__restrict__ z, const double *__restrict__ u, const double *dot,
-                      double *__restrict__ x) {
-  const double w = dot[0];
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    if (r < n) s = d[r] * z[r];
-    if (r + 1 < n) s = fma(e[r], z[r + 1], s);
-    x[r] = fma(u[r], w, s);
-  }
-}
+constexpr int kT = 512;           // threads of a block = rows of a row group
+constexpr int kBarSpin = 1 << 22;  // bound on the wait of one grid barrier
 
-// y = B^T q + v * dot: y[c] = d[c] q[c] + e[c-1] q[c-1] + v[c] dot (c < n).
-__global__ void k_bmvt(const double *__restrict__ d, const double *__restrict__ e, int n,
-                       const double *__restrict__ q, const double *__restrict__ v, const double *dot,
-                       double *__restrict__ y) {
-  const double w = dot[0];
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    double s = d[c] * q[c];
-    if (c > 0) s = fma(e[c - 1], q[c - 1], s);
-    y[c] = fma(v[c], w, s);
-  }
-}
+struct BhuArgs {
+  int m, n, steps, nl, nr;
+  int64_t ldl, ldr, ldp;
+  const double *d, *e, *u, *v;
+  double *alpha, *beta, *Y, *W, *SL, *SR;
+  double *z, *x, *a, *q, *ra, *as, *g, *hv, *p1, *gw, *hw, *sv, *part, *part2, *tp;
+  unsigned *cnt, *bar;  // counters per row group (zero, left zero); the barrier's count and generation (zero)
+  int *status;
+};
 
-__global__ void k_unit(double *z, int n, int j) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) z[r] = r == j ? 1.0 : 0.0;
-}
-
-// The reflector of a[lo..R) (Sec. 2.1, Eq. house, normalized): with make,
-// y[lo..R) = (a + sign(a_lo) ||a|| e_lo) / ||.||, *alpha = -sign(a_lo) ||a||,
-// *sdiag = 2 (the new diagonal entry of S or R'); a = 0 gives y = 0,
-// alpha = 0.  Without make, *alpha = a[lo] (an entry read off without a
-// reflector).
-__global__ void __launch_bounds__(kHouseThreads) k_house(const double *__restrict__ a, int lo, int R, int make,
-                                                         double *__restrict__ y, double *alpha, double *sdiag) {
-  __shared__ double sh[32];
-  if (!make) {
-    if (threadIdx.x == 0) alpha[0] = a[lo];
-    return;
-  }
-  double s = 0.0;
-  for (int r = lo + threadIdx.x; r < R; r += blockDim.x) s = fma(a[r], a[r], s);
-  const double ss = block_sum(s, sh);
-  const double sigma = sqrt(ss);
-  const double a0 = a[lo];
-  const double sg = copysign(1.0, a0);
-  // ||a + sg sigma e_lo||^2 = 2 sigma (sigma + |a0|)
-  const double inv = sigma > 0.0 ? 1.0 / sqrt(2.0 * sigma * (sigma + fabs(a0))) : 0.0;
-  for (int r = lo + threadIdx.x; r < R; r += blockDim.x) {
-    const double v = r == lo ? fma(sg, sigma, a0) : a[r];
-    y[r] = v * inv;
-  }
+// Grid barrier (the blocks of a cooperative launch are co-resident): the last
+// block to arrive resets the count and releases the next generation.  A wait
+// that runs out sets ERR_BHU; every block stops at its next barrier once the
+// bit is set, so the kernel ends in bounded time.  Returns false to stop.
+__device__ bool grid_barrier(const BhuArgs &A, unsigned &gen) {
+  __shared__ int s_stop;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    alpha[0] = sigma > 0.0 ? -sg * sigma : 0.0;
-    sdiag[0] = 2.0;
+    int stop = 0;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&A.bar[0], 1u);
+    if (arrived == gridDim.x - 1) {
+      A.bar[0] = 0;
+      st_release_u32(&A.bar[1], gen + 1);
+    } else {
+      int it = 0;
+      while (ld_acquire_u32(&A.bar[1]) == gen) {
+        if (++it > kBarSpin) {
+          atomicOr(A.status, ERR_BHU);
+          stop = 1;
+          break;
+        }
+        if ((it & 255) == 0 && (*(volatile int *)A.status & ERR_BHU)) {
+          stop = 1;
+          break;
+        }
+      }
+    }
+    // (the acquire load above orders this block's later reads after every
+    // block's writes, which each fenced before arriving)
+    if (*(volatile int *)A.status & ERR_BHU) stop = 1;
+    s_stop = stop;
+  }
+  __syncthreads();
+  gen++;
+  return !s_stop;
+}
+
+__device__ __forceinline__ int groups_of(int rows) { return rows > 0 ? (rows + kT - 1) / kT : 0; }
+
+// Sum of the row groups' partials, in group order (every thread, every block:
+// the same value everywhere).
+__device__ __forceinline__ double tp_sum(const double *tp, int groups) {
+  double s = 0.0;
+  int k = 0;
+  for (; k + 7 < groups; k += 8) {  // eight loads in flight, added in order
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = __ldcg(tp + k + q);
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += v[q];
+  }
+  for (; k < groups; k++) s += __ldcg(tp + k);
+  return s;
+}
+
+// out[c] = sum_{r in [lo(c), hi(c))} M(r, c) x[r] for c < C: one warp per
+// column over the grid's warps, lanes over rows in order, a fixed shuffle tree.
+__device__ void colprod(const double *__restrict__ M, int64_t ld, int r0, int R, int C, int shape,
+                        const double *__restrict__ x, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < C; c += warps) {
+    const int lo = col_lo(shape, c, r0), hi = col_hi(shape, c, R);
+    const double *col = M + (size_t)c * ld;
+    // eight independent loads of each operand in flight per lane
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int r = lo + lane;
+    for (; r + 7 * 32 < hi; r += 8 * 32) {
+      double cv[8], xv[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        cv[k] = __ldcg(col + r + 32 * k);
+        xv[k] = __ldcg(x + r + 32 * k);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k++) acc[k & 3] = fma(cv[k], xv[k], acc[k & 3]);
+    }
+    for (; r < hi; r += 32) acc[0] = fma(__ldcg(col + r), __ldcg(x + r), acc[0]);
+    double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = s;
+  }
+}
+
+// Row products over rows [r0, R), columns [0, C): s0(r) = sum_c M(r, c) t0[c ts0]
+// (and s1(r) with t1 when NV = 2).  Tiles of kT rows x kCols columns go to the
+// blocks; each writes its partial sums, and the last block of a row group to
+// finish adds them in chunk order and calls epi(r, s0, s1), whose return
+// values it sums over the group into tp_out[group] (when tp_out is set).
+template <int NV, class Epi>
+__device__ void rowprod(const BhuArgs &A, const double *__restrict__ M, int64_t ld, int r0, int R, int C, int shape,
+                        const double *t0, int64_t ts0, const double *t1, int64_t ts1, Epi epi, double *tp_out) {
+  __shared__ double tc[2][kCols];
+  __shared__ int s_last;
+  __shared__ double red[32];
+  const int groups = groups_of(R - r0), chunks = C > 0 ? (C + kCols - 1) / kCols : 0;
+  for (int tile = blockIdx.x; tile < groups * chunks; tile += gridDim.x) {
+    const int gi = tile / chunks, ch = tile - gi * chunks;
+    const int ra = r0 + gi * kT, rb = min(ra + kT, R), ca = ch * kCols, cb = min(ca + kCols, C);
+    const int r = ra + threadIdx.x;
+    __syncthreads();
+    if (!tile_zero(shape, ra, rb, ca, cb)) {
+      for (int c = ca + threadIdx.x; c < cb; c += blockDim.x) {
+        tc[0][c - ca] = __ldcg(t0 + (size_t)c * ts0);
+        if (NV == 2) tc[1][c - ca] = __ldcg(t1 + (size_t)c * ts1);
+      }
+      __syncthreads();
+      if (r < rb) {
+        // eight independent loads in flight per thread, four accumulators
+        const double *row = M + r;
+        double sa[4] = {0.0, 0.0, 0.0, 0.0}, qa[4] = {0.0, 0.0, 0.0, 0.0};
+        int c = ca;
+        for (; c + 7 < cb; c += 8) {
+          double mv[8];
+#pragma unroll
+          for (int k = 0; k < 8; k++) mv[k] = __ldcg(row + (size_t)(c + k) * ld);
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            sa[k & 3] = fma(mv[k], tc[0][c + k - ca], sa[k & 3]);
+            if (NV == 2) qa[k & 3] = fma(mv[k], tc[1][c + k - ca], qa[k & 3]);
+          }
+        }
+        for (; c < cb; c++) {
+          const double m0 = __ldcg(row + (size_t)c * ld);
+          sa[0] = fma(m0, tc[0][c - ca], sa[0]);
+          if (NV == 2) qa[0] = fma(m0, tc[1][c - ca], qa[0]);
+        }
+        A.part[(size_t)ch * A.ldp + r] = (sa[0] + sa[1]) + (sa[2] + sa[3]);
+        if (NV == 2) A.part2[(size_t)ch * A.ldp + r] = (qa[0] + qa[1]) + (qa[2] + qa[3]);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned prev = atomicAdd(&A.cnt[gi], 1u);
+      s_last = prev == (unsigned)chunks - 1;
+      if (s_last) A.cnt[gi] = 0;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double contrib = 0.0;
+      if (r < rb) {
+        // the chunks that hold more than structural zeros form one range
+        // [k0, k1); eight partial loads in flight, added in chunk order
+        int k0 = 0, k1 = chunks;
+        while (k0 < k1 && tile_zero(shape, ra, rb, k0 * kCols, min(k0 * kCols + kCols, C))) k0++;
+        while (k1 > k0 && tile_zero(shape, ra, rb, (k1 - 1) * kCols, min((k1 - 1) * kCols + kCols, C))) k1--;
+        double a0 = 0.0, a1 = 0.0;
+        int k = k0;
+        for (; k + 7 < k1; k += 8) {
+          double v0[8], v1[8];
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            v0[q] = __ldcg(A.part + (size_t)(k + q) * A.ldp + r);
+            if (NV == 2) v1[q] = __ldcg(A.part2 + (size_t)(k + q) * A.ldp + r);
+          }
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            a0 += v0[q];
+            if (NV == 2) a1 += v1[q];
+          }
+        }
+        for (; k < k1; k++) {
+          a0 += __ldcg(A.part + (size_t)k * A.ldp + r);
+          if (NV == 2) a1 += __ldcg(A.part2 + (size_t)k * A.ldp + r);
+        }
+        contrib = epi(r, a0, a1);
+      }
+      if (tp_out) {
+        const double sum = block_sum(contrib, red);
+        if (threadIdx.x == 0) tp_out[gi] = sum;
+      }
+    }
+  }
+}
+
+// Group partials of sum w(r) over rows [r0, R) without a product (the first
+// column or row of a step, when no reflector of that side exists yet).
+template <class F>
+__device__ void group_partials(int r0, int R, F w, double *tp_out) {
+  __shared__ double red[32];
+  for (int gi = blockIdx.x; gi < groups_of(R - r0); gi += gridDim.x) {
+    const int r = r0 + gi * kT + threadIdx.x;
+    const double sum = block_sum(r < R ? w(r) : 0.0, red);
+    if (threadIdx.x == 0) tp_out[gi] = sum;
+  }
+}
+
+// The whole of Algorithm 1 in one cooperative launch: per step j the phases
+// below, each ended by a grid barrier.
+__global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
+  unsigned gen = 0;
+  const int m = A.m, n = A.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+  for (int j = 0; j < A.steps; j++) {
+    const int cR = min(j, A.nr), cL = min(j, A.nl);
+    // z = P_{j-1} e_j = e_j - W p1, p1 = R' W^T e_j (from the previous step); partials of v^T z
+    if (cR > 0) {
+      rowprod<1>(A, A.W, n, 0, n, cR, kW, A.p1, 1, nullptr, 0, [&](int r, double s, double) {
+        const double zr = (r == j ? 1.0 : 0.0) - s;
+        A.z[r] = zr;
+        return A.v[r] * zr;
+      }, A.tp);
+    } else {
+      for (int r = gtid; r < n; r += gthreads) A.z[r] = r == j ? 1.0 : 0.0;
+    }
+    if (!grid_barrier(A, gen)) return;
+    // x = B z + u (v^T z)
+    {
+      const double w = cR > 0 ? tp_sum(A.tp, groups_of(n)) : A.v[j];
+      for (int r = gtid; r < m; r += gthreads) {
+        double s = 0.0;
+        if (r < n) s = A.d[r] * __ldcg(A.z + r);
+        if (r + 1 < n) s = fma(A.e[r], __ldcg(A.z + r + 1), s);
+        A.x[r] = fma(A.u[r], w, s);
+      }
+    }
+    if (!grid_barrier(A, gen)) return;
+    // a = Q_{j-1}^T x = x - Y S^T Y^T x (rows j..m); partials of a^2 there
+    const double *acol = A.x;
+    if (cL > 0) {
+      colprod(A.Y, m, 0, m, cL, kY, A.x, A.g);
+      if (!grid_barrier(A, gen)) return;
+      colprod(A.SL, A.ldl, 0, cL, cL, kUT, A.g, A.hv);
+      if (!grid_barrier(A, gen)) return;
+      rowprod<1>(A, A.Y, m, j, m, cL, kY, A.hv, 1, nullptr, 0, [&](int r, double s, double) {
+        const double ar = __ldcg(A.x + r) - s;
+        A.a[r] = ar;
+        return ar * ar;
+      }, A.tp);
+      acol = A.a;
+    } else {
+      group_partials(j, m, [&](int r) { const double xr = __ldcg(A.x + r); return xr * xr; }, A.tp);
+    }
+    if (!grid_barrier(A, gen)) return;
+    // the left reflector of a(j..m): y_j, alpha_j, S(j, j) = 2 (Eq. house)
+    const bool lmake = j < A.nl;
+    double *yj = A.Y + (size_t)j * m;
+    {
+      const double a0 = __ldcg(acol + j);
+      if (lmake) {
+        const double sigma = sqrt(tp_sum(A.tp, groups_of(m - j)));
+        const double sg = copysign(1.0, a0);
+        const double inv = sigma > 0.0 ? 1.0 / sqrt(2.0 * sigma * (sigma + fabs(a0))) : 0.0;
+        for (int r = j + gtid; r < m; r += gthreads) {
+          const double y = (r == j ? fma(sg, sigma, a0) : __ldcg(acol + r)) * inv;
+          yj[r] = y;
+          if (r == 0) A.p1[0] = 2.0 * y;  // j = 0: S_0 Y_0^T e_0
+        }
+        if (gtid == 0) {
+          A.alpha[j] = sigma > 0.0 ? -sg * sigma : 0.0;
+          A.SL[j + (size_t)j * A.ldl] = 2.0;
+        }
+      } else if (gtid == 0) {
+        A.alpha[j] = a0;
+      }
+    }
+    if (!grid_barrier(A, gen)) return;
+    const bool right = j <= n - 2;
+    if (lmake && j > 0) {
+      // s = Y_{j-1}^T y_j; then S(:, j) = -2 S s and p1 = S_j Y_j^T e_j =
+      // (S yr + eta S(:, j), 2 eta), yr = Y(j, 0..j-1), eta = Y(j, j)
+      colprod(A.Y, m, 0, m, j, kY, yj, A.sv);
+      if (!grid_barrier(A, gen)) return;
+      const double eta = __ldcg(yj + j);
+      rowprod<2>(A, A.SL, A.ldl, 0, j, j, kUT, A.sv, 1, A.Y + j, m, [&](int r, double ss, double sy) {
+        const double col = -2.0 * ss;
+        A.SL[r + (size_t)j * A.ldl] = col;
+        A.p1[r] = fma(eta, col, sy);
+        return 0.0;
+      }, nullptr);
+      if (gtid == 0) A.p1[j] = 2.0 * eta;
+      if (!grid_barrier(A, gen)) return;
+    }
+    if (!right) continue;
+    // q = Q_j e_j = e_j - Y p1; partials of u^T q
+    const int cL1 = min(j + 1, A.nl);
+    rowprod<1>(A, A.Y, m, 0, m, cL1, kY, A.p1, 1, nullptr, 0, [&](int r, double s, double) {
+      const double qr = (r == j ? 1.0 : 0.0) - s;
+      A.q[r] = qr;
+      return A.u[r] * qr;
+    }, A.tp);
+    if (!grid_barrier(A, gen)) return;
+    // r = B^T q + v (u^T q)
+    {
+      const double w = tp_sum(A.tp, groups_of(m));
+      for (int c = gtid; c < n; c += gthreads) {
+        double s = A.d[c] * __ldcg(A.q + c);
+        if (c > 0) s = fma(A.e[c - 1], __ldcg(A.q + c - 1), s);
+        A.ra[c] = fma(A.v[c], w, s);
+      }
+    }
+    if (!grid_barrier(A, gen)) return;
+    // a* = P_{j-1}^T r = r - W R'^T W^T r (columns j+1..n); partials of a*^2 there
+    const double *arow = A.ra;
+    if (cR > 0) {
+      colprod(A.W, n, 0, n, cR, kW, A.ra, A.gw);
+      if (!grid_barrier(A, gen)) return;
+      colprod(A.SR, A.ldr, 0, cR, cR, kUT, A.gw, A.hw);
+      if (!grid_barrier(A, gen)) return;
+      rowprod<1>(A, A.W, n, j + 1, n, cR, kW, A.hw, 1, nullptr, 0, [&](int r, double s, double) {
+        const double ar = __ldcg(A.ra + r) - s;
+        A.as[r] = ar;
+        return ar * ar;
+      }, A.tp);
+      arow = A.as;
+    } else {
+      group_partials(j + 1, n, [&](int r) { const double xr = __ldcg(A.ra + r); return xr * xr; }, A.tp);
+    }
+    if (!grid_barrier(A, gen)) return;
+    // the right reflector of a*(j+1..n): w_{j+1}, beta_j, R'(j, j) = 2
+    const bool rmake = j < A.nr;
+    double *wj = A.W + (size_t)j * n;
+    {
+      const double a0 = __ldcg(arow + j + 1);
+      if (rmake) {
+        const double sigma = sqrt(tp_sum(A.tp, groups_of(n - j - 1)));
+        const double sg = copysign(1.0, a0);
+        const double inv = sigma > 0.0 ? 1.0 / sqrt(2.0 * sigma * (sigma + fabs(a0))) : 0.0;
+        for (int c = j + 1 + gtid; c < n; c += gthreads) {
+          const double w = (c == j + 1 ? fma(sg, sigma, a0) : __ldcg(arow + c)) * inv;
+          wj[c] = w;
+          if (j == 0 && c == 1) A.p1[0] = 2.0 * w;  // the next step's R'_0 W_0^T e_1
+        }
+        if (gtid == 0) {
+          A.beta[j] = sigma > 0.0 ? -sg * sigma : 0.0;
+          A.SR[j + (size_t)j * A.ldr] = 2.0;
+        }
+      } else if (gtid == 0) {
+        A.beta[j] = a0;
+      }
+    }
+    if (!grid_barrier(A, gen)) return;
+    if (j + 1 >= A.steps) continue;
+    // the next step's p1 = R'_j W_j^T e_{j+1}
+    if (rmake && j > 0) {
+      colprod(A.W, n, 0, n, j, kW, wj, A.sv);  // s' = W_{j-1}^T w
+      if (!grid_barrier(A, gen)) return;
+      const double om = __ldcg(wj + j + 1);
+      rowprod<2>(A, A.SR, A.ldr, 0, j, j, kUT, A.sv, 1, A.W + j + 1, n, [&](int r, double ss, double sw) {
+        const double col = -2.0 * ss;
+        A.SR[r + (size_t)j * A.ldr] = col;
+        A.p1[r] = fma(om, col, sw);
+        return 0.0;
+      }, nullptr);
+      if (gtid == 0) A.p1[j] = 2.0 * om;
+      if (!grid_barrier(A, gen)) return;
+    } else if (!rmake) {
+      const int c2 = A.nr;  // every right reflector made: p1 = R' W^T e_{j+1}
+      if (c2 > 0) {
+        rowprod<1>(A, A.SR, A.ldr, 0, c2, c2, kUT, A.W + j + 1, n, nullptr, 0, [&](int r, double s, double) {
+          A.p1[r] = s;
+          return 0.0;
+        }, nullptr);
+        if (!grid_barrier(A, gen)) return;
+      }
+    }
   }
 }
 
@@ -247,33 +500,6 @@ int grid_for(int64_t count, int threads) {
   return (int)(g < 1 ? 1 : (g > 1184 ? 1184 : g));
 }
 
-struct Gemv {
-  double *part;
-  int64_t ldp;
-  unsigned *cnt;
-  cudaStream_t s;
-  int64_t *launches;
-  cudaError_t err = cudaSuccess;
-  void t(const double *M, int64_t ld, int r0, int R, int C, int shape, const double *x, double scale, double *out) {
-    if (err != cudaSuccess || C <= 0) return;
-    const int threads = 256, blocks = grid_for((int64_t)C * 32, threads);
-    k_gemv_t<<<blocks, threads, 0, s>>>(M, ld, r0, R, C, shape, x, scale, out);
-    err = cudaGetLastError();
-    (*launches)++;
-  }
-  void n(const double *M, int64_t ld, int r0, int R, int C, int shape, const double *tv, int64_t ts,
-         const double *base, int unit, double scale, double *out) {
-    if (err != cudaSuccess || R <= r0) return;
-    if (C <= 0) {  // out = base(r) only
-      return;
-    }
-    dim3 grid((R - r0 + kRows - 1) / kRows, (C + kCols - 1) / kCols);
-    k_gemv_n<<<grid, kRows, 0, s>>>(M, ld, r0, R, C, shape, tv, ts, base, unit, scale, out, part, ldp, cnt);
-    err = cudaGetLastError();
-    (*launches)++;
-  }
-};
-
 }  // namespace
 
 BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps) {
@@ -283,104 +509,55 @@ BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps) {
   z.kr = steps < nr ? steps : nr;
   const int64_t big = m > n ? m : n;
   const int64_t chunks = (big + kCols - 1) / kCols + 1;
-  const int64_t tiles = (big + kRows - 1) / kRows + 1;
-  // vectors: z, x, a, q, ra, astar (big each), g, h, p1, gw, hw, sv (big each), dot (2), d, e (big each)
-  z.ws_doubles = 14 * big + 8 + chunks * big;
-  z.ws_counters = tiles;
+  const int64_t groups = (big + kT - 1) / kT + 1;
+  // twelve vectors, two partial-sum planes, the group partials
+  z.ws_doubles = 12 * big + 2 * chunks * big + groups + 8;
+  z.ws_counters = groups + 4;  // per row group, then the barrier's count and generation
   return z;
 }
 
 cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e, const double *u, const double *v,
                        double *alpha, double *beta, double *Y, double *W, double *SL, double *SR, double *ws,
-                       unsigned *cnt, cudaStream_t s, int64_t *launches) {
+                       unsigned *cnt, int *status, cudaStream_t s, int64_t *launches) {
   const BhuSizes z = bhu_sizes(m, n, steps);
-  const int nl = m > n ? n : n - 1, nr = n > 2 ? n - 2 : 0;
-  const int kl = (int)z.kl, kr = (int)z.kr;
   const int big = m > n ? m : n;
-  const int64_t ldl = kl > 0 ? kl : 1, ldr = kr > 0 ? kr : 1;
+  const int64_t chunks = (big + kCols - 1) / kCols + 1;
+  const int64_t groups = (big + kT - 1) / kT + 1;
+  BhuArgs A{};
+  A.m = m; A.n = n; A.steps = steps;
+  A.nl = m > n ? n : n - 1;
+  A.nr = n > 2 ? n - 2 : 0;
+  A.ldl = z.kl > 0 ? z.kl : 1;
+  A.ldr = z.kr > 0 ? z.kr : 1;
+  A.ldp = big;
+  A.d = d; A.e = e; A.u = u; A.v = v;
+  A.alpha = alpha; A.beta = beta; A.Y = Y; A.W = W; A.SL = SL; A.SR = SR;
   double *p = ws;
-  double *zv = p; p += big;
-  double *x = p; p += big;
-  double *av = p; p += big;
-  double *q = p; p += big;
-  double *ra = p; p += big;
-  double *as = p; p += big;
-  double *g = p; p += big;
-  double *hv = p; p += big;
-  double *p1 = p; p += big;
-  double *gw = p; p += big;
-  double *hw = p; p += big;
-  double *sv = p; p += big;
-  p += 2 * big;  // (d, e copies live with the caller)
-  double *dot = p; p += 8;
-  double *part = p;
-  int64_t dummy = 0;
-  Gemv G{part, big, cnt, s, launches ? launches : &dummy};
+  double **vecs[12] = {&A.z, &A.x, &A.a, &A.q, &A.ra, &A.as, &A.g, &A.hv, &A.p1, &A.gw, &A.hw, &A.sv};
+  for (double **vp : vecs) { *vp = p; p += big; }
+  A.part = p; p += chunks * big;
+  A.part2 = p; p += chunks * big;
+  A.tp = p;
+  A.cnt = cnt;
+  A.bar = cnt + groups;
+  A.status = status;
   cudaError_t err = cudaSuccess;
-  auto chk = [&]() { if (err == cudaSuccess) err = cudaGetLastError(); if (err == cudaSuccess) err = G.err; };
-  if (kl > 0) err = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)m * kl, s);
-  if (err == cudaSuccess && kr > 0) err = cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * kr, s);
-  if (err == cudaSuccess && kl > 0) err = cudaMemsetAsync(SL, 0, sizeof(double) * (size_t)kl * kl, s);
-  if (err == cudaSuccess && kr > 0) err = cudaMemsetAsync(SR, 0, sizeof(double) * (size_t)kr * kr, s);
-  const int vb = grid_for(big, 256);
-  for (int j = 0; j < steps && err == cudaSuccess; j++) {
-    // ---- column j of Q_{j-1}^T A P_{j-1}
-    const int cR = j < nr ? j : nr;  // right reflectors so far
-    if (cR > 0) {
-      G.n(SR, ldr, 0, cR, cR, kUT, W + j, n, nullptr, -1, 1.0, p1);   // p1 = R' W^T e_j
-      G.n(W, n, 0, n, cR, kW, p1, 1, nullptr, j, -1.0, zv);          // z = e_j - W p1
-    } else {
-      k_unit<<<vb, 256, 0, s>>>(zv, n, j);
-      (*G.launches)++;
-    }
-    k_dot<<<1, 1024, 0, s>>>(v, zv, n, dot);
-    k_bmv<<<vb, 256, 0, s>>>(d, e, m, n, zv, u, dot, x);
-    *G.launches += 2;
-    chk();
-    const double *acol = x;
-    const int cL = j < nl ? j : nl;  // left reflectors so far
-    if (cL > 0) {
-      G.t(Y, m, 0, m, cL, kY, x, 1.0, g);                            // g = Y^T x
-      G.t(SL, ldl, 0, cL, cL, kUT, g, 1.0, hv);                      // h = S^T g
-      G.n(Y, m, j, m, cL, kY, hv, 1, x, -1, -1.0, av);               // a = x - Y h (rows j..m)
-      acol = av;
-    }
-    const bool lmake = j < nl;
-    k_house<<<1, kHouseThreads, 0, s>>>(acol, j, m, lmake ? 1 : 0, lmake ? Y + (size_t)j * m : nullptr, alpha + j,
-                                        lmake ? SL + j + (size_t)j * ldl : nullptr);
-    (*G.launches)++;
-    chk();
-    if (lmake && j > 0) {
-      G.t(Y, m, 0, m, j, kY, Y + (size_t)j * m, 1.0, sv);           // s = Y^T y_j
-      G.n(SL, ldl, 0, j, j, kUT, sv, 1, nullptr, -1, -2.0, SL + (size_t)j * ldl);  // S(:, j) = -2 S s
-    }
-    if (j > n - 2) continue;
-    // ---- row j of Q_j^T A P_{j-1}
-    const int cL1 = (j + 1) < nl ? (j + 1) : nl;
-    G.n(SL, ldl, 0, cL1, cL1, kUT, Y + j, m, nullptr, -1, 1.0, p1);   // p1 = S Y^T e_j
-    G.n(Y, m, 0, m, cL1, kY, p1, 1, nullptr, j, -1.0, q);            // q = e_j - Y p1
-    k_dot<<<1, 1024, 0, s>>>(u, q, m, dot + 1);
-    k_bmvt<<<vb, 256, 0, s>>>(d, e, n, q, v, dot + 1, ra);
-    *G.launches += 2;
-    chk();
-    const double *arow = ra;
-    if (cR > 0) {
-      G.t(W, n, 0, n, cR, kW, ra, 1.0, gw);                          // gw = W^T r
-      G.t(SR, ldr, 0, cR, cR, kUT, gw, 1.0, hw);                     // hw = R'^T gw
-      G.n(W, n, j + 1, n, cR, kW, hw, 1, ra, -1, -1.0, as);          // a* = r - W hw (columns j+1..n)
-      arow = as;
-    }
-    const bool rmake = j < nr;
-    k_house<<<1, kHouseThreads, 0, s>>>(arow, j + 1, n, rmake ? 1 : 0, rmake ? W + (size_t)j * n : nullptr, beta + j,
-                                        rmake ? SR + j + (size_t)j * ldr : nullptr);
-    (*G.launches)++;
-    chk();
-    if (rmake && j > 0) {
-      G.t(W, n, 0, n, j, kW, W + (size_t)j * n, 1.0, sv);           // s = W^T w
-      G.n(SR, ldr, 0, j, j, kUT, sv, 1, nullptr, -1, -2.0, SR + (size_t)j * ldr);  // R'(:, j) = -2 R' s
-    }
-    chk();
-  }
+  if (z.kl > 0) err = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)m * z.kl, s);
+  if (err == cudaSuccess && z.kr > 0) err = cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * z.kr, s);
+  if (err == cudaSuccess && z.kl > 0) err = cudaMemsetAsync(SL, 0, sizeof(double) * (size_t)z.kl * z.kl, s);
+  if (err == cudaSuccess && z.kr > 0) err = cudaMemsetAsync(SR, 0, sizeof(double) * (size_t)z.kr * z.kr, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), s);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0, per = 0;
+  err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bhu_persist, kT, 0);
+  if (err != cudaSuccess) return err;
+  if (per < 1) return cudaErrorLaunchOutOfResources;
+  const int blocks = sms * (per > 2 ? 2 : per);
+  void *args[] = {&A};
+  err = cudaLaunchCooperativeKernel((const void *)k_bhu_persist, dim3(blocks), dim3(kT), args, 0, s);
+  if (launches) *launches += 1;
   return err;
 }
 
