@@ -440,7 +440,10 @@ void bdu_thin_destroy(bdu_thin_handle h);
  *     form) starts no copy of rotation records, and its compute warps give up
  *     after `value` polls of a wait;
  *   BDU_INJECT_ROTVEC_STALL: likewise for the rotation of projected vectors
- *     (overlapped mixed form and mixed rank-r updates).
+ *     (overlapped mixed form and mixed rank-r updates);
+ *   BDU_INJECT_BHU_STALL: the first block of the BHU kernel (bdu_bhu_factor,
+ *     bdu_update_bhu) leaves before its first grid barrier, and the other
+ *     blocks give up a barrier wait after `value` polls.
  * In each case nothing is in flight when the waits give up; the expiry sets a
  * bit of the handle's device status word, the next synchronizing call reports
  * BDU_ETIMEOUT and the handle is poisoned.  Returns BDU_EINVAL for an unknown
@@ -449,7 +452,8 @@ enum {
   BDU_INJECT_NONE = 0,
   BDU_INJECT_STEP_BUDGET = 1,
   BDU_INJECT_APPLY_STALL = 2,
-  BDU_INJECT_ROTVEC_STALL = 3
+  BDU_INJECT_ROTVEC_STALL = 3,
+  BDU_INJECT_BHU_STALL = 4
 };
 bdu_status bdu_set_fault_injection(int site, int64_t value);
 

@@ -136,7 +136,7 @@ def load(build_if_missing: bool = True):
     return L
 
 
-INJECT_NONE, INJECT_STEP_BUDGET, INJECT_APPLY_STALL, INJECT_ROTVEC_STALL = 0, 1, 2, 3
+INJECT_NONE, INJECT_STEP_BUDGET, INJECT_APPLY_STALL, INJECT_ROTVEC_STALL, INJECT_BHU_STALL = 0, 1, 2, 3, 4
 
 
 def set_fault_injection(site: int, value: int = 1) -> None:

@@ -2040,7 +2040,7 @@ bdu_status bdu_set_fault_injection(int site, int64_t value) {
     g_inject_value.store(0);
     return BDU_OK;
   }
-  if (site < BDU_INJECT_STEP_BUDGET || site > BDU_INJECT_ROTVEC_STALL || value < 1) return BDU_EINVAL;
+  if (site < BDU_INJECT_STEP_BUDGET || site > BDU_INJECT_BHU_STALL || value < 1) return BDU_EINVAL;
   g_inject_value.store(value);
   g_inject_site.store(site);
   return BDU_OK;

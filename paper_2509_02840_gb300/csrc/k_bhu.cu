@@ -114,6 +114,8 @@ struct BhuArgs {
   double *z, *x, *a, *q, *ra, *as, *g, *hv, *p1, *gw, *hw, *sv, *part, *part2, *tp;
   unsigned *cnt, *bar;  // counters per row group (zero, left zero); the barrier's count and generation (zero)
   int *status;
+  int spin;   // bound on one barrier wait (polls)
+  int stall;  // failure injection: block 0 leaves at once, so the others' first wait runs out
 };
 
 // Grid barrier (the blocks of a cooperative launch are co-resident): the last
@@ -133,7 +135,7 @@ __device__ bool grid_barrier(const BhuArgs &A, unsigned &gen) {
     } else {
       int it = 0;
       while (ld_acquire_u32(&A.bar[1]) == gen) {
-        if (++it > kBarSpin) {
+        if (++it > A.spin) {
           atomicOr(A.status, ERR_BHU);
           stop = 1;
           break;
@@ -311,6 +313,7 @@ __device__ void group_partials(int r0, int R, F w, double *tp_out) {
 // below, each ended by a grid barrier.
 __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
   unsigned gen = 0;
+  if (A.stall && blockIdx.x == 0) return;
   const int m = A.m, n = A.n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
   for (int j = 0; j < A.steps; j++) {
@@ -541,6 +544,9 @@ cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e
   A.cnt = cnt;
   A.bar = cnt + groups;
   A.status = status;
+  const Injection inj = injection();
+  A.stall = inj.site == BDU_INJECT_BHU_STALL ? 1 : 0;
+  A.spin = A.stall ? (int)(inj.value < kBarSpin ? inj.value : kBarSpin) : kBarSpin;
   cudaError_t err = cudaSuccess;
   if (z.kl > 0) err = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)m * z.kl, s);
   if (err == cudaSuccess && z.kr > 0) err = cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * z.kr, s);

@@ -117,3 +117,25 @@ def test_fault_injection_arguments_without_a_gpu(lib):
     assert lib.bdu_set_fault_injection(bdu.INJECT_NONE, 0) == 0
     with pytest.raises(bdu.BduError):
         bdu.set_fault_injection(bdu.INJECT_ROTVEC_STALL, 0)
+
+
+def test_bhu_sizes_and_argument_checks_without_a_gpu(lib):
+    """bdu_bhu_sizes gives Algorithm 1's reflector counts (Sec. 3.3: n-1 left
+    and n-2 right for m = n, one more left for m > n; fewer for a partial run)
+    and validates its sizes; the BHU entry points reject bad arguments before
+    touching the device."""
+    import ctypes
+    kl, kr, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    for (m, n, t, el, er) in ((6, 6, 6, 5, 4), (9, 6, 6, 6, 4), (9, 6, 2, 2, 2), (5, 1, 1, 1, 0), (2, 2, 2, 1, 0)):
+        assert lib.bdu_bhu_sizes(m, n, t, ctypes.byref(kl), ctypes.byref(kr), ctypes.byref(wb)) == 0
+        assert (kl.value, kr.value) == (el, er) and wb.value > 0
+    assert lib.bdu_bhu_sizes(5, 6, 5, None, None, None) == 1      # m < n
+    assert lib.bdu_bhu_sizes(6, 6, 7, None, None, None) == 1      # steps > n
+    assert lib.bdu_bhu_sizes(6, 0, 0, None, None, None) == 1      # n < 1
+    assert lib.bdu_bhu_factor(5, 6, 5, *([None] * 12)) == 1
+    assert lib.bdu_bhu_factor(6, 6, 6, *([None] * 12)) == 1       # NULL pointers
+    assert lib.bdu_update_bhu(None, None, None, 1) == 1
+    assert lib.bdu_update_bhu_dev(None, None, None, 1) == 1
+    assert lib.bdu_set_fault_injection(bdu.INJECT_BHU_STALL, 0) == 1
+    assert lib.bdu_set_fault_injection(bdu.INJECT_BHU_STALL, 5) == 0
+    assert lib.bdu_set_fault_injection(bdu.INJECT_NONE, 0) == 0

@@ -107,3 +107,32 @@ def test_bounded_waits_expire_and_poison(site, rank, what):
     finally:
         F.close()
     _healthy_update_still_works(m, n)
+
+
+def test_bhu_grid_barrier_expires_and_poisons():
+    """BHU's grid barriers are bounded waits: failure injection makes the first
+    block leave before it arrives, so every other block's first wait runs out
+    (after 2000 polls); the kernel records the expiry and all blocks return."""
+    m, n = 96, 80
+    Q, d, e, P = I.factorization(m, n, config=0, which=5)
+    B, C = I.dense_update(m, n, 0, config=0, r=1)
+    F = bdu.Factorization(Q, d, e, P, precision=bdu.FP64)
+    try:
+        bdu.set_fault_injection(bdu.INJECT_BHU_STALL, 2000)
+        try:
+            with pytest.raises(bdu.BduError) as info:
+                F.update_bhu(B, C)
+                F.sync()
+        finally:
+            bdu.set_fault_injection(bdu.INJECT_NONE)
+        assert info.value.code == ETIMEOUT and "grid barrier" in str(info.value)
+        with pytest.raises(bdu.BduError) as again:
+            F.update_bhu(B, C)
+        assert again.value.code == EPOISONED
+    finally:
+        F.close()
+    # a fresh handle runs BHU normally afterwards
+    with bdu.Factorization(Q, d, e, P, precision=bdu.FP64) as G:
+        G.update_bhu(B, C)
+        G.sync()
+    _healthy_update_still_works(m, n)
