@@ -72,6 +72,8 @@ def parse():
                     help="rows of Q and P the CPU oracle applies in its bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bhu", action="store_true", help="no BHU (Algorithm 1) measurement in the bench line")
+    ap.add_argument("--bhu", action="store_true",
+                    help="only the BHU measurement, at m = n = --size (profiling runs; --steps timed updates)")
     ap.add_argument("--size", type=int, default=4096,
                     help="m = n of the workload (4096 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--quick", action="store_true",
@@ -286,7 +288,7 @@ def serving(args):
     return out
 
 
-def bhu_bench(steps=2):
+def bhu_bench(steps=2, shapes=None):
     """BHU (Sec. 3.3, Algorithm 1) beside the FP64 Givens form on the same
     rank-1 updates, at m = n = 4096 (the recommender stream) and m = 8192 x
     n = 2048 (dense b, c: a tall factorization, the case Sec. 3.3 names for
@@ -300,7 +302,8 @@ def bhu_bench(steps=2):
     from paper_2509_02840_gb300 import bdu, inputs as I
     peak = 152 * 2 * 2 * 2.07e9
     out = {}
-    for name, m, n in (("recommender_4096", M, N), ("tall_8192x2048", 8192, 2048)):
+    shapes = shapes or ((f"recommender_{M}", M, N), ("tall_8192x2048", 8192, 2048))
+    for name, m, n in shapes:
         Q, d, e, P = I.factorization(m, n, config=1 if m == n else 2)
         if m == n:
             ups = [I.recommender_update(m, n, h + 500, config=1) for h in range(steps + 1)]
@@ -722,6 +725,13 @@ def main():
         return
     if args.network:
         run_network(args)
+        return
+    if args.bhu:
+        r = bhu_bench(steps=args.steps, shapes=((f"m=n={M}", M, N),))[f"m=n={M}"]
+        print(json.dumps({"metric": "BHU updates/s (Algorithm 1, FP64)", "value": r["bhu_updates_per_s"],
+                          "unit": "updates/s", "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+                          "dtype": "f64", "data": "synthetic", "config": {"workload": f"recommender m=n={M}"},
+                          "bhu": r}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
