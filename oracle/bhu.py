@@ -40,6 +40,12 @@ Readings (listed with the others in the design notes):
 - A partial factorization after t iterations of the loop is the matrix after
   the first t left reflectors and the right reflectors that come with them
   (Sec. 3.3: stopping early gives a partial factorization).
+- Direct rank-r absorption.  Sec. 3.2 takes rank r as r repeated rank-1 steps.
+  Algorithm 1 needs only the products of A with a vector, so it runs just as
+  well once on B + U V^T with the r projected columns U = Q^T B, V = P^T C
+  (Theorem 1's first block grows from one column to r).  The result keeps
+  P's first column, as r sequential sweeps do, so by the implicit-Q theorem
+  the two bidiagonals agree up to the signs of their entries.
 
 Functions
 ---------
@@ -48,6 +54,7 @@ bhu(d, e, u, v, m, steps=None)        Algorithm 1 on B + u v^T (dense form)
 factors(Y, W, m, n)                   Q_k, P_k as explicit products (Eq. QP)
 theorem1(d, e, u, v, m, Y, W)         the factored form of Eq. comp
 update(Q, d, e, P, Bm, Cm)            a rank-r update by r BHU steps (Eq. bidiagplus)
+update_direct(Q, d, e, P, Bm, Cm)     a rank-r update by one BHU sweep on B + U V^T
 """
 import numpy as np
 
@@ -82,7 +89,8 @@ def counts(m, n):
 
 
 def bhu(d, e, u, v, m, steps=None):
-    """Algorithm 1 (Sec. 3.3) on A = B + u v^T, written out on the dense matrix.
+    """Algorithm 1 (Sec. 3.3) on A = B + u v^T, written out on the dense matrix
+    (u, v may also be m x r and n x r: A = B + U V^T, direct rank-r absorption).
 
     Returns a dict with
       alpha (steps,), beta (min(steps, n-1),): the new diagonal / superdiagonal,
@@ -97,7 +105,9 @@ def bhu(d, e, u, v, m, steps=None):
     t = n if steps is None else int(steps)
     assert 0 <= t <= n
     nl, nr = counts(m, n)
-    A = bidiag_dense(d, e, m) + np.outer(np.asarray(u, dtype=np.float64), np.asarray(v, dtype=np.float64))
+    U = np.asarray(u, dtype=np.float64).reshape(m, -1)
+    V = np.asarray(v, dtype=np.float64).reshape(n, -1)
+    A = bidiag_dense(d, e, m) + U @ V.T
     alpha = np.zeros(t)
     beta = np.zeros(min(t, n - 1))
     Y = np.zeros((m, min(t, nl)))
@@ -180,3 +190,17 @@ def update(Q, d, e, P, Bm, Cm):
         d = r["alpha"]
         e = r["beta"]
     return Q, d, e, P
+
+
+def update_direct(Q, d, e, P, Bm, Cm):
+    """Rank-r update A + Bm Cm^T by one BHU sweep on B + U V^T with U = Q^T Bm,
+    V = P^T Cm (direct rank-r absorption), then Q <- Q Q_k, P <- P P_k and
+    (d, e) <- (alpha, beta)."""
+    Q = np.array(Q, dtype=np.float64, copy=True)
+    P = np.array(P, dtype=np.float64, copy=True)
+    m, n = Q.shape[0], P.shape[0]
+    U = Q.T @ np.asarray(Bm, dtype=np.float64).reshape(m, -1)
+    V = P.T @ np.asarray(Cm, dtype=np.float64).reshape(n, -1)
+    r = bhu(d, e, U, V, m)
+    Qk, Pk = factors(r["Y"], r["W"], m, n)
+    return Q @ Qk, r["alpha"], r["beta"], P @ Pk

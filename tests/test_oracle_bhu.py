@@ -134,3 +134,40 @@ def test_full_update_matches_givens_update():
     assert np.abs(np.abs(dh) - np.abs(dg)).max() <= 1e-12 * np.linalg.norm(A1)
     assert np.abs(np.abs(eh) - np.abs(eg)).max() <= 1e-12 * np.linalg.norm(A1)
     assert np.array_equal(Ph[:, 0], P[:, 0]) or np.abs(Ph[:, 0] - P[:, 0]).max() <= 1e-15
+
+
+@pytest.mark.parametrize("m,n,rk", [(14, 10, 2), (20, 20, 3), (33, 17, 5), (12, 12, 12)])
+def test_direct_rank_r_matches_givens_update(m, n, rk):
+    """One BHU sweep on B + U V^T against the Givens oracle's r rank-1 steps:
+    both keep P's first column, so the bidiagonals agree up to signs; the
+    factorization reconstructs A + B C^T."""
+    rng = np.random.default_rng(m * 31 + rk)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    P, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = rng.standard_normal(n); e = rng.standard_normal(n - 1)
+    Bm = rng.standard_normal((m, rk)); Cm = rng.standard_normal((n, rk))
+    Qh, dh, eh, Ph = H.update_direct(Q, d, e, P, Bm, Cm)
+    Qg, dg, eg, Pg, _ = O.update(Q, d, e, P, Bm, Cm)
+    A1 = Q @ H.bidiag_dense(d, e, m) @ P.T + Bm @ Cm.T
+    scale = np.linalg.norm(A1)
+    assert np.abs(Qh @ H.bidiag_dense(dh, eh, m) @ Ph.T - A1).max() <= 1e-13 * scale
+    assert np.abs(np.abs(dh) - np.abs(dg)).max() <= 1e-12 * scale
+    assert np.abs(np.abs(eh) - np.abs(eg)).max() <= 1e-12 * scale
+    assert np.array_equal(Ph[:, 0], P[:, 0]) or np.abs(Ph[:, 0] - P[:, 0]).max() <= 1e-15
+    s0 = np.linalg.svd(A1, compute_uv=False)
+    assert np.abs(s0 - np.linalg.svd(H.bidiag_dense(dh, eh, m), compute_uv=False)).max() <= 1e-13 * s0[0]
+
+
+@pytest.mark.parametrize("m,n,rk", [(30, 30, 1), (30, 30, 3), (40, 25, 4)])
+def test_rank_r_terminates(m, n, rk):
+    """B = 0: A = U V^T has rank r, and the Householder bidiagonalization with
+    P's first column kept ends after r + 1 columns (its Krylov space from
+    p_1 = e_1 has dimension <= r + 1): every later alpha, beta vanishes, and
+    alpha, beta carry all of ||U V^T||_F^2."""
+    rng = np.random.default_rng(m + 10 * rk)
+    U = rng.standard_normal((m, rk)); V = rng.standard_normal((n, rk))
+    r = H.bhu(np.zeros(n), np.zeros(n - 1), U, V, m)
+    nf = np.linalg.norm(U @ V.T)
+    assert np.abs(r["alpha"][rk + 1:]).max() <= 1e-13 * nf
+    assert np.abs(r["beta"][rk + 1:]).max() <= 1e-13 * nf
+    assert abs(np.sum(r["alpha"] ** 2) + np.sum(r["beta"] ** 2) - nf ** 2) <= 1e-12 * nf ** 2
