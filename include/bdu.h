@@ -210,9 +210,15 @@ bdu_status bdu_update_batch(bdu_handle *hs, int count, const double *const *dB, 
 bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64_t *kr,
                          int64_t *workspace_bytes);
 
-/* Algorithm 1 on B + u v^T, FP64, every pointer in device memory,
+/* Columns of U, V one BHU sweep absorbs (bdu_bhu_factor's r). */
+#define BDU_BHU_MAX_RANK 8
+
+/* Algorithm 1 on B + U V^T, FP64, every pointer in device memory,
  * column-major:
- *   in:  d (n), e (n-1; may be NULL when n == 1), u (m), v (n);
+ *   in:  d (n), e (n-1; may be NULL when n == 1), U (m x r, leading
+ *        dimension m), V (n x r, leading dimension n), 1 <= r <=
+ *        BDU_BHU_MAX_RANK: the projected columns U = Q^T B, V = P^T C (Eq. rk1);
+ *        r > 1 absorbs a rank-r update in one sweep instead of r;
  *   out: alpha (steps), beta (min(steps, n-1); may be NULL when n == 1): the
  *        first `steps` diagonal and superdiagonal entries of the new
  *        bidiagonal (a partial factorization when steps < n, Sec. 3.3);
@@ -230,12 +236,13 @@ bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64
  * bounded waits.
  * Errors: BDU_EINVAL (sizes, NULL pointers, unaligned workspace), BDU_ECUDA,
  * BDU_ETIMEOUT (a grid barrier ran out). */
-bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, const double *e,
-                          const double *u, const double *v, double *alpha, double *beta, double *Y,
+bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t r, int64_t steps, const double *d, const double *e,
+                          const double *U, const double *V, double *alpha, double *beta, double *Y,
                           double *W, double *SL, double *SR, void *workspace, void *stream);
 
-/* A+ = A + B C^T by BHU instead of the Givens update: for each of the r
- * columns, u = Q^T b, v = P^T c with the current factors, Algorithm 1 to
+/* A+ = A + B C^T by BHU instead of the Givens update: the r columns in sweeps
+ * of up to BDU_BHU_MAX_RANK (direct rank-r absorption): U = Q^T B(:, cols),
+ * V = P^T C(:, cols) with the current factors, Algorithm 1 on B + U V^T to
  * completion, Q <- Q - (Q Y) SL Y^T, P <- P - (P W) SR W^T (cuBLAS FP64
  * products) and (d, e) <- (alpha, beta).  FP64 handles only; m < n through the
  * transposed form as bdu_update.  Host (bdu_update_bhu) or device

@@ -126,7 +126,7 @@ def load(build_if_missing: bool = True):
     L.bdu_bhu_sizes.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i64p, i64p, i64p]
     L.bdu_bhu_sizes.restype = ctypes.c_int
     vp = ctypes.c_void_p
-    L.bdu_bhu_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + [vp] * 12
+    L.bdu_bhu_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + [vp] * 12
     L.bdu_bhu_factor.restype = ctypes.c_int
     L.bdu_update_bhu.argtypes = [H, dp, dp, ctypes.c_int64]
     L.bdu_update_bhu.restype = ctypes.c_int
@@ -208,12 +208,16 @@ def bhu_sizes(m: int, n: int, steps: int):
     return kl.value, kr.value, wb.value
 
 
+BHU_MAX_RANK = 8
+
+
 def bhu_factor(m: int, n: int, steps: int, d: int, e: int, u: int, v: int, alpha: int, beta: int, Y: int, W: int,
-               SL: int, SR: int, workspace: int, stream: int = 0):
-    """bdu_bhu_factor with device pointers (ints; 0 for NULL)."""
+               SL: int, SR: int, workspace: int, stream: int = 0, r: int = 1):
+    """bdu_bhu_factor with device pointers (ints; 0 for NULL); u, v hold r
+    columns (leading dimensions m and n)."""
     L = load()
     ptrs = [ctypes.c_void_p(p or None) for p in (d, e, u, v, alpha, beta, Y, W, SL, SR, workspace, stream)]
-    code = L.bdu_bhu_factor(int(m), int(n), int(steps), *ptrs)
+    code = L.bdu_bhu_factor(int(m), int(n), int(r), int(steps), *ptrs)
     if code != 0:
         raise BduError(code, (L.bdu_last_error(None) or b"").decode())
 

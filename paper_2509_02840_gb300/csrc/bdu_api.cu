@@ -1360,11 +1360,12 @@ bdu_status bdu_bhu_sizes(int64_t m, int64_t n, int64_t steps, int64_t *kl, int64
   return BDU_OK;
 }
 
-bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, const double *e, const double *u,
-                          const double *v, double *alpha, double *beta, double *Y, double *W, double *SL,
-                          double *SR, void *workspace, void *stream) {
+bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t r, int64_t steps, const double *d, const double *e,
+                          const double *u, const double *v, double *alpha, double *beta, double *Y, double *W,
+                          double *SL, double *SR, void *workspace, void *stream) {
   if (m < n || n < 1 || steps < 0 || steps > n || m > (int64_t)1 << 30)
     return fail(nullptr, BDU_EINVAL, "bdu_bhu_factor: need m >= n >= 1 and 0 <= steps <= n");
+  if (r < 1 || r > BDU_BHU_MAX_RANK) return fail(nullptr, BDU_EINVAL, "bdu_bhu_factor: need 1 <= r <= %d", BDU_BHU_MAX_RANK);
   if (steps == 0) return BDU_OK;
   const BhuSizes z = bhu_sizes(m, n, steps);
   if (!d || !u || !v || !alpha || !workspace || (n > 1 && !e) || (steps > 0 && n > 1 && !beta) ||
@@ -1377,8 +1378,8 @@ bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t steps, const double *d, 
   int *status = (int *)(cnt + z.ws_counters);
   cudaError_t ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * z.ws_counters + sizeof(int), s);
   if (ce == cudaSuccess)
-    ce = launch_bhu((int)m, (int)n, (int)steps, d, n > 1 ? e : d, u, v, alpha, n > 1 ? beta : alpha, Y, W, SL, SR,
-                    ws, cnt, status, s, nullptr);
+    ce = launch_bhu((int)m, (int)n, (int)steps, (int)r, d, n > 1 ? e : d, u, m, v, n, alpha, n > 1 ? beta : alpha,
+                    Y, W, SL, SR, ws, cnt, status, s, nullptr);
   int hst = 0;
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1445,13 +1446,15 @@ static bdu_status run_update_bhu(bdu_ctx *h, const double *dB, const double *dC,
   if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS) return fail(h, BDU_EINTERNAL, "cublasSetStream failed");
   double *d = h->bhu_vec, *e = d + (n + 1), *alpha = e + (n + 1), *beta = alpha + (n + 1);
   int64_t launches = 0;
-  for (int64_t k = 0; k < r; k++) {
-    // u = Q^T b, v = P^T c with the current factors
-    cudaError_t ce = launch_project_nz(BDU_FP64, h->Q, m, (int)m, (int)m, dB + k * m, m, 1, h->U, m, h->nzB, s);
-    if (ce == cudaSuccess) ce = launch_project_nz(BDU_FP64, h->P, n, (int)n, (int)n, dC + k * n, n, 1, h->V, n, h->nzC, s);
+  // direct rank-r absorption: up to BDU_BHU_MAX_RANK columns per sweep
+  for (int64_t k0 = 0; k0 < r; k0 += BDU_BHU_MAX_RANK) {
+    const int rc = (int)std::min<int64_t>(BDU_BHU_MAX_RANK, r - k0);
+    // U = Q^T B(:, k0..), V = P^T C(:, k0..) with the current factors
+    cudaError_t ce = launch_project_nz(BDU_FP64, h->Q, m, (int)m, (int)m, dB + k0 * m, m, rc, h->U, m, h->nzB, s);
+    if (ce == cudaSuccess) ce = launch_project_nz(BDU_FP64, h->P, n, (int)n, (int)n, dC + k0 * n, n, rc, h->V, n, h->nzC, s);
     if (ce == cudaSuccess) ce = launch_bhu_band_get(h->band, (int)m, (int)n, d, e, s);
     if (ce == cudaSuccess)
-      ce = launch_bhu((int)m, (int)n, (int)n, d, e, h->U, h->V, alpha, beta, h->bhu_Y, h->bhu_W, h->bhu_SL,
+      ce = launch_bhu((int)m, (int)n, (int)n, rc, d, e, h->U, m, h->V, n, alpha, beta, h->bhu_Y, h->bhu_W, h->bhu_SL,
                       h->bhu_SR, h->bhu_ws, h->bhu_cnt, h->status, s, &launches);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "BHU reflectors");
     if (!bhu_apply_factor(cb, (double *)h->Q, m, h->bhu_Y, z.kl, h->bhu_SL, h->bhu_G1, h->bhu_G2) ||
@@ -1460,7 +1463,7 @@ static bdu_status run_update_bhu(bdu_ctx *h, const double *dB, const double *dC,
     ce = launch_bhu_band_put(h->band, (int)m, (int)n, alpha, beta, s);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "BHU: storing the bidiagonal");
     launches += 6;
-    h->updates++;
+    h->updates += rc;
     h->bhu_updates++;
   }
   h->launches += launches;

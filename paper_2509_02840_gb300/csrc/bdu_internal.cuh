@@ -228,9 +228,11 @@ struct BhuSizes {
 };
 BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps);
 // status: the device status word (ERR_BHU when a grid barrier runs out).
-cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e, const double *u, const double *v,
-                       double *alpha, double *beta, double *Y, double *W, double *SL, double *SR, double *ws,
-                       unsigned *cnt, int *status, cudaStream_t s, int64_t *launches);
+// rk (1..BDU_BHU_MAX_RANK) columns of U (leading dimension ldu) and V (ldv).
+cudaError_t launch_bhu(int m, int n, int steps, int rk, const double *d, const double *e, const double *u,
+                       int64_t ldu, const double *v, int64_t ldv, double *alpha, double *beta, double *Y, double *W,
+                       double *SL, double *SR, double *ws, unsigned *cnt, int *status, cudaStream_t s,
+                       int64_t *launches);
 cudaError_t launch_bhu_band_get(double *band, int m, int n, double *d, double *e, cudaStream_t s);
 cudaError_t launch_bhu_band_put(double *band, int m, int n, const double *d, const double *e, cudaStream_t s);
 

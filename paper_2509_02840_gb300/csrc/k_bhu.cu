@@ -104,12 +104,16 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 }
 
 constexpr int kT = 512;           // threads of a block = rows of a row group
+constexpr int kMaxRank = BDU_BHU_MAX_RANK;  // columns of U, V one sweep absorbs
 constexpr int kBarSpin = 1 << 22;  // bound on the wait of one grid barrier
 
 struct BhuArgs {
   int m, n, steps, nl, nr;
   int64_t ldl, ldr, ldp;
-  const double *d, *e, *u, *v;
+  const double *d, *e;
+  const double *u, *v;  // U (m x rk, leading dimension ldu), V (n x rk, ldv)
+  int rk;
+  int64_t ldu, ldv, tps;  // tps: stride of the group partials of the rk dot products
   double *alpha, *beta, *Y, *W, *SL, *SR;
   double *z, *x, *a, *q, *ra, *as, *g, *hv, *p1, *gw, *hw, *sv, *part, *part2, *tp;
   unsigned *cnt, *bar;  // counters per row group (zero, left zero); the barrier's count and generation (zero)
@@ -207,11 +211,13 @@ __device__ void colprod(const double *__restrict__ M, int64_t ld, int r0, int R,
 // Row products over rows [r0, R), columns [0, C): s0(r) = sum_c M(r, c) t0[c ts0]
 // (and s1(r) with t1 when NV = 2).  Tiles of kT rows x kCols columns go to the
 // blocks; each writes its partial sums, and the last block of a row group to
-// finish adds them in chunk order and calls epi(r, s0, s1), whose return
-// values it sums over the group into tp_out[group] (when tp_out is set).
+// finish adds them in chunk order and calls epi(r, s0, s1, c), which stores
+// the row's results and its shares c[0..np) of np sums; those are added over
+// the group into tp_out[k tps + group] (when tp_out is set).
 template <int NV, class Epi>
 __device__ void rowprod(const BhuArgs &A, const double *__restrict__ M, int64_t ld, int r0, int R, int C, int shape,
-                        const double *t0, int64_t ts0, const double *t1, int64_t ts1, Epi epi, double *tp_out) {
+                        const double *t0, int64_t ts0, const double *t1, int64_t ts1, Epi epi, double *tp_out,
+                        int np = 1) {
   __shared__ double tc[2][kCols];
   __shared__ int s_last;
   __shared__ double red[32];
@@ -261,7 +267,9 @@ __device__ void rowprod(const BhuArgs &A, const double *__restrict__ M, int64_t 
     __syncthreads();
     if (s_last) {
       __threadfence();
-      double contrib = 0.0;
+      double contrib[kMaxRank];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; k++) contrib[k] = 0.0;
       if (r < rb) {
         // the chunks that hold more than structural zeros form one range
         // [k0, k1); eight partial loads in flight, added in chunk order
@@ -287,11 +295,13 @@ __device__ void rowprod(const BhuArgs &A, const double *__restrict__ M, int64_t 
           a0 += __ldcg(A.part + (size_t)k * A.ldp + r);
           if (NV == 2) a1 += __ldcg(A.part2 + (size_t)k * A.ldp + r);
         }
-        contrib = epi(r, a0, a1);
+        epi(r, a0, a1, contrib);
       }
       if (tp_out) {
-        const double sum = block_sum(contrib, red);
-        if (threadIdx.x == 0) tp_out[gi] = sum;
+        for (int k = 0; k < np; k++) {
+          const double sum = block_sum(contrib[k], red);
+          if (threadIdx.x == 0) tp_out[k * A.tps + gi] = sum;
+        }
       }
     }
   }
@@ -320,23 +330,25 @@ __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
     const int cR = min(j, A.nr), cL = min(j, A.nl);
     // z = P_{j-1} e_j = e_j - W p1, p1 = R' W^T e_j (from the previous step); partials of v^T z
     if (cR > 0) {
-      rowprod<1>(A, A.W, n, 0, n, cR, kW, A.p1, 1, nullptr, 0, [&](int r, double s, double) {
+      rowprod<1>(A, A.W, n, 0, n, cR, kW, A.p1, 1, nullptr, 0, [&](int r, double s, double, double *c) {
         const double zr = (r == j ? 1.0 : 0.0) - s;
         A.z[r] = zr;
-        return A.v[r] * zr;
-      }, A.tp);
+        for (int k = 0; k < A.rk; k++) c[k] = A.v[r + k * A.ldv] * zr;
+      }, A.tp, A.rk);
     } else {
       for (int r = gtid; r < n; r += gthreads) A.z[r] = r == j ? 1.0 : 0.0;
     }
     if (!grid_barrier(A, gen)) return;
-    // x = B z + u (v^T z)
+    // x = B z + U (V^T z)
     {
-      const double w = cR > 0 ? tp_sum(A.tp, groups_of(n)) : A.v[j];
+      double w[kMaxRank];
+      for (int k = 0; k < A.rk; k++) w[k] = cR > 0 ? tp_sum(A.tp + k * A.tps, groups_of(n)) : A.v[j + k * A.ldv];
       for (int r = gtid; r < m; r += gthreads) {
         double s = 0.0;
         if (r < n) s = A.d[r] * __ldcg(A.z + r);
         if (r + 1 < n) s = fma(A.e[r], __ldcg(A.z + r + 1), s);
-        A.x[r] = fma(A.u[r], w, s);
+        for (int k = 0; k < A.rk; k++) s = fma(A.u[r + k * A.ldu], w[k], s);
+        A.x[r] = s;
       }
     }
     if (!grid_barrier(A, gen)) return;
@@ -347,10 +359,10 @@ __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
       if (!grid_barrier(A, gen)) return;
       colprod(A.SL, A.ldl, 0, cL, cL, kUT, A.g, A.hv);
       if (!grid_barrier(A, gen)) return;
-      rowprod<1>(A, A.Y, m, j, m, cL, kY, A.hv, 1, nullptr, 0, [&](int r, double s, double) {
+      rowprod<1>(A, A.Y, m, j, m, cL, kY, A.hv, 1, nullptr, 0, [&](int r, double s, double, double *c) {
         const double ar = __ldcg(A.x + r) - s;
         A.a[r] = ar;
-        return ar * ar;
+        c[0] = ar * ar;
       }, A.tp);
       acol = A.a;
     } else {
@@ -387,31 +399,32 @@ __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
       colprod(A.Y, m, 0, m, j, kY, yj, A.sv);
       if (!grid_barrier(A, gen)) return;
       const double eta = __ldcg(yj + j);
-      rowprod<2>(A, A.SL, A.ldl, 0, j, j, kUT, A.sv, 1, A.Y + j, m, [&](int r, double ss, double sy) {
+      rowprod<2>(A, A.SL, A.ldl, 0, j, j, kUT, A.sv, 1, A.Y + j, m, [&](int r, double ss, double sy, double *) {
         const double col = -2.0 * ss;
         A.SL[r + (size_t)j * A.ldl] = col;
         A.p1[r] = fma(eta, col, sy);
-        return 0.0;
       }, nullptr);
       if (gtid == 0) A.p1[j] = 2.0 * eta;
       if (!grid_barrier(A, gen)) return;
     }
     if (!right) continue;
-    // q = Q_j e_j = e_j - Y p1; partials of u^T q
+    // q = Q_j e_j = e_j - Y p1; partials of U^T q
     const int cL1 = min(j + 1, A.nl);
-    rowprod<1>(A, A.Y, m, 0, m, cL1, kY, A.p1, 1, nullptr, 0, [&](int r, double s, double) {
+    rowprod<1>(A, A.Y, m, 0, m, cL1, kY, A.p1, 1, nullptr, 0, [&](int r, double s, double, double *c) {
       const double qr = (r == j ? 1.0 : 0.0) - s;
       A.q[r] = qr;
-      return A.u[r] * qr;
-    }, A.tp);
+      for (int k = 0; k < A.rk; k++) c[k] = A.u[r + k * A.ldu] * qr;
+    }, A.tp, A.rk);
     if (!grid_barrier(A, gen)) return;
-    // r = B^T q + v (u^T q)
+    // r = B^T q + V (U^T q)
     {
-      const double w = tp_sum(A.tp, groups_of(m));
+      double w[kMaxRank];
+      for (int k = 0; k < A.rk; k++) w[k] = tp_sum(A.tp + k * A.tps, groups_of(m));
       for (int c = gtid; c < n; c += gthreads) {
         double s = A.d[c] * __ldcg(A.q + c);
         if (c > 0) s = fma(A.e[c - 1], __ldcg(A.q + c - 1), s);
-        A.ra[c] = fma(A.v[c], w, s);
+        for (int k = 0; k < A.rk; k++) s = fma(A.v[c + k * A.ldv], w[k], s);
+        A.ra[c] = s;
       }
     }
     if (!grid_barrier(A, gen)) return;
@@ -422,10 +435,10 @@ __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
       if (!grid_barrier(A, gen)) return;
       colprod(A.SR, A.ldr, 0, cR, cR, kUT, A.gw, A.hw);
       if (!grid_barrier(A, gen)) return;
-      rowprod<1>(A, A.W, n, j + 1, n, cR, kW, A.hw, 1, nullptr, 0, [&](int r, double s, double) {
+      rowprod<1>(A, A.W, n, j + 1, n, cR, kW, A.hw, 1, nullptr, 0, [&](int r, double s, double, double *c) {
         const double ar = __ldcg(A.ra + r) - s;
         A.as[r] = ar;
-        return ar * ar;
+        c[0] = ar * ar;
       }, A.tp);
       arow = A.as;
     } else {
@@ -461,20 +474,18 @@ __global__ void __launch_bounds__(kT, 1) k_bhu_persist(BhuArgs A) {
       colprod(A.W, n, 0, n, j, kW, wj, A.sv);  // s' = W_{j-1}^T w
       if (!grid_barrier(A, gen)) return;
       const double om = __ldcg(wj + j + 1);
-      rowprod<2>(A, A.SR, A.ldr, 0, j, j, kUT, A.sv, 1, A.W + j + 1, n, [&](int r, double ss, double sw) {
+      rowprod<2>(A, A.SR, A.ldr, 0, j, j, kUT, A.sv, 1, A.W + j + 1, n, [&](int r, double ss, double sw, double *) {
         const double col = -2.0 * ss;
         A.SR[r + (size_t)j * A.ldr] = col;
         A.p1[r] = fma(om, col, sw);
-        return 0.0;
       }, nullptr);
       if (gtid == 0) A.p1[j] = 2.0 * om;
       if (!grid_barrier(A, gen)) return;
     } else if (!rmake) {
       const int c2 = A.nr;  // every right reflector made: p1 = R' W^T e_{j+1}
       if (c2 > 0) {
-        rowprod<1>(A, A.SR, A.ldr, 0, c2, c2, kUT, A.W + j + 1, n, nullptr, 0, [&](int r, double s, double) {
+        rowprod<1>(A, A.SR, A.ldr, 0, c2, c2, kUT, A.W + j + 1, n, nullptr, 0, [&](int r, double s, double, double *) {
           A.p1[r] = s;
-          return 0.0;
         }, nullptr);
         if (!grid_barrier(A, gen)) return;
       }
@@ -513,15 +524,17 @@ BhuSizes bhu_sizes(int64_t m, int64_t n, int64_t steps) {
   const int64_t big = m > n ? m : n;
   const int64_t chunks = (big + kCols - 1) / kCols + 1;
   const int64_t groups = (big + kT - 1) / kT + 1;
-  // twelve vectors, two partial-sum planes, the group partials
-  z.ws_doubles = 12 * big + 2 * chunks * big + groups + 8;
+  // twelve vectors, two partial-sum planes, the group partials of kMaxRank sums
+  z.ws_doubles = 12 * big + 2 * chunks * big + kMaxRank * groups + 8;
   z.ws_counters = groups + 4;  // per row group, then the barrier's count and generation
   return z;
 }
 
-cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e, const double *u, const double *v,
-                       double *alpha, double *beta, double *Y, double *W, double *SL, double *SR, double *ws,
-                       unsigned *cnt, int *status, cudaStream_t s, int64_t *launches) {
+cudaError_t launch_bhu(int m, int n, int steps, int rk, const double *d, const double *e, const double *u,
+                       int64_t ldu, const double *v, int64_t ldv, double *alpha, double *beta, double *Y, double *W,
+                       double *SL, double *SR, double *ws, unsigned *cnt, int *status, cudaStream_t s,
+                       int64_t *launches) {
+  if (rk < 1 || rk > kMaxRank) return cudaErrorInvalidValue;
   const BhuSizes z = bhu_sizes(m, n, steps);
   const int big = m > n ? m : n;
   const int64_t chunks = (big + kCols - 1) / kCols + 1;
@@ -534,6 +547,7 @@ cudaError_t launch_bhu(int m, int n, int steps, const double *d, const double *e
   A.ldr = z.kr > 0 ? z.kr : 1;
   A.ldp = big;
   A.d = d; A.e = e; A.u = u; A.v = v;
+  A.rk = rk; A.ldu = ldu; A.ldv = ldv; A.tps = groups;
   A.alpha = alpha; A.beta = beta; A.Y = Y; A.W = W; A.SL = SL; A.SR = SR;
   double *p = ws;
   double **vecs[12] = {&A.z, &A.x, &A.a, &A.q, &A.ra, &A.as, &A.g, &A.hv, &A.p1, &A.gw, &A.hw, &A.sv};

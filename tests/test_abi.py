@@ -132,8 +132,10 @@ def test_bhu_sizes_and_argument_checks_without_a_gpu(lib):
     assert lib.bdu_bhu_sizes(5, 6, 5, None, None, None) == 1      # m < n
     assert lib.bdu_bhu_sizes(6, 6, 7, None, None, None) == 1      # steps > n
     assert lib.bdu_bhu_sizes(6, 0, 0, None, None, None) == 1      # n < 1
-    assert lib.bdu_bhu_factor(5, 6, 5, *([None] * 12)) == 1
-    assert lib.bdu_bhu_factor(6, 6, 6, *([None] * 12)) == 1       # NULL pointers
+    assert lib.bdu_bhu_factor(5, 6, 1, 5, *([None] * 12)) == 1
+    assert lib.bdu_bhu_factor(6, 6, 1, 6, *([None] * 12)) == 1    # NULL pointers
+    assert lib.bdu_bhu_factor(6, 6, 9, 6, *([None] * 12)) == 1    # r > BDU_BHU_MAX_RANK
+    assert lib.bdu_bhu_factor(6, 6, 0, 6, *([None] * 12)) == 1
     assert lib.bdu_update_bhu(None, None, None, 1) == 1
     assert lib.bdu_update_bhu_dev(None, None, None, 1) == 1
     assert lib.bdu_set_fault_injection(bdu.INJECT_BHU_STALL, 0) == 1

@@ -62,8 +62,12 @@ def _ptr(t):
 def run_factor(m, n, d, e, u, v, steps=None):
     bdu = _bdu()
     steps = n if steps is None else steps
+    U = np.asarray(u, dtype=np.float64).reshape(m, -1)
+    V = np.asarray(v, dtype=np.float64).reshape(n, -1)
+    rk = U.shape[1]
     kl, kr, wb = bdu.bhu_sizes(m, n, steps)
-    dd, ee, uu, vv = _dev(d), _dev(e if n > 1 else [0.0]), _dev(u), _dev(v)
+    dd, ee = _dev(d), _dev(e if n > 1 else [0.0])
+    uu, vv = _dev(U.T.reshape(-1)), _dev(V.T.reshape(-1))  # column-major
     alpha = torch.zeros(max(steps, 1), dtype=torch.float64, device="cuda")
     beta = torch.zeros(max(min(steps, n - 1), 1), dtype=torch.float64, device="cuda")
     Y = torch.zeros(max(m * kl, 1), dtype=torch.float64, device="cuda")
@@ -74,7 +78,7 @@ def run_factor(m, n, d, e, u, v, steps=None):
     s = torch.cuda.current_stream().cuda_stream
     bdu.bhu_factor(m, n, steps, _ptr(dd), _ptr(ee) if n > 1 else 0, _ptr(uu), _ptr(vv), _ptr(alpha),
                    _ptr(beta) if n > 1 else 0, _ptr(Y) if kl else 0, _ptr(W) if kr else 0, _ptr(SL) if kl else 0,
-                   _ptr(SR) if kr else 0, _ptr(ws), s)
+                   _ptr(SR) if kr else 0, _ptr(ws), s, r=rk)
     torch.cuda.synchronize()
     return {"alpha": alpha.cpu().numpy()[:steps], "beta": beta.cpu().numpy()[:min(steps, n - 1)],
             "Y": Y.cpu().numpy()[:m * kl].reshape(kl, m).T, "W": W.cpu().numpy()[:n * kr].reshape(kr, n).T,
@@ -100,6 +104,21 @@ def test_factor_matches_oracle(m, n):
         _vec_close(g["W"], o["W"], o["beta"], scale)
         for j in range(g["W"].shape[1]):
             assert not np.any(g["W"][:j + 1, j])
+
+
+@pytest.mark.parametrize("m,n,rk", [(64, 64, 2), (300, 200, 3), (530, 529, 8), (1030, 700, 5)])
+def test_factor_rank_r_matches_oracle(m, n, rk):
+    """Direct rank-r absorption: one sweep of Algorithm 1 on B + U V^T."""
+    rng = np.random.default_rng(m + 7 * rk)
+    d, e = rng.standard_normal(n), rng.standard_normal(n - 1)
+    U, V = rng.standard_normal((m, rk)), rng.standard_normal((n, rk))
+    g = run_factor(m, n, d, e, U, V)
+    o = H.bhu(d, e, U, V, m)
+    scale = np.linalg.norm(H.bidiag_dense(d, e, m) + U @ V.T)
+    assert np.abs(g["alpha"] - o["alpha"]).max() <= tol(n, scale)
+    assert np.abs(g["beta"] - o["beta"]).max() <= tol(n, scale)
+    _vec_close(g["Y"], o["Y"], o["alpha"], scale)
+    _vec_close(g["W"], o["W"], o["beta"], scale)
 
 
 @pytest.mark.parametrize("m,n", [(5, 3), (64, 64), (300, 200), (530, 529)])
@@ -171,7 +190,7 @@ def test_update_bhu_matches_oracle(m, n, r):
         for h in range(2):
             Bm = rng.standard_normal((m, r)); Cm = rng.standard_normal((n, r))
             F.update_bhu(Bm, Cm)
-            Q, d, e, P = H.update(Q, d, e, P, Bm, Cm)
+            Q, d, e, P = H.update_direct(Q, d, e, P, Bm, Cm)  # one sweep for the r columns
             A = A + Bm @ Cm.T
         Qg, dg, eg, Pg = F.read()
     scale = np.linalg.norm(A)
@@ -233,5 +252,27 @@ def test_full_size_against_the_givens_handle():
     assert np.abs(sh - sg).max() <= 1e-12 * sg[0]
     # ||A+||_F <= ||Bd||_F + ||b|| ||c||
     scale = np.sqrt(np.sum(d ** 2) + np.sum(e ** 2)) + np.linalg.norm(B) * np.linalg.norm(C)
+    assert np.abs(np.abs(dh) - np.abs(dg)).max() <= tol(n, scale)
+    assert np.abs(np.abs(eh) - np.abs(eg)).max() <= tol(n, scale)
+
+
+@pytest.mark.parametrize("m,n,rk", [(300, 200, 10), (257, 257, 3)])
+def test_update_bhu_rank_r_against_the_givens_handle(m, n, rk):
+    """A rank-r update by BHU (sweeps of up to 8 columns) and by the Givens
+    update (r rank-1 steps, bit-identical to its oracle) on two handles: the
+    bidiagonals agree up to signs, both factorizations reconstruct A + B C^T."""
+    bdu = _bdu()
+    Q, d, e, P = _factorization(m, n, 9 * m + rk)
+    rng = np.random.default_rng(rk)
+    Bm = rng.standard_normal((m, rk)); Cm = rng.standard_normal((n, rk))
+    A = Q @ H.bidiag_dense(d, e, m) @ P.T + Bm @ Cm.T
+    with bdu.Factorization(Q, d, e, P, precision=bdu.FP64) as F:
+        F.update_bhu(Bm, Cm)
+        Qh, dh, eh, Ph = F.read()
+    with bdu.Factorization(Q, d, e, P, precision=bdu.FP64) as F:
+        F.update(Bm, Cm)
+        _, dg, eg, _ = F.read()
+    scale = np.linalg.norm(A)
+    assert np.abs(Qh @ H.bidiag_dense(dh, eh[: n - 1], m) @ Ph.T - A).max() <= 1e-12 * scale
     assert np.abs(np.abs(dh) - np.abs(dg)).max() <= tol(n, scale)
     assert np.abs(np.abs(eh) - np.abs(eg)).max() <= tol(n, scale)
