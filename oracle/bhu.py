@@ -204,3 +204,58 @@ def update_direct(Q, d, e, P, Bm, Cm):
     r = bhu(d, e, U, V, m)
     Qk, Pk = factors(r["Y"], r["W"], m, n)
     return Q @ Qk, r["alpha"], r["beta"], P @ Pk
+
+
+# ---------------------------------------------------------------------------
+# The symmetric variant (Sec. 6, future directions: the updating algorithms
+# adapted to generate a tridiagonal).  A = Q T Q^T with T symmetric tridiagonal
+# (diagonal a, off-diagonal b); A + rho c c^T = Q (T + rho u u^T) Q^T with
+# u = Q^T c.  The same process as Algorithm 1 with one reflector per step
+# applied on both sides: column k's entries k+1..n give reflector k (Eq. house),
+# which acts on rows and columns k+1..n, so Q's first column is kept.  Readings:
+# n-2 reflectors (k = 1..n-2); the last off-diagonal entry and the diagonal
+# entries are read off the transformed matrix.
+# ---------------------------------------------------------------------------
+
+def tridiag_dense(a, b):
+    """The symmetric tridiagonal with diagonal a and off-diagonal b."""
+    n = len(a)
+    T = np.diag(np.asarray(a, dtype=np.float64))
+    if n > 1:
+        T += np.diag(np.asarray(b, dtype=np.float64), 1) + np.diag(np.asarray(b, dtype=np.float64), -1)
+    return T
+
+
+def tri(a, b, u, rho, steps=None):
+    """Householder tridiagonalization of T + rho u u^T, written out on the dense
+    matrix.  Returns alpha (steps,), beta (min(steps, n-1),), Y (n x k, the
+    normalized vectors, y_k with zeros in rows 1..k) and the transformed A."""
+    a = np.asarray(a, dtype=np.float64)
+    n = len(a)
+    t = n if steps is None else int(steps)
+    nt = max(n - 2, 0)
+    u = np.asarray(u, dtype=np.float64)
+    A = tridiag_dense(a, b) + rho * np.outer(u, u)
+    alpha = np.zeros(t)
+    beta = np.zeros(min(t, n - 1))
+    Y = np.zeros((n, min(t, nt)))
+    for k in range(t):
+        alpha[k] = A[k, k]
+        if k < nt:
+            beta[k], y = house(A[k + 1:, k])
+            Y[k + 1:, k] = y
+            A[k + 1:, :] -= 2.0 * np.outer(y, y @ A[k + 1:, :])
+            A[:, k + 1:] -= 2.0 * np.outer(A[:, k + 1:] @ y, y)
+        elif k == n - 2:
+            beta[k] = A[k + 1, k]
+    return {"alpha": alpha, "beta": beta, "Y": Y, "A": A}
+
+
+def tri_update(Q, a, b, rho, c):
+    """A + rho c c^T for A = Q T Q^T: u = Q^T c, the tridiagonalization of
+    T + rho u u^T, Q <- Q Q_k; returns (Q, alpha, beta)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    n = Q.shape[0]
+    r = tri(a, b, Q.T @ np.asarray(c, dtype=np.float64), rho)
+    Qk, _ = factors(r["Y"], np.zeros((1, 0)), n, 1)
+    return Q @ Qk, r["alpha"], r["beta"]

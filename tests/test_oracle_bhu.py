@@ -171,3 +171,69 @@ def test_rank_r_terminates(m, n, rk):
     assert np.abs(r["alpha"][rk + 1:]).max() <= 1e-13 * nf
     assert np.abs(r["beta"][rk + 1:]).max() <= 1e-13 * nf
     assert abs(np.sum(r["alpha"] ** 2) + np.sum(r["beta"] ** 2) - nf ** 2) <= 1e-12 * nf ** 2
+
+
+# ---- the symmetric (tridiagonal) variant
+
+def _tri_case(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n), rng.standard_normal(max(n - 1, 0)), rng.standard_normal(n), float(rng.choice([-1.5, 0.7, 2.0]))
+
+
+def test_tri_golden_3x3():
+    g = json.load(open(os.path.join(GOLDEN, "tri_3x3_worked_example.json")))
+    r = H.tri(g["a"], g["b"], g["u"], g["rho"])
+    assert np.allclose(r["alpha"], g["alpha"], rtol=0, atol=1e-14)
+    assert np.allclose(r["beta"], g["beta"], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 9, 30, 64])
+def test_tri_reconstruction_eigenvalues_first_column(n):
+    a, b, u, rho = _tri_case(n, 40 + n)
+    r = H.tri(a, b, u, rho)
+    M = H.tridiag_dense(a, b) + rho * np.outer(u, u)
+    Qk, _ = H.factors(r["Y"], np.zeros((1, 0)), n, 1)
+    Tp = H.tridiag_dense(r["alpha"], r["beta"])
+    scale = np.linalg.norm(M)
+    assert np.abs(Qk @ Tp @ Qk.T - M).max() <= 1e-14 * scale * max(n, 4)
+    assert np.array_equal(Qk[:, 0], np.eye(n)[:, 0])
+    assert np.abs(r["A"] - Tp).max() <= 1e-14 * scale * max(n, 4)
+    assert np.abs(np.linalg.eigvalsh(M) - np.linalg.eigvalsh(Tp)).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("n", [4, 9, 30, 64])
+def test_tri_matches_lapack_hessenberg_up_to_signs(n):
+    """LAPACK's Householder reduction to Hessenberg form also keeps e_1, so for a
+    symmetric matrix its tridiagonal equals this one up to signs."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    a, b, u, rho = _tri_case(n, 70 + n)
+    M = H.tridiag_dense(a, b) + rho * np.outer(u, u)
+    Hs = scipy_linalg.hessenberg(M)
+    r = H.tri(a, b, u, rho)
+    scale = np.linalg.norm(M)
+    assert np.abs(np.abs(np.diag(Hs)) - np.abs(r["alpha"])).max() <= 1e-12 * scale
+    assert np.abs(np.abs(np.diag(Hs, -1)) - np.abs(r["beta"])).max() <= 1e-12 * scale
+
+
+def test_tri_no_update_and_rank1_closed_forms():
+    a, b, u, _ = _tri_case(12, 3)
+    r = H.tri(a, b, u, 0.0)
+    assert np.array_equal(r["alpha"], a) and np.array_equal(np.abs(r["beta"]), np.abs(b))
+    # T = 0: rho u u^T has the one nonzero eigenvalue rho ||u||^2, carried by the
+    # leading 2 x 2 block
+    r = H.tri(np.zeros(12), np.zeros(11), u, 1.5)
+    nu = 1.5 * np.dot(u, u)
+    assert abs(r["alpha"][0] + r["alpha"][1] - nu) <= 1e-14 * nu
+    assert abs(r["alpha"][0] * r["alpha"][1] - r["beta"][0] ** 2) <= 1e-13 * nu ** 2
+    assert np.abs(r["alpha"][2:]).max() <= 1e-14 * nu and np.abs(r["beta"][1:]).max() <= 1e-14 * nu
+
+
+def test_tri_update_reconstructs():
+    rng = np.random.default_rng(8)
+    n = 20
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    a, b, c, rho = _tri_case(n, 9)
+    Qn, al, be = H.tri_update(Q, a, b, rho, c)
+    A1 = Q @ H.tridiag_dense(a, b) @ Q.T + rho * np.outer(c, c)
+    assert np.abs(Qn @ H.tridiag_dense(al, be) @ Qn.T - A1).max() <= 1e-13 * np.linalg.norm(A1)
+    assert np.array_equal(Qn[:, 0], Q[:, 0]) or np.abs(Qn[:, 0] - Q[:, 0]).max() <= 1e-15
