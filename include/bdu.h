@@ -253,6 +253,44 @@ bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t r, int64_t steps, const 
 bdu_status bdu_update_bhu(bdu_handle h, const double *B, const double *C, int64_t r);
 bdu_status bdu_update_bhu_dev(bdu_handle h, const double *dB, const double *dC, int64_t r);
 
+/* ---- The symmetric variant (Sec. 6: the updating algorithms adapted to
+ * generate a tridiagonal)
+ *
+ * A = Q T Q^T, n x n, T symmetric tridiagonal (diagonal a, off-diagonal b).
+ * A + rho c c^T = Q (T + rho u u^T) Q^T with u = Q^T c is brought back to
+ * tridiagonal form by the Householder process of BHU with one reflector per
+ * step applied on both sides: reflector k (k = 1..n-2) is built from column k's
+ * entries k+1..n and acts on rows and columns k+1..n, so Q's first column is
+ * kept.  Its product is Q_k = I - Y S Y^T (S = 2 T^{-1} of Eq. TR). */
+
+/* Sizes: *k = min(steps, n-2) reflectors, the device workspace bdu_tri_factor
+ * needs for `steps` steps, and the workspace bdu_tri_update_dev needs.  Any
+ * output may be NULL.  Errors: BDU_EINVAL (n < 1, steps out of range). */
+bdu_status bdu_tri_sizes(int64_t n, int64_t steps, int64_t *k, int64_t *workspace_bytes, int64_t *update_bytes);
+
+/* The tridiagonalization of T + rho u u^T, FP64, device pointers:
+ *   in:  a (n), b (n-1; may be NULL when n == 1), u (n), rho (finite);
+ *   out: alpha (steps), beta (min(steps, n-1); may be NULL when n == 1): the
+ *        first `steps` diagonal and off-diagonal entries of the new
+ *        tridiagonal; Y (n x k, leading dimension n): normalized reflector
+ *        vectors, y_k with zeros in rows 1..k; S (k x k, leading dimension k),
+ *        upper triangular, Q_k = I - Y S Y^T;
+ *   workspace: bdu_tri_sizes' workspace bytes, 16-byte aligned, the caller's;
+ *   stream: cudaStream_t (NULL = the legacy default stream).
+ * Returns when the work is done.  Deterministic; equal to the dense Householder
+ * process up to rounding.  Errors: BDU_EINVAL, BDU_ECUDA, BDU_ETIMEOUT (a grid
+ * barrier ran out). */
+bdu_status bdu_tri_factor(int64_t n, int64_t steps, const double *a, const double *b, double rho, const double *u,
+                          double *alpha, double *beta, double *Y, double *S, void *workspace, void *stream);
+
+/* A+ = A + rho c c^T in place: Q (n x n, column-major), a (n) and b (n-1) in
+ * device memory are replaced by Q+ and the new tridiagonal; c (n) device
+ * memory.  u = Q^T c, bdu_tri_factor, then Q <- Q - (Q Y)(S Y^T) (cuBLAS FP64).
+ * workspace: bdu_tri_sizes' update bytes, 16-byte aligned.  Returns when the
+ * work is done.  Errors: as bdu_tri_factor; BDU_ENOMEM if no cuBLAS handle. */
+bdu_status bdu_tri_update_dev(int64_t n, double *Q, double *a, double *b, double rho, const double *c,
+                              void *workspace, void *stream);
+
 /* Waits for all queued work and reports device-side failures
  * (BDU_ETIMEOUT, BDU_EINTERNAL, BDU_ECUDA). */
 bdu_status bdu_sync(bdu_handle h);

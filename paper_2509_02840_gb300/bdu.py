@@ -128,6 +128,12 @@ def load(build_if_missing: bool = True):
     vp = ctypes.c_void_p
     L.bdu_bhu_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + [vp] * 12
     L.bdu_bhu_factor.restype = ctypes.c_int
+    L.bdu_tri_sizes.argtypes = [ctypes.c_int64, ctypes.c_int64, i64p, i64p, i64p]
+    L.bdu_tri_sizes.restype = ctypes.c_int
+    L.bdu_tri_factor.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
+    L.bdu_tri_factor.restype = ctypes.c_int
+    L.bdu_tri_update_dev.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.c_double, vp, vp, vp]
+    L.bdu_tri_update_dev.restype = ctypes.c_int
     L.bdu_update_bhu.argtypes = [H, dp, dp, ctypes.c_int64]
     L.bdu_update_bhu.restype = ctypes.c_int
     L.bdu_update_bhu_dev.argtypes = [H, vp, vp, ctypes.c_int64]
@@ -218,6 +224,36 @@ def bhu_factor(m: int, n: int, steps: int, d: int, e: int, u: int, v: int, alpha
     L = load()
     ptrs = [ctypes.c_void_p(p or None) for p in (d, e, u, v, alpha, beta, Y, W, SL, SR, workspace, stream)]
     code = L.bdu_bhu_factor(int(m), int(n), int(r), int(steps), *ptrs)
+    if code != 0:
+        raise BduError(code, (L.bdu_last_error(None) or b"").decode())
+
+
+def tri_sizes(n: int, steps: int):
+    """bdu_tri_sizes: (k, factor workspace bytes, update workspace bytes)."""
+    L = load()
+    k, wb, ub = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    code = L.bdu_tri_sizes(int(n), int(steps), ctypes.byref(k), ctypes.byref(wb), ctypes.byref(ub))
+    if code != 0:
+        raise BduError(code, (L.bdu_last_error(None) or b"").decode())
+    return k.value, wb.value, ub.value
+
+
+def tri_factor(n: int, steps: int, a: int, b: int, rho: float, u: int, alpha: int, beta: int, Y: int, S: int,
+               workspace: int, stream: int = 0):
+    """bdu_tri_factor with device pointers (ints; 0 for NULL)."""
+    L = load()
+    v = lambda p: ctypes.c_void_p(p or None)
+    code = L.bdu_tri_factor(int(n), int(steps), v(a), v(b), float(rho), v(u), v(alpha), v(beta), v(Y), v(S),
+                            v(workspace), v(stream))
+    if code != 0:
+        raise BduError(code, (L.bdu_last_error(None) or b"").decode())
+
+
+def tri_update_dev(n: int, Q: int, a: int, b: int, rho: float, c: int, workspace: int, stream: int = 0):
+    """bdu_tri_update_dev: A + rho c c^T in place on device buffers."""
+    L = load()
+    v = lambda p: ctypes.c_void_p(p or None)
+    code = L.bdu_tri_update_dev(int(n), v(Q), v(a), v(b), float(rho), v(c), v(workspace), v(stream))
     if code != 0:
         raise BduError(code, (L.bdu_last_error(None) or b"").decode())
 

@@ -1388,6 +1388,91 @@ bdu_status bdu_bhu_factor(int64_t m, int64_t n, int64_t r, int64_t steps, const 
   return BDU_OK;
 }
 
+// ---- the symmetric variant (Sec. 6): A = Q T Q^T, A + rho c c^T
+
+bdu_status bdu_tri_sizes(int64_t n, int64_t steps, int64_t *k, int64_t *workspace_bytes, int64_t *update_bytes) {
+  if (n < 1 || steps < 0 || steps > n || n > (int64_t)1 << 30)
+    return fail(nullptr, BDU_EINVAL, "bdu_tri_sizes: need n >= 1 and 0 <= steps <= n");
+  const BhuSizes z = bhu_sizes(n, n, steps);
+  const int64_t ws = (int64_t)(sizeof(double) * z.ws_doubles + sizeof(unsigned) * z.ws_counters + sizeof(int) + 16);
+  if (k) *k = z.kr;
+  if (workspace_bytes) *workspace_bytes = ws;
+  if (update_bytes) {
+    const BhuSizes f = bhu_sizes(n, n, n);
+    const int64_t kk = f.kr > 0 ? f.kr : 1;
+    // the factor's workspace, then u, alpha, beta, Y, S and two n x k products
+    const int64_t wsf = (int64_t)(sizeof(double) * f.ws_doubles + sizeof(unsigned) * f.ws_counters + sizeof(int) + 16);
+    *update_bytes = ((wsf + 15) / 16) * 16 + (int64_t)sizeof(double) * (3 * (n + 2) + n * kk + kk * kk + 2 * n * kk) + 64;
+  }
+  return BDU_OK;
+}
+
+bdu_status bdu_tri_factor(int64_t n, int64_t steps, const double *a, const double *b, double rho, const double *u,
+                          double *alpha, double *beta, double *Y, double *S, void *workspace, void *stream) {
+  if (n < 1 || steps < 0 || steps > n || n > (int64_t)1 << 30)
+    return fail(nullptr, BDU_EINVAL, "bdu_tri_factor: need n >= 1 and 0 <= steps <= n");
+  if (steps == 0) return BDU_OK;
+  if (!std::isfinite(rho)) return fail(nullptr, BDU_EINVAL, "bdu_tri_factor: non-finite rho");
+  const BhuSizes z = bhu_sizes(n, n, steps);
+  if (!a || !u || !alpha || !workspace || (n > 1 && (!b || !beta)) || (z.kr > 0 && (!Y || !S)))
+    return fail(nullptr, BDU_EINVAL, "bdu_tri_factor: NULL argument");
+  if (((uintptr_t)workspace & 15) != 0) return fail(nullptr, BDU_EINVAL, "bdu_tri_factor: workspace not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *ws = (double *)workspace;
+  unsigned *cnt = (unsigned *)(ws + z.ws_doubles);
+  int *status = (int *)(cnt + z.ws_counters);
+  cudaError_t ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * z.ws_counters + sizeof(int), s);
+  if (ce == cudaSuccess)
+    ce = launch_tri((int)n, (int)steps, a, n > 1 ? b : a, rho, u, alpha, n > 1 ? beta : alpha, Y, S, ws, cnt, status, s);
+  int hst = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(nullptr, BDU_ECUDA, "bdu_tri_factor: %s", cudaGetErrorString(ce));
+  if (hst & ERR_BHU) return fail(nullptr, BDU_ETIMEOUT, "bdu_tri_factor: a grid barrier ran out");
+  return BDU_OK;
+}
+
+bdu_status bdu_tri_update_dev(int64_t n, double *Q, double *a, double *b, double rho, const double *c,
+                              void *workspace, void *stream) {
+  if (n < 1 || n > (int64_t)1 << 30) return fail(nullptr, BDU_EINVAL, "bdu_tri_update_dev: need n >= 1");
+  if (!Q || !a || !c || !workspace || (n > 1 && !b)) return fail(nullptr, BDU_EINVAL, "bdu_tri_update_dev: NULL argument");
+  if (((uintptr_t)workspace & 15) != 0) return fail(nullptr, BDU_EINVAL, "bdu_tri_update_dev: workspace not 16-byte aligned");
+  const BhuSizes f = bhu_sizes(n, n, n);
+  const int64_t k = f.kr, kk = k > 0 ? k : 1;
+  const int64_t wsf = (int64_t)(sizeof(double) * f.ws_doubles + sizeof(unsigned) * f.ws_counters + sizeof(int) + 16);
+  char *base = (char *)workspace;
+  double *dv = (double *)(base + ((wsf + 15) / 16) * 16);
+  double *u = dv, *al = u + (n + 2), *be = al + (n + 2), *Y = be + (n + 2), *S = Y + n * kk, *G1 = S + kk * kk,
+         *G2 = G1 + n * kk;
+  cudaStream_t s = (cudaStream_t)stream;
+  cublasHandle_t cb = nullptr;
+  if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) return fail(nullptr, BDU_ENOMEM, "bdu_tri_update_dev: cublasCreate failed");
+  bdu_status st = BDU_OK;
+  const double one = 1.0, zero = 0.0, minus = -1.0;
+  // u = Q^T c
+  if (cublasSetStream(cb, s) != CUBLAS_STATUS_SUCCESS ||
+      cublasDgemv(cb, CUBLAS_OP_T, (int)n, (int)n, &one, Q, (int)n, c, 1, &zero, u, 1) != CUBLAS_STATUS_SUCCESS)
+    st = fail(nullptr, BDU_ECUDA, "bdu_tri_update_dev: the projection failed");
+  if (st == BDU_OK) st = bdu_tri_factor(n, n, a, b, rho, u, al, be, Y, S, workspace, stream);
+  // Q <- Q - (Q Y) (S Y^T); a, b <- alpha, beta
+  if (st == BDU_OK && k > 0 &&
+      (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, (int)k, (int)n, &one, Q, (int)n, Y, (int)n, &zero, G1, (int)n) !=
+           CUBLAS_STATUS_SUCCESS ||
+       cublasDtrmm(cb, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, (int)n, (int)k, &one,
+                   S, (int)k, G1, (int)n, G2, (int)n) != CUBLAS_STATUS_SUCCESS ||
+       cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, (int)n, (int)k, &minus, G2, (int)n, Y, (int)n, &one, Q, (int)n) !=
+           CUBLAS_STATUS_SUCCESS))
+    st = fail(nullptr, BDU_ECUDA, "bdu_tri_update_dev: a cuBLAS product failed");
+  if (st == BDU_OK) {
+    cudaError_t ce = cudaMemcpyAsync(a, al, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess && n > 1) ce = cudaMemcpyAsync(b, be, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) st = fail(nullptr, BDU_ECUDA, "bdu_tri_update_dev: %s", cudaGetErrorString(ce));
+  }
+  cublasDestroy(cb);
+  return st;
+}
+
 static bdu_status bhu_ensure(bdu_ctx *h) {
   if (h->bhu_ws) return BDU_OK;
   const int64_t m = h->m, n = h->n;

@@ -233,6 +233,12 @@ cudaError_t launch_bhu(int m, int n, int steps, int rk, const double *d, const d
                        int64_t ldu, const double *v, int64_t ldv, double *alpha, double *beta, double *Y, double *W,
                        double *SL, double *SR, double *ws, unsigned *cnt, int *status, cudaStream_t s,
                        int64_t *launches);
+// The symmetric variant: the tridiagonalization of T + rho u u^T (n x n; Y
+// n x k, S k x k with k = bhu_sizes(n, n, steps).kr; the workspace of
+// bhu_sizes(n, n, steps)).
+cudaError_t launch_tri(int n, int steps, const double *a, const double *b, double rho, const double *u,
+                       double *alpha, double *beta, double *Y, double *S, double *ws, unsigned *cnt, int *status,
+                       cudaStream_t s);
 cudaError_t launch_bhu_band_get(double *band, int m, int n, double *d, double *e, cudaStream_t s);
 cudaError_t launch_bhu_band_put(double *band, int m, int n, const double *d, const double *e, cudaStream_t s);
 

@@ -118,6 +118,7 @@ struct BhuArgs {
   double *z, *x, *a, *q, *ra, *as, *g, *hv, *p1, *gw, *hw, *sv, *part, *part2, *tp;
   unsigned *cnt, *bar;  // counters per row group (zero, left zero); the barrier's count and generation (zero)
   int *status;
+  double rho;  // the symmetric variant's weight (k_tri_persist)
   int spin;   // bound on one barrier wait (polls)
   int stall;  // failure injection: block 0 leaves at once, so the others' first wait runs out
 };
@@ -509,6 +510,105 @@ __global__ void k_band_put(BandPtrs b, int n, const double *d, const double *e) 
   }
 }
 
+// The symmetric variant (Sec. 6, future directions): the Householder
+// tridiagonalization of T + rho u u^T (T symmetric tridiagonal, diagonal d,
+// off-diagonal e; u = Q^T c).  Step j is the left half of a BHU step with the
+// reflector applied on both sides: column j of Q_{j-1}^T (T + rho u u^T) Q_{j-1}
+// from z = Q_{j-1} e_j, x = T z + u (rho u^T z), a = Q_{j-1}^T x, with
+// Q_{j-1} = I - W R' W^T (w_j with zeros in rows 0..j, as the right reflectors
+// of BHU); alpha_j = a(j), and the reflector of a(j+1..n) gives beta_j and w_j.
+// Eight phases a step.
+__global__ void __launch_bounds__(kT, 1) k_tri_persist(BhuArgs A) {
+  unsigned gen = 0;
+  if (A.stall && blockIdx.x == 0) return;
+  const int n = A.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+  for (int j = 0; j < A.steps; j++) {
+    const int cY = min(j, A.nr);
+    // z = Q_{j-1} e_j = e_j - W p1 (p1 = R' W^T e_j from the previous step); partials of u^T z
+    if (cY > 0) {
+      rowprod<1>(A, A.W, n, 0, n, cY, kW, A.p1, 1, nullptr, 0, [&](int r, double s, double, double *c) {
+        const double zr = (r == j ? 1.0 : 0.0) - s;
+        A.z[r] = zr;
+        c[0] = A.u[r] * zr;
+      }, A.tp);
+    } else {
+      for (int r = gtid; r < n; r += gthreads) A.z[r] = r == j ? 1.0 : 0.0;
+    }
+    if (!grid_barrier(A, gen)) return;
+    // x = T z + u (rho u^T z)
+    {
+      const double w = A.rho * (cY > 0 ? tp_sum(A.tp, groups_of(n)) : A.u[j]);
+      for (int r = gtid; r < n; r += gthreads) {
+        double s = A.d[r] * __ldcg(A.z + r);
+        if (r + 1 < n) s = fma(A.e[r], __ldcg(A.z + r + 1), s);
+        if (r > 0) s = fma(A.e[r - 1], __ldcg(A.z + r - 1), s);
+        A.x[r] = fma(A.u[r], w, s);
+      }
+    }
+    if (!grid_barrier(A, gen)) return;
+    // a = Q_{j-1}^T x (rows j..n); partials of a^2 over rows j+1..n
+    const double *acol = A.x;
+    if (cY > 0) {
+      colprod(A.W, n, 0, n, cY, kW, A.x, A.g);
+      if (!grid_barrier(A, gen)) return;
+      colprod(A.SR, A.ldr, 0, cY, cY, kUT, A.g, A.hv);
+      if (!grid_barrier(A, gen)) return;
+      rowprod<1>(A, A.W, n, j, n, cY, kW, A.hv, 1, nullptr, 0, [&](int r, double s, double, double *c) {
+        const double ar = __ldcg(A.x + r) - s;
+        A.a[r] = ar;
+        c[0] = r > j ? ar * ar : 0.0;
+      }, A.tp);
+      acol = A.a;
+    } else {
+      group_partials(j, n, [&](int r) { const double xr = __ldcg(A.x + r); return r > j ? xr * xr : 0.0; }, A.tp);
+    }
+    if (!grid_barrier(A, gen)) return;
+    // alpha_j = a(j); the reflector of a(j+1..n): w_j, beta_j, R'(j, j) = 2
+    const bool make = j < A.nr;
+    double *wj = A.W + (size_t)j * n;
+    if (gtid == 0) A.alpha[j] = __ldcg(acol + j);
+    if (make) {
+      const double a0 = __ldcg(acol + j + 1);
+      const double sigma = sqrt(tp_sum(A.tp, groups_of(n - j)));
+      const double sg = copysign(1.0, a0);
+      const double inv = sigma > 0.0 ? 1.0 / sqrt(2.0 * sigma * (sigma + fabs(a0))) : 0.0;
+      for (int r = j + 1 + gtid; r < n; r += gthreads) {
+        const double w = (r == j + 1 ? fma(sg, sigma, a0) : __ldcg(acol + r)) * inv;
+        wj[r] = w;
+        if (j == 0 && r == 1) A.p1[0] = 2.0 * w;  // the next step's R'_0 W_0^T e_1
+      }
+      if (gtid == 0) {
+        A.beta[j] = sigma > 0.0 ? -sg * sigma : 0.0;
+        A.SR[j + (size_t)j * A.ldr] = 2.0;
+      }
+    } else if (j == n - 2 && gtid == 0) {
+      A.beta[j] = __ldcg(acol + j + 1);
+    }
+    if (!grid_barrier(A, gen)) return;
+    if (j + 1 >= A.steps) continue;
+    // the next step's p1 = R'_j W_j^T e_{j+1}
+    if (make && j > 0) {
+      colprod(A.W, n, 0, n, j, kW, wj, A.sv);
+      if (!grid_barrier(A, gen)) return;
+      const double om = __ldcg(wj + j + 1);
+      rowprod<2>(A, A.SR, A.ldr, 0, j, j, kUT, A.sv, 1, A.W + j + 1, n, [&](int r, double ss, double sw, double *) {
+        const double col = -2.0 * ss;
+        A.SR[r + (size_t)j * A.ldr] = col;
+        A.p1[r] = fma(om, col, sw);
+      }, nullptr);
+      if (gtid == 0) A.p1[j] = 2.0 * om;
+      if (!grid_barrier(A, gen)) return;
+    } else if (!make && A.nr > 0) {
+      const int c2 = A.nr;
+      rowprod<1>(A, A.SR, A.ldr, 0, c2, c2, kUT, A.W + j + 1, n, nullptr, 0, [&](int r, double s, double, double *) {
+        A.p1[r] = s;
+      }, nullptr);
+      if (!grid_barrier(A, gen)) return;
+    }
+  }
+}
+
 int grid_for(int64_t count, int threads) {
   int64_t g = (count + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 1184 ? 1184 : g));
@@ -579,6 +679,50 @@ cudaError_t launch_bhu(int m, int n, int steps, int rk, const double *d, const d
   err = cudaLaunchCooperativeKernel((const void *)k_bhu_persist, dim3(blocks), dim3(kT), args, 0, s);
   if (launches) *launches += 1;
   return err;
+}
+
+cudaError_t launch_tri(int n, int steps, const double *a, const double *b, double rho, const double *u,
+                       double *alpha, double *beta, double *Y, double *S, double *ws, unsigned *cnt, int *status,
+                       cudaStream_t s) {
+  const BhuSizes z = bhu_sizes(n, n, steps);
+  const int64_t chunks = (n + kCols - 1) / kCols + 1;
+  const int64_t groups = (n + kT - 1) / kT + 1;
+  BhuArgs A{};
+  A.m = n; A.n = n; A.steps = steps;
+  A.nl = 0;
+  A.nr = n > 2 ? n - 2 : 0;  // reflectors of a complete run
+  const int64_t k = z.kr;     // reflectors of this run
+  A.ldl = 1;
+  A.ldr = k > 0 ? k : 1;
+  A.ldp = n;
+  A.d = a; A.e = b; A.u = u; A.v = u; A.rho = rho;
+  A.rk = 1; A.ldu = n; A.ldv = n; A.tps = groups;
+  A.alpha = alpha; A.beta = beta; A.W = Y; A.SR = S;
+  double *p = ws;
+  double **vecs[12] = {&A.z, &A.x, &A.a, &A.q, &A.ra, &A.as, &A.g, &A.hv, &A.p1, &A.gw, &A.hw, &A.sv};
+  for (double **vp : vecs) { *vp = p; p += n; }
+  A.part = p; p += chunks * n;
+  A.part2 = p; p += chunks * n;
+  A.tp = p;
+  A.cnt = cnt;
+  A.bar = cnt + groups;
+  A.status = status;
+  const Injection inj = injection();
+  A.stall = inj.site == BDU_INJECT_BHU_STALL ? 1 : 0;
+  A.spin = A.stall ? (int)(inj.value < kBarSpin ? inj.value : kBarSpin) : kBarSpin;
+  cudaError_t err = cudaSuccess;
+  if (k > 0) err = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * k, s);
+  if (err == cudaSuccess && k > 0) err = cudaMemsetAsync(S, 0, sizeof(double) * (size_t)k * k, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), s);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0, per = 0;
+  err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tri_persist, kT, 0);
+  if (err != cudaSuccess) return err;
+  if (per < 1) return cudaErrorLaunchOutOfResources;
+  void *args[] = {&A};
+  return cudaLaunchCooperativeKernel((const void *)k_tri_persist, dim3(sms), dim3(kT), args, 0, s);
 }
 
 cudaError_t launch_bhu_band_get(double *band, int m, int n, double *d, double *e, cudaStream_t s) {

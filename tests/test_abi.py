@@ -141,3 +141,19 @@ def test_bhu_sizes_and_argument_checks_without_a_gpu(lib):
     assert lib.bdu_set_fault_injection(bdu.INJECT_BHU_STALL, 0) == 1
     assert lib.bdu_set_fault_injection(bdu.INJECT_BHU_STALL, 5) == 0
     assert lib.bdu_set_fault_injection(bdu.INJECT_NONE, 0) == 0
+
+
+def test_tri_sizes_and_argument_checks_without_a_gpu(lib):
+    """bdu_tri_sizes gives the symmetric variant's reflector count (n-2 for a
+    complete run) and validates its sizes; the entry points reject bad
+    arguments before touching the device."""
+    import ctypes
+    k, wb, ub = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    for (n, t, ek) in ((6, 6, 4), (6, 2, 2), (2, 2, 0), (1, 1, 0)):
+        assert lib.bdu_tri_sizes(n, t, ctypes.byref(k), ctypes.byref(wb), ctypes.byref(ub)) == 0
+        assert k.value == ek and wb.value > 0 and ub.value > wb.value
+    assert lib.bdu_tri_sizes(0, 0, None, None, None) == 1
+    assert lib.bdu_tri_sizes(5, 6, None, None, None) == 1
+    assert lib.bdu_tri_factor(6, 6, None, None, 1.0, None, None, None, None, None, None, None) == 1
+    assert lib.bdu_tri_factor(6, 7, None, None, 1.0, None, None, None, None, None, None, None) == 1
+    assert lib.bdu_tri_update_dev(6, None, None, None, 1.0, None, None, None) == 1
