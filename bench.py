@@ -339,6 +339,38 @@ def bhu_bench(steps=2, shapes=None):
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
                                   "frac": achieved * 1e12 / peak, "flops_per_update": flops,
                                   "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}}
+    # the symmetric variant (Sec. 6): A + rho c c^T for A = Q T Q^T, n = M, in place
+    n = M
+    k, _, ub = bdu.tri_sizes(n, n)
+    g = np.random.default_rng(77)
+    # an orthogonal Q (its row-major storage read as column-major is its transpose, also orthogonal)
+    Qt = torch.linalg.qr(torch.from_numpy(g.standard_normal((n, n))).cuda())[0].contiguous()
+    at = torch.from_numpy(g.uniform(1.0, 10.0, n)).cuda()
+    bt = torch.from_numpy(g.standard_normal(n - 1)).cuda()
+    cs = [torch.from_numpy(g.standard_normal(n)).cuda() for _ in range(steps + 1)]
+    wst = torch.zeros((ub + 7) // 8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bdu.tri_update_dev(n, Qt.data_ptr(), at.data_ptr(), bt.data_ptr(), 1.0, cs[0].data_ptr(), wst.data_ptr(),
+                           stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in cs[1:]:
+            bdu.tri_update_dev(n, Qt.data_ptr(), at.data_ptr(), bt.data_ptr(), 1.0, c.data_ptr(), wst.data_ptr(),
+                               stream.cuda_stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # multiplications of the reflector products (four passes over the trapezoidal Y a step,
+    # sum_j 4 (n - j/2) j ~ 4/3 n^3) and the update of Q (4 n^2 k + n k^2), two flops each
+    flops = 2 * (4.0 / 3.0) * n ** 3 + 4 * n * n * k + n * k * k
+    out[f"tridiagonal_{n}"] = {"n": n, "ms_per_update": ms, "updates_per_s": 1e3 / ms, "steps": steps,
+                               "what": "A + rho c c^T for A = Q T Q^T (bdu_tri_update_dev: u = Q^T c, the "
+                                       "tridiagonalization of T + rho u u^T, Q updated), device time",
+                               "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12,
+                                            "peak": peak / 1e12, "unit": "TFLOP/s",
+                                            "frac": flops / (ms * 1e-3) / peak, "flops_per_update": flops,
+                                            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}}
     return out
 
 
