@@ -179,33 +179,58 @@ __device__ __forceinline__ double tp_sum(const double *tp, int groups) {
   return s;
 }
 
-// out[c] = sum_{r in [lo(c), hi(c))} M(r, c) x[r] for c < C: one warp per
-// column over the grid's warps, lanes over rows in order, a fixed shuffle tree.
+// out[c] = sum_{r in [lo(c), hi(c))} M(r, c) x[r] for c < C.  A column goes to
+// a group of wpc warps of one block (wpc = the grid's warps over C, a power of
+// two up to 16: long columns get many warps when there are few of them); the
+// lanes of the group take its rows in order, eight loads in flight each, and
+// the group's sums are added in warp order (fixed shuffle tree inside a warp):
+// the same result on every run (the split depends only on C and the grid).
 __device__ void colprod(const double *__restrict__ M, int64_t ld, int r0, int R, int C, int shape,
                         const double *__restrict__ x, double *__restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < C; c += warps) {
-    const int lo = col_lo(shape, c, r0), hi = col_hi(shape, c, R);
-    const double *col = M + (size_t)c * ld;
-    // eight independent loads of each operand in flight per lane
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    int r = lo + lane;
-    for (; r + 7 * 32 < hi; r += 8 * 32) {
-      double cv[8], xv[8];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int total = gridDim.x * nwb;
+  int wpc = 1;
+  while (wpc < nwb && wpc * 2 * C <= total) wpc *= 2;
+  const int gpb = nwb / wpc;                            // column groups per block
+  const int grp = warp / wpc, wi = warp - grp * wpc;    // this warp's group and rank in it
+  const int groups = gridDim.x * gpb;
+  const int stride = 32 * wpc;
+  for (int base = 0; base < C; base += groups) {        // the same trip count in every block
+    const int c = base + blockIdx.x * gpb + grp;
+    double s = 0.0;
+    if (c < C) {
+      const int lo = col_lo(shape, c, r0), hi = col_hi(shape, c, R);
+      const double *col = M + (size_t)c * ld;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      int r = lo + wi * 32 + lane;
+      for (; r + 7 * stride < hi; r += 8 * stride) {
+        double cv[8], xv[8];
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        cv[k] = __ldcg(col + r + 32 * k);
-        xv[k] = __ldcg(x + r + 32 * k);
+        for (int k = 0; k < 8; k++) {
+          cv[k] = __ldcg(col + r + stride * k);
+          xv[k] = __ldcg(x + r + stride * k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[k & 3] = fma(cv[k], xv[k], acc[k & 3]);
       }
+      for (; r < hi; r += stride) acc[0] = fma(__ldcg(col + r), __ldcg(x + r), acc[0]);
+      s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
-      for (int k = 0; k < 8; k++) acc[k & 3] = fma(cv[k], xv[k], acc[k & 3]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
-    for (; r < hi; r += 32) acc[0] = fma(__ldcg(col + r), __ldcg(x + r), acc[0]);
-    double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[c] = s;
+    if (wpc == 1) {
+      if (c < C && lane == 0) out[c] = s;
+    } else {
+      __syncthreads();
+      if (lane == 0) red[warp] = s;
+      __syncthreads();
+      if (c < C && wi == 0 && lane == 0) {
+        double t = 0.0;
+        for (int k = 0; k < wpc; k++) t += red[grp * wpc + k];
+        out[c] = t;
+      }
+    }
   }
 }
 
