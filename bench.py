@@ -198,10 +198,10 @@ ALU_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # root, 2 divisions counted as one flop each).
 CHASE_FLOPS_PER_ROTATION = 26
 # DRAM bytes (read + write) of one mixed-form chase launch at m = n = 4096, from one
-# ncu capture of this benchmark's launches: the rotation records written
-# (FP32 (c, s) and an int32 pair index per rotation, 12 B x 25.2M = 302 MB, part of
-# which is still in L2 when the launch ends).
-CHASE_TRAFFIC_4096 = 6.08e6 + 248.72e6
+# ncu capture (one pass) of this benchmark's launches with the chase kernel as it is:
+# the rotation records written (FP32 (c, s) and an int32 pair index per rotation,
+# 12 B x 25.2M = 302 MB, part of which is still in L2 when the launch ends).
+CHASE_TRAFFIC_4096 = 5.91e6 + 248.74e6
 
 
 def roofline(st, precision, rotations_per_update, launches_per_update, steps_per_update=None):
