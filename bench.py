@@ -265,6 +265,10 @@ def apply_roofline(st, rotations_per_update):
             "algorithmic_bytes": alg, "ms_per_launch": per_launch_ms, "achieved": ach, "unit": "GB/s",
             "peak": hbm, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None,
             "frac": ach / hbm if hbm else None,
+            # the work the rotations define (6 flops per rotation and row), which the
+            # blocked apply (orders >= 1024) performs as tensor-core products of
+            # accumulated rotation blocks: far from HBM-bound
+            "rotation_tflops": 6.0 * (rotations_per_update / 2) * M / (per_launch_ms * 1e-3) / 1e12,
             "note": "timed beside the concurrent chase of the next update (overlapped form)"}
 
 
