@@ -237,3 +237,63 @@ def test_tri_update_reconstructs():
     A1 = Q @ H.tridiag_dense(a, b) @ Q.T + rho * np.outer(c, c)
     assert np.abs(Qn @ H.tridiag_dense(al, be) @ Qn.T - A1).max() <= 1e-13 * np.linalg.norm(A1)
     assert np.array_equal(Qn[:, 0], Q[:, 0]) or np.abs(Qn[:, 0] - Q[:, 0]).max() <= 1e-15
+
+
+# ---- the pins catch plausible mistakes planted in copies of the oracle
+
+def _mutant(src_old, src_new):
+    """A copy of oracle.bhu with one line changed (compiled from its source)."""
+    import inspect
+    import types
+    src = inspect.getsource(H)
+    assert src.count(src_old) == 1, src_old
+    mod = types.ModuleType("bhu_mutant")
+    exec(compile(src.replace(src_old, src_new), "bhu_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+def _passes_pins(M):
+    """The golden examples, reconstruction with the factors, agreement with the
+    Givens oracle up to signs and with LAPACK's Hessenberg reduction."""
+    try:
+        g = json.load(open(os.path.join(GOLDEN, "bhu_2x2_worked_example.json")))
+        r = M.bhu(g["d"], g["e"], g["u"], g["v"], g["m"])
+        if not (np.allclose(r["alpha"], g["alpha"], atol=1e-14) and np.allclose(r["beta"], g["beta"], atol=1e-14)):
+            return False
+        g = json.load(open(os.path.join(GOLDEN, "tri_3x3_worked_example.json")))
+        r = M.tri(g["a"], g["b"], g["u"], g["rho"])
+        if not (np.allclose(r["alpha"], g["alpha"], atol=1e-14) and np.allclose(r["beta"], g["beta"], atol=1e-14)):
+            return False
+        for (m, n) in ((9, 6), (7, 7)):
+            d, e, u, v = _case(m, n, m + n)
+            r = M.bhu(d, e, u, v, m)
+            Qk, Pk = M.factors(r["Y"], r["W"], m, n)
+            A0 = M.bidiag_dense(d, e, m) + np.outer(u, v)
+            if np.abs(Qk @ M.bidiag_dense(r["alpha"], r["beta"], m) @ Pk.T - A0).max() > 1e-12:
+                return False
+            dg, eg = O.generate(m, n, d, e, u.reshape(m, 1), v.reshape(n, 1))[:2]
+            if np.abs(np.abs(r["alpha"]) - np.abs(dg)).max() > 1e-10 or np.abs(np.abs(r["beta"]) - np.abs(eg)).max() > 1e-10:
+                return False
+        a, b, u, rho = _tri_case(8, 2)
+        r = M.tri(a, b, u, rho)
+        Qk, _ = M.factors(r["Y"], np.zeros((1, 0)), 8, 1)
+        Mx = M.tridiag_dense(a, b) + rho * np.outer(u, u)
+        return np.abs(Qk @ M.tridiag_dense(r["alpha"], r["beta"]) @ Qk.T - Mx).max() <= 1e-12
+    except (AssertionError, ValueError, IndexError, np.linalg.LinAlgError):
+        return False
+
+
+def test_pins_pass_on_the_oracle_itself():
+    assert _passes_pins(H)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("    y[0] += s * sigma\n", "    y[0] -= s * sigma\n"),                                   # the other reflector sign
+    ("            beta[k], w = house(A[k, k + 1:])\n", "            beta[k], w = house(A[min(k + 1, m - 1), k + 1:])\n"),  # row k+1
+    ("            A[k:, :] -= 2.0 * np.outer(y, y @ A[k:, :])\n", "            A[k:, :] -= 1.0 * np.outer(y, y @ A[k:, :])\n"),  # a dropped 2
+    ("            A[:, k + 1:] -= 2.0 * np.outer(A[:, k + 1:] @ w, w)\n", "            A[:, k + 1:] -= 2.0 * np.outer(A[:, k + 1:] @ w, w.T)[:, ::-1]\n"),  # a reversed vector
+    ("            A[:, k + 1:] -= 2.0 * np.outer(A[:, k + 1:] @ y, y)\n", "            pass\n"),   # one-sided symmetric step
+    ("    A = tridiag_dense(a, b) + rho * np.outer(u, u)\n", "    A = tridiag_dense(a, b) - rho * np.outer(u, u)\n"),  # wrong sign of rho
+])
+def test_pins_catch_a_planted_mistake(old, new):
+    assert not _passes_pins(_mutant(old, new))
