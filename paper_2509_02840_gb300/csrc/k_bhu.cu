@@ -1,7 +1,8 @@
 // BHU, the bidiagonal Householder update (Sec. 3.3, Algorithm 1, Theorem 1),
 // FP64, on the GPU.
 //
-// The m x n matrix A = B + u v^T (B upper bidiagonal, m >= n) is
+// The m x n matrix A = B + U V^T (B upper bidiagonal, m >= n; U, V the rk <= 8
+// projected columns of a rank-rk update, absorbed in one sweep) is
 // bidiagonalized by Householder reflectors applied alternately from the left
 // and the right, without forming A.  After j left and j right reflectors
 //
@@ -17,10 +18,10 @@
 //
 // Step j needs one column and one row of the transformed matrix (the products
 // a_k = A_{k-1,k-1} e_k and a*_{k+1} of Algorithm 1); both come from the
-// factored form Q^T (B + u v^T) P that Theorem 1 expands:
+// factored form Q^T (B + U V^T) P that Theorem 1 expands:
 //
-//   column j:  z = P_{j-1} e_j,  x = B z + u (v^T z),  a = Q_{j-1}^T x,
-//   row j:     q = Q_j e_j,      r = B^T q + v (u^T q), a* = P_{j-1}^T r,
+//   column j:  z = P_{j-1} e_j,  x = B z + U (V^T z),  a = Q_{j-1}^T x,
+//   row j:     q = Q_j e_j,      r = B^T q + V (U^T q), a* = P_{j-1}^T r,
 //
 // each O((m + n) j) work in products with Y, W, S, R'.  The reflector of a
 // (rows j..m) gives alpha_j and y_j, the reflector of a* (columns j+1..n)
@@ -31,8 +32,9 @@
 //
 // One cooperative launch runs the whole loop; the blocks meet at a grid
 // barrier (bounded waits) between the phases of a step, 16 at most per step.
-// Column products: one warp per column, lanes over rows in order, a fixed
-// shuffle tree.  Row products: tiles of 512 rows x 64 columns, partial sums per
+// Column products: a column to one warp, or to a group of up to 16 warps of a
+// block when there are few columns, lanes over rows in order, a fixed shuffle
+// tree.  Row products: tiles of 512 rows x 64 columns, partial sums per
 // column chunk, added in chunk order by the last block of each row group to
 // finish, which also sums the group's share of the dot product or norm the next
 // phase needs.  The new column of S (R') and the next product with it are one
